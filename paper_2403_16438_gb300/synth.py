@@ -1,0 +1,228 @@
+"""Seeded synthetic voltage-imaging videos with planted rigid shifts.
+
+This module only makes inputs.  It holds none of the motion-correction or
+summary arithmetic, and both the CUDA path's tests and the CPU oracle's tests
+take their inputs from it.
+
+Content model (the workloads the paper evaluates on are not available, so
+these stand in for them; shapes and rates follow the paper's Fig. 1 video and
+its datasets table):
+  * background: two axis-aligned anisotropic 2-D Gaussians on a pedestal;
+  * neurons: ellipses with a 1-px logistic edge, baseline brightness 25 % of
+    the background amplitude, limited pairwise overlap;
+  * activity: Poisson spike trains; each spike adds dF/F * exp(-k/3) for
+    k >= 0 frames after it (3-frame decay);
+  * noise: Poisson shot noise on the expected counts plus Gaussian read
+    noise, rounded and clamped to uint16;
+  * motion: rigid 2-D Gaussian random walk clamped to +-clamp px, optional
+    3-px jumps; frame t shows Scene(x - s_t), so the planted shift s_t is
+    what registration against the template Scene(x) should return.
+The scene is evaluated analytically at the shifted coordinates, so subpixel
+shifts carry no interpolation bias.  Everything runs through torch on either
+device; a torch.Generator seeded from the config makes it reproducible.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import torch
+
+
+@dataclasses.dataclass
+class VideoConfig:
+    H: int = 128
+    W: int = 128
+    n_frames: int = 1000
+    fps: float = 741.0
+    n_neurons: int = 8
+    r_lo: float = 4.0
+    r_hi: float = 8.0
+    overlap_max: float = 0.30
+    bg_amp: float = 2000.0
+    rate_lo: float = 10.0  # spikes/s
+    rate_hi: float = 10.0
+    dff_lo: float = 0.05
+    dff_hi: float = 0.05
+    decay: float = 3.0  # frames
+    read_sigma: float = 20.0
+    walk_sigma: float = 0.3  # px/frame
+    clamp: float = 8.0
+    jump_frac: float = 0.0
+    jump_px: float = 3.0
+    template_frames: int = 200
+    seed: int = 1001
+
+
+def tiny_config(**kw) -> VideoConfig:
+    """128x128, 1,000 frames, 8 neurons (r 4-8 px, <=30 % overlap), background
+    2,000 counts, 10 Hz spikes of 5 % dF/F, read noise 20, walk 0.3 px clamped
+    at +-8 px."""
+    return dataclasses.replace(VideoConfig(), **kw)
+
+
+def paper_scale_config(**kw) -> VideoConfig:
+    """512x512, 10,000 frames, 40 neurons (r 5-10 px, <=40 % overlap),
+    background 4,000 counts, 5-20 Hz spikes of 2-8 % dF/F, read noise 30, walk
+    0.5 px clamped at +-12 px, 1 % of frames with 3-px jumps."""
+    base = VideoConfig(H=512, W=512, n_frames=10000, n_neurons=40, r_lo=5.0, r_hi=10.0,
+                       overlap_max=0.40, bg_amp=4000.0, rate_lo=5.0, rate_hi=20.0, dff_lo=0.02,
+                       dff_hi=0.08, read_sigma=30.0, walk_sigma=0.5, clamp=12.0, jump_frac=0.01,
+                       seed=1002)
+    return dataclasses.replace(base, **kw)
+
+
+def scaled_config(H: int, W: int, n_frames: int, seed: int, **kw) -> VideoConfig:
+    """Paper-scale content at another size, neuron count scaled to area."""
+    n = max(1, round(40 * H * W / (512 * 512)))
+    return paper_scale_config(H=H, W=W, n_frames=n_frames, n_neurons=n, seed=seed, **kw)
+
+
+@dataclasses.dataclass
+class Scene:
+    cfg: VideoConfig
+    bg: list  # per Gaussian: (weight, cy, cx, sy, sx)
+    neurons: list  # per neuron: (cy, cx, a, b, theta, f0)
+    rates: list
+    dffs: list
+
+
+def make_scene(cfg: VideoConfig, gen: torch.Generator) -> Scene:
+    def u(lo=0.0, hi=1.0):
+        return lo + (hi - lo) * torch.rand((), generator=gen).item()
+
+    H, W = cfg.H, cfg.W
+    bg = []
+    for wgt in (1.0, 0.6):
+        bg.append((wgt, u(0.2, 0.8) * H, u(0.2, 0.8) * W, u(0.25, 0.5) * H, u(0.25, 0.5) * W))
+    neurons, tries = [], 0
+    while len(neurons) < cfg.n_neurons and tries < 20000:
+        tries += 1
+        r = u(cfg.r_lo, cfg.r_hi)
+        a, b = r * u(0.85, 1.15), r * u(0.85, 1.15)
+        m = max(a, b) + 2
+        cy, cx = u(m, H - m), u(m, W - m)
+        ok = True
+        for (py, px, pa, pb, _, _) in neurons:
+            ov = _disc_overlap(math.sqrt(a * b), math.sqrt(pa * pb), math.hypot(cy - py, cx - px))
+            if ov > cfg.overlap_max:
+                ok = False
+                break
+        if ok:
+            neurons.append((cy, cx, a, b, u(0, math.pi), 0.25 * cfg.bg_amp))
+    rates = [u(cfg.rate_lo, cfg.rate_hi) for _ in neurons]
+    dffs = [u(cfg.dff_lo, cfg.dff_hi) for _ in neurons]
+    return Scene(cfg, bg, neurons, rates, dffs)
+
+
+def _disc_overlap(r1: float, r2: float, d: float) -> float:
+    """Intersection area of two discs over the smaller disc's area."""
+    if d >= r1 + r2:
+        return 0.0
+    if d <= abs(r1 - r2):
+        return 1.0
+    a1 = r1 * r1 * math.acos((d * d + r1 * r1 - r2 * r2) / (2 * d * r1))
+    a2 = r2 * r2 * math.acos((d * d + r2 * r2 - r1 * r1) / (2 * d * r2))
+    a3 = 0.5 * math.sqrt(max(0.0, (-d + r1 + r2) * (d + r1 - r2) * (d - r1 + r2) * (d + r1 + r2)))
+    return (a1 + a2 - a3) / (math.pi * min(r1, r2) ** 2)
+
+
+def planted_shifts(cfg: VideoConfig, n: int, gen: torch.Generator) -> torch.Tensor:
+    """Rigid drift (dy, dx) per frame, float64 [n, 2]."""
+    steps = torch.randn((n, 2), generator=gen, dtype=torch.float64) * cfg.walk_sigma
+    if cfg.jump_frac > 0:
+        jumps = torch.rand((n,), generator=gen, dtype=torch.float64) < cfg.jump_frac
+        ang = torch.rand((n,), generator=gen, dtype=torch.float64) * 2 * math.pi
+        steps[:, 0] += jumps * cfg.jump_px * torch.sin(ang)
+        steps[:, 1] += jumps * cfg.jump_px * torch.cos(ang)
+    s = torch.zeros((n, 2), dtype=torch.float64)
+    cur = torch.zeros(2, dtype=torch.float64)
+    for t in range(n):
+        if t > 0:
+            cur = torch.clamp(cur + steps[t], -cfg.clamp, cfg.clamp)
+        s[t] = cur
+    return s
+
+
+def activity(scene: Scene, n: int, gen: torch.Generator) -> torch.Tensor:
+    """dF/F per neuron and frame, float32 [n, n_neurons]."""
+    cfg = scene.cfg
+    k = len(scene.neurons)
+    if k == 0:
+        return torch.zeros((n, 0))
+    rate = torch.tensor(scene.rates, dtype=torch.float32) / cfg.fps
+    spikes = torch.poisson(rate.expand(n, k).contiguous(), generator=gen)
+    act = torch.zeros((n, k))
+    cur = torch.zeros(k)
+    dec = math.exp(-1.0 / cfg.decay)
+    for t in range(n):
+        cur = cur * dec + spikes[t]
+        act[t] = cur
+    return act * torch.tensor(scene.dffs, dtype=torch.float32)
+
+
+def render(scene: Scene, shifts: torch.Tensor, act: torch.Tensor, device) -> torch.Tensor:
+    """Expected counts float32 [n, H, W] of frames showing Scene(x - s_t)."""
+    cfg = scene.cfg
+    H, W = cfg.H, cfg.W
+    n = shifts.shape[0]
+    sy = shifts[:, 0].to(device=device, dtype=torch.float32).view(n, 1, 1)
+    sx = shifts[:, 1].to(device=device, dtype=torch.float32).view(n, 1, 1)
+    ys = torch.arange(H, device=device, dtype=torch.float32).view(1, H, 1)
+    xs = torch.arange(W, device=device, dtype=torch.float32).view(1, 1, W)
+    out = torch.full((n, H, W), 0.3 * cfg.bg_amp, device=device)
+    for (wgt, cy, cx, gy, gx) in scene.bg:
+        ey = torch.exp(-0.5 * ((ys - sy - cy) / gy) ** 2)
+        ex = torch.exp(-0.5 * ((xs - sx - cx) / gx) ** 2)
+        out += (0.7 * cfg.bg_amp * wgt) * ey * ex
+    act = act.to(device)
+    margin = int(math.ceil(max(cfg.clamp + 4 * cfg.jump_px * (cfg.jump_frac > 0), 1))) + 4
+    for j, (cy, cx, a, b, th, f0) in enumerate(scene.neurons):
+        half = int(math.ceil(max(a, b))) + margin
+        y0, y1 = max(0, int(cy) - half), min(H, int(cy) + half + 1)
+        x0, x1 = max(0, int(cx) - half), min(W, int(cx) + half + 1)
+        yy = ys[:, y0:y1, :] - sy - cy
+        xx = xs[:, :, x0:x1] - sx - cx
+        c, s = math.cos(th), math.sin(th)
+        u = (c * xx + s * yy) / a
+        v = (-s * xx + c * yy) / b
+        rho = torch.sqrt(u * u + v * v)
+        fp = torch.sigmoid((1.0 - rho) * math.sqrt(a * b))  # ~1-px logistic edge
+        out[:, y0:y1, x0:x1] += (f0 * (1.0 + act[:, j])).view(n, 1, 1) * fp
+    return out
+
+
+def add_noise(expected: torch.Tensor, read_sigma: float, gen: torch.Generator) -> torch.Tensor:
+    shot = torch.poisson(expected.clamp_min(0), generator=gen)
+    read = torch.randn(expected.shape, generator=gen, device=expected.device) * read_sigma
+    return torch.clamp(torch.round(shot + read), 0, 65535).to(torch.int32).to(torch.uint16)
+
+
+def make_video(cfg: VideoConfig, n_frames: int | None = None, device="cpu", chunk: int = 256,
+               out: torch.Tensor | None = None):
+    """Returns (frames uint16 [n,H,W], planted shifts float64 [n,2] (CPU),
+    template float32 [H,W]) on `device`.  `out` may be a preallocated frames
+    tensor (e.g. pinned host memory)."""
+    n = cfg.n_frames if n_frames is None else n_frames
+    device = torch.device(device)
+    g_cpu = torch.Generator().manual_seed(cfg.seed)
+    scene = make_scene(cfg, g_cpu)
+    shifts = planted_shifts(cfg, n, g_cpu)
+    act = activity(scene, n, g_cpu)
+    g_dev = torch.Generator(device=device).manual_seed(cfg.seed + 7919)
+    frames = out if out is not None else torch.empty((n, cfg.H, cfg.W), dtype=torch.uint16,
+                                                     device=device)
+    for t0 in range(0, n, chunk):
+        t1 = min(n, t0 + chunk)
+        exp_ = render(scene, shifts[t0:t1], act[t0:t1], device)
+        frames[t0:t1].copy_(add_noise(exp_, cfg.read_sigma, g_dev))
+    # Template: mean of template_frames noisy frames at zero shift.
+    nt = cfg.template_frames
+    act_t = activity(scene, nt, g_cpu)
+    acc = torch.zeros((cfg.H, cfg.W), dtype=torch.float64, device=device)
+    for t0 in range(0, nt, chunk):
+        t1 = min(nt, t0 + chunk)
+        exp_ = render(scene, torch.zeros((t1 - t0, 2), dtype=torch.float64), act_t[t0:t1], device)
+        acc += add_noise(exp_, cfg.read_sigma, g_dev).to(torch.float64).sum(0)
+    template = (acc / nt).to(torch.float32)
+    return frames, shifts, template
