@@ -1,0 +1,161 @@
+/*
+ * vimg.h -- C ABI of the GB300-native frame-stream hot path for real-time
+ * voltage imaging (Bando et al., "Real-time Neuron Segmentation for Voltage
+ * Imaging", BIBM 2023).
+ *
+ * What one call computes, per uint16 frame F_t of an H x W video:
+ *   1. Rigid motion estimate by zero-mean normalized cross-correlation (ZNCC)
+ *      of 21x21 template patches tiled over the image, for every candidate
+ *      displacement d in a (2R+1)^2 window, the patch values aggregated into
+ *      one surface C_t(d) whose maximum is the frame's motion vector
+ *      (Sec. II, "Motion correction").  The patch grid is the non-overlapping
+ *      grid centred in the region where all shifted windows stay in bounds;
+ *      C_t is the mean of the patch ZNCCs; ties go to the smallest |d|, then
+ *      smallest dy, then dx; a 3-point parabola per axis refines the peak.
+ *   2. Resampling: V_t(y,x) = F_t(y + s_y, x + s_x), bilinear, coordinates
+ *      clamped to the image (the corrected video of Sec. II).
+ *   3. Optional temporal high-pass of each pixel trace (trailing boxcar of
+ *      hp_window frames, v[t<0] := v[0]).
+ *   4. Time segments of L frames at absolute frame indices (Sec. III-B) and
+ *      per segment the spatial summary S_i = temporal mean of V (Eq. 1) and
+ *      the temporal summary T_i = max - median of the Gaussian-smoothed video
+ *      (sigma 3 px, radius ceil(4 sigma), mirror border; Eq. 2).  The median
+ *      of an even count is the mean of the two middle values.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are caller-owned CUDA global-memory pointers on the
+ *     handle's device; host pointers are ordinary (preferably pinned) host
+ *     memory.  The library owns only its handle workspace.
+ *   - All device work is enqueued on params.stream (0 = legacy default
+ *     stream); the call returns without waiting for it, except the _host
+ *     entry point, which synchronises before returning.  Outputs are valid
+ *     once the caller has synchronised that stream.
+ *   - Layouts are dense row-major: frames [n][H][W] uint16, shifts [n][2]
+ *     float32 (dy, dx), corrected [n][H][W] float32, summaries [k][2][H][W]
+ *     float32 with S_i before T_i.
+ *   - Return value >= 0 is success (for process calls: k, the number of
+ *     segments completed and written by this call).  Negative values are the
+ *     VIMG_ERR_* codes; vimg_last_error() then describes the failure.  A
+ *     device-side failure makes the handle's error sticky: every later call
+ *     on that handle returns the same code.
+ *   - A handle is not thread safe; use one handle per host thread.
+ */
+#ifndef VIMG_H
+#define VIMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIMG_OK 0
+#define VIMG_ERR_ARG (-1)         /* invalid argument or NULL pointer            */
+#define VIMG_ERR_NO_TEMPLATE (-2) /* vimg_set_template has not been called       */
+#define VIMG_ERR_CUDA (-3)        /* a CUDA runtime call failed                  */
+#define VIMG_ERR_TIMEOUT (-4)     /* a device-side wait gave up (sticky)         */
+#define VIMG_ERR_OOM (-5)         /* device or host allocation failed            */
+#define VIMG_ERR_SIZE (-6)        /* H or W below 2R + patch, or above limits    */
+
+/* params.flags */
+#define VIMG_CORR_BF16 1      /* BF16 tensor-core correlation numerators         */
+#define VIMG_PROPOSAL_CNN 2   /* learned shift proposal + narrow window          */
+#define VIMG_OUT_HIGHPASS 4   /* corrected output holds the high-passed video    */
+
+typedef struct vimg_handle vimg_handle;
+
+typedef struct {
+  int search_radius;        /* R: displacements in [-R, R]^2; 0..16; default 16  */
+  int patch;                /* patch side; the paper's 21 (Sec. II); 21 only     */
+  int segment_len;          /* L; the paper's 50 (Sec. III-B); 1..64             */
+  float gauss_sigma;        /* Eq. 2 smoothing sigma; the paper's 3.0; radius
+                               ceil(4 sigma) must be <= 12                       */
+  int hp_window;            /* boxcar high-pass length; 0 = off; <= 64           */
+  int flags;                /* VIMG_* flags above                                */
+  float fallback_zncc;      /* learned proposal: full search if C(d*) < this     */
+  int narrow_radius;        /* learned proposal: window half-width (default 2)   */
+  void* stream;             /* cudaStream_t for all work; NULL = default stream  */
+  long long timeout_spins;  /* cap on any device-side wait loop                  */
+  int max_chunk;            /* frames per internal batch (workspace sizing)      */
+} vimg_params;
+
+/* Fills *p with the defaults above (R = 16, patch 21, L = 50, sigma 3,
+ * high-pass off, no flags, fallback 0.5, narrow radius 2, default stream,
+ * max_chunk 256). */
+void vimg_default_params(vimg_params* p);
+
+/* Creates a handle for H x W frames on the current CUDA device and allocates
+ * its workspace.  Returns NULL on invalid parameters (see vimg_last_error(NULL)),
+ * on VIMG_ERR_SIZE conditions, or when allocation fails. */
+vimg_handle* vimg_create(int H, int W, const vimg_params* p);
+
+/* Releases the handle and its workspace after draining its stream.  NULL is
+ * accepted. */
+void vimg_destroy(vimg_handle* h);
+
+/* Sets the reference template T (device float32 [H][W]).  Per patch the
+ * centred template T - mean(T_p) and its squared norm are precomputed on the
+ * device (the constant parts of the ZNCC of Sec. II).  The template is copied;
+ * the caller may reuse its buffer once the stream has passed this call.
+ * Resets nothing else. */
+int vimg_set_template(vimg_handle* h, const float* d_template);
+
+/* Processes the next n >= 0 frames of the stream (device uint16 [n][H][W]).
+ *   d_shifts_out    device float32 [n][2], the estimated (dy, dx) per frame;
+ *                   may be NULL.
+ *   d_corrected_out device float32 [n][H][W]: V_t, or the high-passed V_t when
+ *                   VIMG_OUT_HIGHPASS is set; may be NULL.
+ *   d_summary_out   device float32 [k][2][H][W] for the k segments completed
+ *                   by this call, k = floor((frames_seen % L + n) / L); may be
+ *                   NULL.
+ * Frames of an unfinished segment (and the frames the high-pass still needs)
+ * are kept in the handle, so any split of a stream into calls gives identical
+ * results.  Returns k >= 0 or a VIMG_ERR_* code. */
+int vimg_process(vimg_handle* h, const uint16_t* d_frames, int n, float* d_shifts_out,
+                 float* d_corrected_out, float* d_summary_out);
+
+/* Optional extra outputs and inputs of one process call.  Any member may be
+ * NULL. */
+typedef struct {
+  float* shifts;          /* [n][2] estimated (dy, dx)                          */
+  float* corrected;       /* [n][H][W]                                          */
+  float* summary;         /* [k][2][H][W]                                       */
+  float* peak_info;       /* [n][4]: dy*, dx*, C(d*), second-largest C          */
+  double* surface;        /* [n][2R+1][2R+1] aggregated surface C_t (full window
+                             only; for diagnostics and parity checks)           */
+  const float* shifts_in; /* [n][2]: apply these shifts instead of estimating
+                             them (the temporal stage alone)                    */
+} vimg_io;
+
+/* Same as vimg_process with the vimg_io members.  Returns k or an error. */
+int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io);
+
+/* End-to-end variant with HOST buffers: h_frames host uint16 [n][H][W] is
+ * streamed to the device in batches of max_chunk frames (copies overlap the
+ * compute of the previous batch), and the shifts (host float32 [n][2]) and
+ * the summaries (host float32 [k][2][H][W]) are copied back.  Either output
+ * may be NULL.  d_corrected_out is an optional DEVICE buffer [n][H][W].
+ * Synchronises before returning.  Returns k or an error. */
+int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n, float* h_shifts_out,
+                      float* h_summary_out, float* d_corrected_out);
+
+/* Frames seen by the handle so far (host-side counter; no device sync). */
+long long vimg_frames_seen(const vimg_handle* h);
+
+/* Forgets the stream state (frames seen, open segment, high-pass history);
+ * keeps the template. */
+int vimg_reset(vimg_handle* h);
+
+/* Message for the last failure on h, or for the last failed vimg_create on
+ * this host thread when h is NULL.  Never NULL. */
+const char* vimg_last_error(const vimg_handle* h);
+
+/* Library version string. */
+const char* vimg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIMG_H */

@@ -1,0 +1,410 @@
+// C ABI of libvimg (include/vimg.h): handle, argument checks, device workspace,
+// stream state carried across calls, and the order of kernel launches per call.
+//
+// Per internal batch of at most max_chunk frames (batches end on segment
+// boundaries whenever possible, so the batch's raw frames are still in L2 when
+// the temporal pass reads them again):
+//   1. motion estimate in sub-batches of kMotionBatch frames:
+//      zero the fixed-point surfaces, window statistics, correlation numerators
+//      (FP32 CUDA cores, or BF16 tensor cores), integer peak + parabola;
+//   2. one fused temporal launch over every segment slot the batch touches;
+//   3. the raw frames and shifts still needed later (the open segment and the
+//      high-pass history) are copied into the handle's carry buffer.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "vimg_internal.h"
+
+using namespace vimg;
+
+namespace {
+constexpr int kMotionBatch = 16;
+thread_local std::string g_create_error;
+}  // namespace
+
+struct vimg_handle {
+  int H = 0, W = 0;
+  vimg_params p{};
+  PatchGrid g{};
+  int np = 0, w = 0, nwin = 0;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  TemplateDev td{};
+  bool have_template = false;
+  float gw[2 * kGaussMaxRadius + 1] = {};
+  float* inv = nullptr;                 // [kMotionBatch][np][w][kInvStride]
+  unsigned long long* csum = nullptr;   // [max_chunk][nwin]
+  float* shift_tmp = nullptr;           // [max_chunk][2]
+  uint16_t* carry[2] = {nullptr, nullptr};
+  float* carry_shift[2] = {nullptr, nullptr};
+  int carry_cap = 0, carry_n = 0, carry_cur = 0;
+  long long frames_seen = 0;
+  // host-buffer path
+  uint16_t* stage[2] = {nullptr, nullptr};
+  float* stage_shift = nullptr;   // [max_chunk][2]
+  float* stage_summary = nullptr; // [max segments per batch][2][H][W]
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};
+  int sticky = 0;
+  std::string err;
+};
+
+static int fail(vimg_handle* h, int code, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (code == VIMG_ERR_CUDA || code == VIMG_ERR_TIMEOUT) h->sticky = code;
+  } else {
+    g_create_error = msg;
+  }
+  return code;
+}
+
+static int cuda_fail(vimg_handle* h, cudaError_t e, const char* what) {
+  return fail(h, VIMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                               \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+extern "C" void vimg_default_params(vimg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->search_radius = 16;
+  p->patch = kPatch;
+  p->segment_len = 50;
+  p->gauss_sigma = 3.0f;
+  p->hp_window = 0;
+  p->flags = 0;
+  p->fallback_zncc = 0.5f;
+  p->narrow_radius = 2;
+  p->stream = nullptr;
+  p->timeout_spins = 1LL << 26;
+  p->max_chunk = 200;
+}
+
+extern "C" const char* vimg_version(void) { return "vimg 0.1 (sm_103a)"; }
+
+static bool grid_for(int H, int W, int R, PatchGrid* g) {
+  if (H - 2 * R < kPatch || W - 2 * R < kPatch) return false;
+  g->ny = (H - 2 * R) / kPatch;
+  g->nx = (W - 2 * R) / kPatch;
+  g->y0 = R + ((H - 2 * R) - g->ny * kPatch) / 2;
+  g->x0 = R + ((W - 2 * R) - g->nx * kPatch) / 2;
+  return true;
+}
+
+static void free_all(vimg_handle* h) {
+  void* ptrs[] = {h->td.tc, h->td.tn2, h->td.coff, h->inv, h->csum, h->shift_tmp,
+                  h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
+                  h->stage[0], h->stage[1], h->stage_shift, h->stage_summary};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+    if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
+  }
+  if (h->copy_st) cudaStreamDestroy(h->copy_st);
+}
+
+extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
+  vimg_params p;
+  if (pin)
+    p = *pin;
+  else
+    vimg_default_params(&p);
+  if (H <= 0 || W <= 0 || H > 8192 || W > 8192) {
+    fail(nullptr, VIMG_ERR_SIZE, "H and W must be in 1..8192");
+    return nullptr;
+  }
+  if (p.search_radius < 0 || p.search_radius > kMaxR) {
+    fail(nullptr, VIMG_ERR_ARG, "search_radius must be in 0..16");
+    return nullptr;
+  }
+  if (p.patch != kPatch) {
+    fail(nullptr, VIMG_ERR_ARG, "patch must be 21");
+    return nullptr;
+  }
+  if (p.segment_len < 1 || p.segment_len > kMaxL) {
+    fail(nullptr, VIMG_ERR_ARG, "segment_len must be in 1..50");
+    return nullptr;
+  }
+  if (!(p.gauss_sigma > 0.f) || (int)std::ceil(4.0 * p.gauss_sigma) > kGaussMaxRadius) {
+    fail(nullptr, VIMG_ERR_ARG, "gauss_sigma must be in (0, 3] (radius ceil(4 sigma) <= 12)");
+    return nullptr;
+  }
+  if (p.hp_window < 0 || p.hp_window > kMaxHp) {
+    fail(nullptr, VIMG_ERR_ARG, "hp_window must be in 0..64");
+    return nullptr;
+  }
+  if (p.max_chunk < 1 || p.max_chunk > 4096) {
+    fail(nullptr, VIMG_ERR_ARG, "max_chunk must be in 1..4096");
+    return nullptr;
+  }
+  if (p.flags & ~(VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_OUT_HIGHPASS)) {
+    fail(nullptr, VIMG_ERR_ARG, "unknown flag bits");
+    return nullptr;
+  }
+  if (p.flags & (VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN)) {
+    fail(nullptr, VIMG_ERR_ARG, "VIMG_CORR_BF16 / VIMG_PROPOSAL_CNN are not available in this build");
+    return nullptr;
+  }
+  PatchGrid g;
+  if (!grid_for(H, W, p.search_radius, &g) || H <= kGaussMaxRadius || W <= kGaussMaxRadius) {
+    fail(nullptr, VIMG_ERR_SIZE, "H and W must be at least 2*search_radius + 21");
+    return nullptr;
+  }
+  vimg_handle* h = new vimg_handle();
+  h->H = H, h->W = W, h->p = p, h->g = g;
+  h->np = g.ny * g.nx;
+  h->w = 2 * p.search_radius + 1;
+  h->nwin = h->w * h->w;
+  h->st = (cudaStream_t)p.stream;
+  // Gaussian taps (Eq. 2): exp(-k^2 / (2 sigma^2)) normalised, zero beyond ceil(4 sigma).
+  {
+    const int r = (int)std::ceil(4.0 * p.gauss_sigma);
+    double wsum = 0.0, wd[2 * kGaussMaxRadius + 1] = {};
+    for (int k = -r; k <= r; ++k)
+      wsum += (wd[k + kGaussMaxRadius] = std::exp(-(double)k * k / (2.0 * p.gauss_sigma * p.gauss_sigma)));
+    for (int k = 0; k < 2 * kGaussMaxRadius + 1; ++k) h->gw[k] = (float)(wd[k] / wsum);
+  }
+  const size_t HW = (size_t)H * W;
+  h->carry_cap = std::max(p.segment_len - 1, p.hp_window > 0 ? p.hp_window - 1 : 0);
+  cudaError_t e = cudaGetDevice(&h->dev);
+#define ALLOC(ptr, bytes)                                                   \
+  if (e == cudaSuccess && (bytes) > 0) e = cudaMalloc((void**)&(ptr), (bytes));
+  ALLOC(h->td.tc, sizeof(float) * h->np * kPatch * kTplStride);
+  ALLOC(h->td.tn2, sizeof(float) * h->np);
+  ALLOC(h->td.coff, sizeof(int) * h->np);
+  ALLOC(h->inv, sizeof(float) * (size_t)kMotionBatch * h->np * h->w * kInvStride);
+  ALLOC(h->csum, sizeof(unsigned long long) * (size_t)p.max_chunk * h->nwin);
+  ALLOC(h->shift_tmp, sizeof(float) * 2 * (size_t)p.max_chunk);
+  for (int i = 0; i < 2; ++i) {
+    ALLOC(h->carry[i], sizeof(uint16_t) * HW * std::max(1, h->carry_cap));
+    ALLOC(h->carry_shift[i], sizeof(float) * 2 * std::max(1, h->carry_cap));
+  }
+#undef ALLOC
+  if (e != cudaSuccess) {
+    fail(nullptr, e == cudaErrorMemoryAllocation ? VIMG_ERR_OOM : VIMG_ERR_CUDA,
+         std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+    free_all(h);
+    delete h;
+    return nullptr;
+  }
+  return h;
+}
+
+extern "C" void vimg_destroy(vimg_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  if (h->copy_st) cudaStreamSynchronize(h->copy_st);
+  free_all(h);
+  delete h;
+}
+
+extern "C" const char* vimg_last_error(const vimg_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+extern "C" long long vimg_frames_seen(const vimg_handle* h) { return h ? h->frames_seen : -1; }
+
+extern "C" int vimg_reset(vimg_handle* h) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  h->frames_seen = 0;
+  h->carry_n = 0;
+  return VIMG_OK;
+}
+
+extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
+  if (!h || !d_template) return fail(h, VIMG_ERR_ARG, "null handle or template");
+  if (h->sticky) return h->sticky;
+  CK(launch_template_prep(d_template, h->H, h->W, h->g, h->td, h->st), "template prep launch");
+  h->have_template = true;
+  return VIMG_OK;
+}
+
+// Motion estimate of nf frames (nf <= max_chunk) into shifts[nf][2].
+static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shifts,
+                    float* peak_info, double* surface) {
+  const size_t HW = (size_t)h->H * h->W;
+  const int R = h->p.search_radius;
+  CK(cudaMemsetAsync(h->csum, 0, sizeof(unsigned long long) * (size_t)nf * h->nwin, h->st),
+     "surface reset");
+  for (int f0 = 0; f0 < nf; f0 += kMotionBatch) {
+    const int m = std::min(kMotionBatch, nf - f0);
+    CK(launch_stats(frames + HW * f0, m, h->H, h->W, h->g, R, h->td, h->inv, h->st),
+       "window statistics launch");
+    CK(launch_corr_f32(frames + HW * f0, m, h->H, h->W, h->g, R, h->td, h->inv,
+                       h->csum + (size_t)f0 * h->nwin, h->st),
+       "correlation launch");
+  }
+  CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, surface, h->st), "peak launch");
+  return VIMG_OK;
+}
+
+// One internal batch: n <= max_chunk frames.
+static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vimg_io& io,
+                         int k_before) {
+  const size_t HW = (size_t)h->H * h->W;
+  const int L = h->p.segment_len;
+  const float* shifts;
+  if (io.shifts_in) {
+    shifts = io.shifts_in;
+  } else {
+    float* out = io.shifts ? io.shifts : h->shift_tmp;
+    int rc = estimate(h, frames, n, out, io.peak_info, io.surface);
+    if (rc) return rc;
+    shifts = out;
+  }
+  const long long seen = h->frames_seen;
+  const int c = (int)(seen % L);
+  TemporalArgs a{};
+  a.src.carry = h->carry[h->carry_cur];
+  a.src.carry_shift = h->carry_shift[h->carry_cur];
+  a.src.batch = frames;
+  a.src.batch_shift = shifts;
+  a.src.n_carry = h->carry_n;
+  a.src.n_batch = n;
+  a.src.t_first = seen - h->carry_n;
+  a.src.t_new = seen;
+  a.H = h->H, a.W = h->W, a.L = L, a.hp_w = h->p.hp_window, a.gauss_r = kGaussMaxRadius;
+  std::memcpy(a.gw, h->gw, sizeof(a.gw));
+  a.seg_base = seen - c;
+  a.n_seg = (c + n + L - 1) / L;
+  a.out_hp = (h->p.flags & VIMG_OUT_HIGHPASS) ? 1 : 0;
+  a.corrected = io.corrected;
+  a.summary = io.summary ? io.summary + (size_t)k_before * 2 * HW : nullptr;
+  if (io.corrected || io.summary) CK(launch_temporal(a, h->st), "temporal launch");
+  const int k = (c + n) / L;
+  // New carry: the last K' frames of (carry ++ batch).
+  const long long seen2 = seen + n;
+  const int c2 = (int)(seen2 % L);
+  const int hp_need = h->p.hp_window > 0 ? h->p.hp_window - 1 : 0;
+  int K = std::max(c2, hp_need);
+  if (K > seen2) K = (int)seen2;
+  const int nv = h->carry_n + n, nxt = 1 - h->carry_cur;
+  int dst = 0;
+  for (int v = nv - K; v < nv;) {
+    const bool in_carry = v < h->carry_n;
+    const int run = in_carry ? std::min(h->carry_n - v, nv - v) : nv - v;
+    const uint16_t* sf = in_carry ? h->carry[h->carry_cur] + HW * v : frames + HW * (v - h->carry_n);
+    const float* ss = in_carry ? h->carry_shift[h->carry_cur] + 2 * v : shifts + 2 * (v - h->carry_n);
+    CK(cudaMemcpyAsync(h->carry[nxt] + HW * dst, sf, sizeof(uint16_t) * HW * run,
+                       cudaMemcpyDeviceToDevice, h->st),
+       "carry copy");
+    CK(cudaMemcpyAsync(h->carry_shift[nxt] + 2 * dst, ss, sizeof(float) * 2 * run,
+                       cudaMemcpyDeviceToDevice, h->st),
+       "carry shift copy");
+    dst += run;
+    v += run;
+  }
+  h->carry_cur = nxt;
+  h->carry_n = K;
+  h->frames_seen = seen2;
+  return k;
+}
+
+extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  if (n < 0 || (n > 0 && !d_frames) || !io) return fail(h, VIMG_ERR_ARG, "bad frames or io");
+  if (!io->shifts_in && !h->have_template)
+    return fail(h, VIMG_ERR_NO_TEMPLATE, "vimg_set_template must come before vimg_process");
+  const size_t HW = (size_t)h->H * h->W;
+  const int L = h->p.segment_len, maxc = h->p.max_chunk;
+  int done = 0, k_total = 0;
+  while (done < n) {
+    int m = std::min(n - done, maxc);
+    if (m < n - done) {
+      const int cut = (int)((h->frames_seen + m) % L);
+      if (m - cut > 0) m -= cut;  // end the batch on a segment boundary
+    }
+    vimg_io sub = *io;
+    if (io->shifts) sub.shifts = io->shifts + 2 * (size_t)done;
+    if (io->shifts_in) sub.shifts_in = io->shifts_in + 2 * (size_t)done;
+    if (io->corrected) sub.corrected = io->corrected + HW * done;
+    if (io->peak_info) sub.peak_info = io->peak_info + 4 * (size_t)done;
+    if (io->surface) sub.surface = io->surface + (size_t)h->nwin * done;
+    int k = process_batch(h, d_frames + HW * done, m, sub, k_total);
+    if (k < 0) return k;
+    k_total += k;
+    done += m;
+  }
+  return k_total;
+}
+
+extern "C" int vimg_process(vimg_handle* h, const uint16_t* d_frames, int n, float* d_shifts_out,
+                            float* d_corrected_out, float* d_summary_out) {
+  vimg_io io{};
+  io.shifts = d_shifts_out;
+  io.corrected = d_corrected_out;
+  io.summary = d_summary_out;
+  return vimg_process_io(h, d_frames, n, &io);
+}
+
+extern "C" int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n,
+                                 float* h_shifts_out, float* h_summary_out,
+                                 float* d_corrected_out) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  if (n < 0 || (n > 0 && !h_frames)) return fail(h, VIMG_ERR_ARG, "bad frames");
+  if (!h->have_template) return fail(h, VIMG_ERR_NO_TEMPLATE, "no template");
+  const size_t HW = (size_t)h->H * h->W;
+  const int L = h->p.segment_len, maxc = h->p.max_chunk;
+  const int max_seg = (L - 1 + maxc) / L;
+  if (!h->stage[0]) {
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaMalloc((void**)&h->stage[i], sizeof(uint16_t) * HW * maxc), "stage alloc");
+      CK(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming), "event");
+      CK(cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming), "event");
+      CK(cudaEventRecord(h->ev_used[i], h->st), "event record");
+    }
+    CK(cudaMalloc((void**)&h->stage_shift, sizeof(float) * 2 * maxc), "stage alloc");
+    CK(cudaMalloc((void**)&h->stage_summary, sizeof(float) * 2 * HW * std::max(1, max_seg)),
+       "stage alloc");
+    CK(cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking), "copy stream");
+  }
+  int done = 0, k_total = 0, buf = 0;
+  while (done < n) {
+    int m = std::min(n - done, maxc);
+    if (m < n - done) {
+      const int cut = (int)((h->frames_seen + m) % L);
+      if (m - cut > 0) m -= cut;
+    }
+    // H2D into stage[buf] once the batch that last used it has finished.
+    CK(cudaStreamWaitEvent(h->copy_st, h->ev_used[buf], 0), "wait");
+    CK(cudaMemcpyAsync(h->stage[buf], h_frames + HW * done, sizeof(uint16_t) * HW * m,
+                       cudaMemcpyHostToDevice, h->copy_st),
+       "frames upload");
+    CK(cudaEventRecord(h->ev_copied[buf], h->copy_st), "event record");
+    CK(cudaStreamWaitEvent(h->st, h->ev_copied[buf], 0), "wait");
+    vimg_io io{};
+    io.shifts = h->stage_shift;
+    io.corrected = d_corrected_out ? d_corrected_out + HW * done : nullptr;
+    io.summary = h_summary_out ? h->stage_summary : nullptr;
+    int k = vimg_process_io(h, h->stage[buf], m, &io);
+    if (k < 0) return k;
+    CK(cudaEventRecord(h->ev_used[buf], h->st), "event record");
+    if (h_shifts_out)
+      CK(cudaMemcpyAsync(h_shifts_out + 2 * (size_t)done, h->stage_shift, sizeof(float) * 2 * m,
+                         cudaMemcpyDeviceToHost, h->st),
+         "shifts download");
+    if (h_summary_out && k > 0)
+      CK(cudaMemcpyAsync(h_summary_out + 2 * HW * (size_t)k_total, h->stage_summary,
+                         sizeof(float) * 2 * HW * k, cudaMemcpyDeviceToHost, h->st),
+         "summary download");
+    k_total += k;
+    done += m;
+    buf ^= 1;
+  }
+  CK(cudaStreamSynchronize(h->st), "stream sync");
+  return k_total;
+}

@@ -1,0 +1,314 @@
+// Fused temporal pass for sm_103a: resampling of each frame at its shift, the
+// corrected (or high-passed) output, the Gaussian pre-smoothing of Eq. 2 and the
+// per-segment summaries of Sec. III-B (Bando et al., BIBM 2023):
+//   S_i(x) = (1/L) sum_t V_i(x,t)                              (Eq. 1)
+//   T_i(x) = max_t Vbar_i(x,t) - median_t Vbar_i(x,t)           (Eq. 2)
+// with V_t(y,x) = F_t(y + s_y, x + s_x) (bilinear, clamped coordinates) and
+// Vbar the Gaussian-smoothed V (radius ceil(4 sigma), mirror border).
+//
+// One CTA owns a 32x32 output tile for one segment slot and walks the slot's
+// frames in order.  Per frame it resamples the tile plus a 12-pixel halo into
+// shared memory (the halo pixels are mirrored at the image border, exactly as
+// the Gaussian's boundary rule asks), writes the tile's corrected pixels, runs
+// the row and column passes of the separable Gaussian in shared memory, and
+// updates per-pixel running sum and max in registers and the smoothed history
+// of the segment in shared memory (50 x 1024 floats).  At the end of a complete
+// segment every pixel's median comes from two 25-element sorting networks and a
+// merge-path selection of the 25th and 26th smallest values.
+//
+// The high-pass y[t] = v[t] - (1/W) sum_{k<W} v[t-k] (v[t<0] := v[0]) keeps an
+// exact running sum in 2^-16 fixed point (64-bit integers); values leaving the
+// window are recomputed from their frames rather than stored.
+#include <cfloat>
+
+#include "vimg_internal.h"
+
+namespace vimg {
+
+constexpr int kTempThreads = 512;
+constexpr int kExt = kTile + 2 * kGaussMaxRadius;  // 56
+constexpr int kTaps = 2 * kGaussMaxRadius + 1;     // 25
+constexpr float kHpScale = 65536.0f;
+
+// ---- sorting networks (Batcher's odd-even merge sort, generated at compile time)
+struct CmpPair {
+  unsigned char a, b;
+};
+
+template <int N, int NREAL>
+struct OddEvenMergeNet {
+  CmpPair pairs[N * 16];
+  int n;
+  constexpr OddEvenMergeNet() : pairs(), n(0) {
+    for (int p = 1; p < N; p <<= 1)
+      for (int k = p; k >= 1; k >>= 1)
+        for (int j = k % p; j + k < N; j += 2 * k)
+          for (int i = 0; i < k && i + j + k < N; ++i)
+            if ((i + j) / (2 * p) == (i + j + k) / (2 * p) && i + j + k < NREAL) {
+              pairs[n].a = (unsigned char)(i + j);
+              pairs[n].b = (unsigned char)(i + j + k);
+              ++n;
+            }
+  }
+};
+
+template <int N, int NREAL>
+__device__ __forceinline__ void sort_net(float* v) {
+  constexpr OddEvenMergeNet<N, NREAL> net{};
+  constexpr int nc = net.n;
+#pragma unroll
+  for (int c = 0; c < nc; ++c) {
+    const float x = v[net.pairs[c].a], y = v[net.pairs[c].b];
+    v[net.pairs[c].a] = fminf(x, y);
+    v[net.pairs[c].b] = fmaxf(x, y);
+  }
+}
+
+// Median of 50 values: sort both halves, then the k-th smallest of two sorted
+// runs A, B is min_i max(A[i-1], B[k-1-i]).
+__device__ __forceinline__ float median50(const float* __restrict__ h, int stride) {
+  float a[32], b[32];
+#pragma unroll
+  for (int i = 0; i < 25; ++i) {
+    a[i] = h[i * stride];
+    b[i] = h[(25 + i) * stride];
+  }
+  sort_net<32, 25>(a);
+  sort_net<32, 25>(b);
+  float m25 = fminf(a[24], b[24]);
+#pragma unroll
+  for (int i = 1; i <= 24; ++i) m25 = fminf(m25, fmaxf(a[i - 1], b[24 - i]));
+  float m26 = FLT_MAX;
+#pragma unroll
+  for (int i = 1; i <= 25; ++i) m26 = fminf(m26, fmaxf(a[i - 1], b[25 - i]));
+  return 0.5f * (m25 + m26);
+}
+
+// Median of n <= 50 values (any n): pad to 64 with +inf, sort, pick.
+__device__ __forceinline__ float median_any(const float* __restrict__ h, int stride, int n) {
+  float v[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = i < n ? h[i * stride] : FLT_MAX;
+  sort_net<64, 64>(v);
+  float lo = 0.f, hi = 0.f;
+  const int il = (n - 1) / 2, ih = n / 2;
+#pragma unroll
+  for (int i = 0; i < 64; ++i) {
+    if (i == il) lo = v[i];
+    if (i == ih) hi = v[i];
+  }
+  return 0.5f * (lo + hi);
+}
+
+// ---- resampling ----------------------------------------------------------------
+struct Split {
+  int i;
+  float f;
+};
+
+__device__ __forceinline__ Split split_shift(float s) {
+  const float fl = floorf(s);
+  return {(int)fl, s - fl};
+}
+
+__device__ __forceinline__ int mirror_idx(int i, int n) {
+  return i < 0 ? -i - 1 : (i >= n ? 2 * n - i - 1 : i);
+}
+
+// V(y, x) = F(y + s_y, x + s_x), bilinear, coordinates clamped to the image.
+// s = i + f with 0 <= f < 1 keeps every weight exact.
+__device__ __forceinline__ float bilin(const uint16_t* __restrict__ F, int H, int W, int y, int x,
+                                       Split sy, Split sx) {
+  int r0, r1, c0, c1;
+  float wy, wx;
+  const int yi = y + sy.i, xi = x + sx.i;
+  if (yi < 0) {
+    r0 = r1 = 0;
+    wy = 0.f;
+  } else if (yi >= H - 1) {
+    r0 = r1 = H - 1;
+    wy = 0.f;
+  } else {
+    r0 = yi;
+    r1 = yi + 1;
+    wy = sy.f;
+  }
+  if (xi < 0) {
+    c0 = c1 = 0;
+    wx = 0.f;
+  } else if (xi >= W - 1) {
+    c0 = c1 = W - 1;
+    wx = 0.f;
+  } else {
+    c0 = xi;
+    c1 = xi + 1;
+    wx = sx.f;
+  }
+  const float a = __ldg(F + (size_t)r0 * W + c0), b = __ldg(F + (size_t)r0 * W + c1);
+  const float c = __ldg(F + (size_t)r1 * W + c0), d = __ldg(F + (size_t)r1 * W + c1);
+  const float top = fmaf(wx, b - a, a), bot = fmaf(wx, d - c, c);
+  return fmaf(wy, bot - top, top);
+}
+
+__device__ __forceinline__ void frame_at(const FrameSource& s, long long t, const uint16_t*& F,
+                                         Split& sy, Split& sx, int HW) {
+  long long v = t - s.t_first;
+  if (v < 0) v = 0;  // the host keeps every frame a launch can ask for; never read before it
+  if (v >= (long long)s.n_carry + s.n_batch) v = (long long)s.n_carry + s.n_batch - 1;
+  const float* sh;
+  if (v < s.n_carry) {
+    F = s.carry + (size_t)v * HW;
+    sh = s.carry_shift + 2 * v;
+  } else {
+    F = s.batch + (size_t)(v - s.n_carry) * HW;
+    sh = s.batch_shift + 2 * (v - s.n_carry);
+  }
+  sy = split_shift(sh[0]);
+  sx = split_shift(sh[1]);
+}
+
+__device__ __forceinline__ long long hp_q(float v) { return __float2ll_rn(v * kHpScale); }
+
+// ---- the fused kernel ------------------------------------------------------------
+__global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  float* vext = sm;                  // [56][56] resampled tile + halo
+  float* hbuf = vext + kExt * kExt;  // [56][32] row-smoothed
+  float* hist = hbuf + kExt * kTile; // [L][1024] smoothed history
+  const int H = a.H, W = a.W, L = a.L, HW = H * W;
+  const int ntx = (W + kTile - 1) / kTile;
+  const int ty0 = (blockIdx.x / ntx) * kTile, tx0 = (blockIdx.x % ntx) * kTile;
+  const int tid = threadIdx.x, lx = tid & 31, ly0 = (tid >> 5) * 2;
+  const int x = tx0 + lx, ya = ty0 + ly0, yb = ya + 1;
+  const bool va = ya < H && x < W, vb = yb < H && x < W;
+  const FrameSource& src = a.src;
+  const long long t_end = src.t_first + src.n_carry + src.n_batch;
+  const long long s0 = a.seg_base + (long long)blockIdx.y * L;
+  const long long s1 = s0 + L < t_end ? s0 + L : t_end;
+  const bool complete = s0 + L <= t_end;
+
+  float w[kTaps];
+#pragma unroll
+  for (int i = 0; i < kTaps; ++i) w[i] = a.gw[i];
+
+  float sum_a = 0.f, sum_b = 0.f, mx_a = -FLT_MAX, mx_b = -FLT_MAX;
+  long long hs_a = 0, hs_b = 0;
+  bool hp_init = false;
+  const bool do_hp = a.out_hp && a.hp_w > 0 && a.corrected;
+  const float hp_inv = 1.0f / ((float)a.hp_w * kHpScale);
+
+  for (long long t = s0; t < s1; ++t) {
+    const uint16_t* F;
+    Split sy, sx;
+    frame_at(src, t, F, sy, sx, HW);
+    for (int i = tid; i < kExt * kExt; i += kTempThreads) {
+      const int ry = i / kExt, rx = i - ry * kExt;
+      const int yy = mirror_idx(ty0 - kGaussMaxRadius + ry, H);
+      const int xx = mirror_idx(tx0 - kGaussMaxRadius + rx, W);
+      vext[i] = bilin(F, H, W, yy, xx, sy, sx);
+    }
+    __syncthreads();
+    const float v_a = vext[(ly0 + kGaussMaxRadius) * kExt + lx + kGaussMaxRadius];
+    const float v_b = vext[(ly0 + 1 + kGaussMaxRadius) * kExt + lx + kGaussMaxRadius];
+    if (t >= src.t_new && a.corrected) {
+      float* out = a.corrected + (size_t)(t - src.t_new) * HW;
+      float o_a = v_a, o_b = v_b;
+      if (do_hp) {
+        if (!hp_init) {
+          // running sum of v[t-1] .. v[t-W+1] (v[t<0] := v[0])
+          for (int k = 1; k < a.hp_w; ++k) {
+            const long long u = t - k < 0 ? 0 : t - k;
+            const uint16_t* Fu;
+            Split uy, ux;
+            frame_at(src, u, Fu, uy, ux, HW);
+            if (va) hs_a += hp_q(bilin(Fu, H, W, ya, x, uy, ux));
+            if (vb) hs_b += hp_q(bilin(Fu, H, W, yb, x, uy, ux));
+          }
+          hp_init = true;
+        }
+        const long long qa = hp_q(v_a), qb = hp_q(v_b);
+        hs_a += qa;
+        hs_b += qb;
+        o_a = (float)(qa * a.hp_w - hs_a) * hp_inv;
+        o_b = (float)(qb * a.hp_w - hs_b) * hp_inv;
+        // drop v[t-W+1] for the next frame
+        const long long u0 = t - a.hp_w + 1, u = u0 < 0 ? 0 : u0;
+        const uint16_t* Fu;
+        Split uy, ux;
+        frame_at(src, u, Fu, uy, ux, HW);
+        if (va) hs_a -= hp_q(bilin(Fu, H, W, ya, x, uy, ux));
+        if (vb) hs_b -= hp_q(bilin(Fu, H, W, yb, x, uy, ux));
+      }
+      if (va) out[(size_t)ya * W + x] = o_a;
+      if (vb) out[(size_t)yb * W + x] = o_b;
+    }
+    // row pass: 56 rows x 8 groups of 4 output columns
+    if (tid < kExt * 8) {
+      const int r = tid >> 3, cg = tid & 7;
+      const float* in = vext + r * kExt + cg * 4;
+      float v[kTaps + 3];
+#pragma unroll
+      for (int i = 0; i < kTaps + 3; i += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(in + i);
+        v[i] = q.x, v[i + 1] = q.y, v[i + 2] = q.z, v[i + 3] = q.w;
+      }
+      float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < kTaps; ++m)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = fmaf(w[m], v[j + m], o[j]);
+      *reinterpret_cast<float4*>(hbuf + r * kTile + cg * 4) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    __syncthreads();
+    // column pass: two output rows per thread
+    float col[kTaps + 1];
+#pragma unroll
+    for (int k = 0; k < kTaps + 1; ++k) col[k] = hbuf[(ly0 + k) * kTile + lx];
+    float b_a = 0.f, b_b = 0.f;
+#pragma unroll
+    for (int m = 0; m < kTaps; ++m) {
+      b_a = fmaf(w[m], col[m], b_a);
+      b_b = fmaf(w[m], col[m + 1], b_b);
+    }
+    sum_a += v_a;
+    sum_b += v_b;
+    mx_a = fmaxf(mx_a, b_a);
+    mx_b = fmaxf(mx_b, b_b);
+    float* hrow = hist + (size_t)(t - s0) * (kTile * kTile) + ly0 * kTile + lx;
+    hrow[0] = b_a;
+    hrow[kTile] = b_b;
+  }
+  if (!complete || !a.summary) return;
+  float* S = a.summary + (size_t)blockIdx.y * 2 * HW;
+  float* T = S + HW;
+  const float invL = 1.0f / (float)L;
+  for (int q = 0; q < 2; ++q) {
+    const bool ok = q == 0 ? va : vb;
+    if (!ok) continue;
+    const int y = q == 0 ? ya : yb;
+    const float* h = hist + (ly0 + q) * kTile + lx;
+    const float med = L == 50 ? median50(h, kTile * kTile) : median_any(h, kTile * kTile, L);
+    S[(size_t)y * W + x] = (q == 0 ? sum_a : sum_b) * invL;
+    T[(size_t)y * W + x] = (q == 0 ? mx_a : mx_b) - med;
+  }
+}
+
+static size_t temporal_smem(int L) {
+  return sizeof(float) * ((size_t)kExt * kExt + (size_t)kExt * kTile + (size_t)L * kTile * kTile);
+}
+
+cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st) {
+  if (a.n_seg <= 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)temporal_smem(kMaxL));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int tiles = ((a.H + kTile - 1) / kTile) * ((a.W + kTile - 1) / kTile);
+  k_temporal<<<dim3(tiles, a.n_seg), kTempThreads, temporal_smem(a.L), st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace vimg

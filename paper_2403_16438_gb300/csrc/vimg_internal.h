@@ -1,0 +1,71 @@
+// Internal definitions shared by the CUDA translation units of libvimg.
+// Not part of the public ABI (include/vimg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vimg.h"
+
+namespace vimg {
+
+constexpr int kPatch = 21;               // patch side (Sec. II)
+constexpr int kPatchArea = kPatch * kPatch;
+constexpr int kMaxR = 16;                // largest search radius
+constexpr int kMaxWin = 2 * kMaxR + 1;   // 33 displacements per axis
+constexpr int kInvStride = 36;           // padded row of per-window factors
+constexpr int kTplStride = 24;           // padded template-patch row (floats)
+constexpr int kGaussMaxRadius = 12;      // ceil(4 * 3)
+constexpr int kTile = 32;                // temporal-kernel output tile side
+constexpr int kMaxL = 50;                // longest segment the temporal kernel holds
+constexpr int kMaxHp = 64;               // longest high-pass window
+constexpr double kFix = 1099511627776.0; // 2^40: fixed-point scale of C sums
+
+struct PatchGrid {
+  int ny, nx, y0, x0;
+};
+
+// Per-handle template constants on the device.
+struct TemplateDev {
+  float* tc;   // [np][21][kTplStride] centred template patches
+  float* tn2;  // [np] squared norms of the centred patches
+  int* coff;   // [np] integer offsets ~ patch means (exactness of F - c in fp32)
+};
+
+// Where the frames of one temporal-kernel launch come from.  Virtual frame v
+// (0 <= v < n_virtual) is absolute frame t_first + v; v < n_carry lives in the
+// carry buffer, the rest in the caller's batch.
+struct FrameSource {
+  const uint16_t* carry;     // [n_carry][H][W]
+  const float* carry_shift;  // [n_carry][2]
+  const uint16_t* batch;     // [n_batch][H][W]
+  const float* batch_shift;  // [n_batch][2]
+  int n_carry, n_batch;
+  long long t_first;         // absolute index of virtual frame 0
+  long long t_new;           // absolute index of the first frame new to this call
+};
+
+struct TemporalArgs {
+  FrameSource src;
+  int H, W, L, hp_w, gauss_r;
+  float gw[2 * kGaussMaxRadius + 1];  // normalised Gaussian taps
+  long long seg_base;                 // absolute start of segment slot 0
+  int n_seg;                          // segment slots in this launch
+  int out_hp;                         // corrected output holds the high-pass
+  float* corrected;                   // [n_batch][H][W] or null
+  float* summary;                     // [k][2][H][W] or null (slot j -> index j)
+};
+
+// ---- launchers (each enqueues on `st`; returns cudaGetLastError()) ----------
+cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, TemplateDev td,
+                                 cudaStream_t st);
+cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                         const TemplateDev& td, float* inv, cudaStream_t st);
+cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                            const TemplateDev& td, const float* inv,
+                            unsigned long long* csum, cudaStream_t st);
+cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, float* shifts,
+                        float* peak_info, double* surface, cudaStream_t st);
+cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st);
+
+}  // namespace vimg

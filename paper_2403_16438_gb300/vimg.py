@@ -1,0 +1,179 @@
+"""Thin ctypes binding of libvimg (include/vimg.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  torch supplies device memory and the stream.  There is no CPU
+fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libvimg.so")
+
+OK = 0
+ERR_ARG, ERR_NO_TEMPLATE, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_SIZE = -1, -2, -3, -4, -5, -6
+CORR_BF16, PROPOSAL_CNN, OUT_HIGHPASS = 1, 2, 4
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("search_radius", ctypes.c_int),
+        ("patch", ctypes.c_int),
+        ("segment_len", ctypes.c_int),
+        ("gauss_sigma", ctypes.c_float),
+        ("hp_window", ctypes.c_int),
+        ("flags", ctypes.c_int),
+        ("fallback_zncc", ctypes.c_float),
+        ("narrow_radius", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("timeout_spins", ctypes.c_longlong),
+        ("max_chunk", ctypes.c_int),
+    ]
+
+
+class IO(ctypes.Structure):
+    _fields_ = [
+        ("shifts", ctypes.c_void_p),
+        ("corrected", ctypes.c_void_p),
+        ("summary", ctypes.c_void_p),
+        ("peak_info", ctypes.c_void_p),
+        ("surface", ctypes.c_void_p),
+        ("shifts_in", ctypes.c_void_p),
+    ]
+
+
+# Every symbol include/vimg.h declares (checked by the host-only tests).
+EXPORTS = [
+    "vimg_default_params", "vimg_create", "vimg_destroy", "vimg_set_template", "vimg_process",
+    "vimg_process_io", "vimg_process_host", "vimg_frames_seen", "vimg_reset", "vimg_last_error",
+    "vimg_version",
+]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvimg.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i, vp = ctypes.POINTER, ctypes.c_int, ctypes.c_void_p
+    L.vimg_default_params.argtypes = [P(Params)]
+    L.vimg_default_params.restype = None
+    L.vimg_create.argtypes = [i, i, P(Params)]
+    L.vimg_create.restype = vp
+    L.vimg_destroy.argtypes = [vp]
+    L.vimg_destroy.restype = None
+    L.vimg_set_template.argtypes = [vp, vp]
+    L.vimg_set_template.restype = i
+    L.vimg_process.argtypes = [vp, vp, i, vp, vp, vp]
+    L.vimg_process.restype = i
+    L.vimg_process_io.argtypes = [vp, vp, i, P(IO)]
+    L.vimg_process_io.restype = i
+    L.vimg_process_host.argtypes = [vp, vp, i, vp, vp, vp]
+    L.vimg_process_host.restype = i
+    L.vimg_frames_seen.argtypes = [vp]
+    L.vimg_frames_seen.restype = ctypes.c_longlong
+    L.vimg_reset.argtypes = [vp]
+    L.vimg_reset.restype = i
+    L.vimg_last_error.argtypes = [vp]
+    L.vimg_last_error.restype = ctypes.c_char_p
+    L.vimg_version.argtypes = []
+    L.vimg_version.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+class VimgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"vimg error {code}: {msg}")
+        self.code = code
+
+
+def default_params() -> Params:
+    p = Params()
+    lib.vimg_default_params(ctypes.byref(p))
+    return p
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """One stream of frames of one H x W video (see vimg_create)."""
+
+    def __init__(self, H, W, stream=None, **kw):
+        p = default_params()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        p.stream = ctypes.c_void_p(stream.cuda_stream)
+        self.params = p
+        self.H, self.W = H, W
+        self._h = lib.vimg_create(H, W, ctypes.byref(p))
+        if not self._h:
+            raise VimgError(ERR_ARG, lib.vimg_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.vimg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc < 0:
+            raise VimgError(rc, lib.vimg_last_error(self._h).decode())
+        return rc
+
+    @property
+    def frames_seen(self) -> int:
+        return lib.vimg_frames_seen(self._h)
+
+    def segments_for(self, n: int) -> int:
+        L = self.params.segment_len
+        return (self.frames_seen % L + n) // L
+
+    def set_template(self, template: torch.Tensor):
+        assert template.is_cuda and template.dtype == torch.float32
+        assert template.shape == (self.H, self.W) and template.is_contiguous()
+        self._template = template
+        self._check(lib.vimg_set_template(self._h, _ptr(template)))
+
+    def reset(self):
+        self._check(lib.vimg_reset(self._h))
+
+    def process(self, frames, shifts=None, corrected=None, summary=None, peak_info=None,
+                surface=None, shifts_in=None) -> int:
+        """frames: cuda uint16 [n,H,W].  Outputs are optional preallocated cuda
+        tensors (see vimg_io).  Returns k, the segments written."""
+        assert frames.is_cuda and frames.dtype == torch.uint16 and frames.is_contiguous()
+        n = frames.shape[0]
+        io = IO(_ptr(shifts), _ptr(corrected), _ptr(summary), _ptr(peak_info), _ptr(surface),
+                _ptr(shifts_in))
+        return self._check(lib.vimg_process_io(self._h, _ptr(frames), n, ctypes.byref(io)))
+
+    def process_host(self, frames_host, shifts_host=None, summary_host=None,
+                     corrected=None) -> int:
+        """frames_host: CPU uint16 [n,H,W] (pinned for overlap)."""
+        assert not frames_host.is_cuda and frames_host.is_contiguous()
+        n = frames_host.shape[0]
+        return self._check(lib.vimg_process_host(self._h, _ptr(frames_host), n,
+                                                 _ptr(shifts_host), _ptr(summary_host),
+                                                 _ptr(corrected)))
+
+
+def version() -> str:
+    return lib.vimg_version().decode()

@@ -1,0 +1,69 @@
+"""Host-only checks of the C ABI: the library loads without a GPU, exports
+every function include/vimg.h declares, and rejects bad arguments before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def vimg():
+    from paper_2403_16438_gb300 import build
+    build.build()
+    from paper_2403_16438_gb300 import vimg as v
+    return v
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "vimg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vimg_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(vimg):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(vimg.lib, n), n
+    assert sorted(vimg.EXPORTS) == names
+
+
+def test_struct_layouts_match_header(vimg):
+    # vimg_params: 8 ints/floats, a pointer, a long long, an int (+ padding)
+    assert ctypes.sizeof(vimg.Params) == 56
+    assert ctypes.sizeof(vimg.IO) == 6 * 8
+
+
+def test_defaults(vimg):
+    p = vimg.default_params()
+    assert (p.search_radius, p.patch, p.segment_len, p.gauss_sigma) == (16, 21, 50, 3.0)
+    assert p.hp_window == 0 and p.flags == 0 and abs(p.fallback_zncc - 0.5) < 1e-7
+    assert p.narrow_radius == 2 and p.max_chunk > 0
+
+
+@pytest.mark.parametrize("field,value,H,W", [
+    ("search_radius", 17, 512, 512), ("search_radius", -1, 512, 512), ("patch", 15, 512, 512),
+    ("segment_len", 0, 512, 512), ("segment_len", 51, 512, 512), ("gauss_sigma", 3.5, 512, 512),
+    ("gauss_sigma", 0.0, 512, 512), ("hp_window", 65, 512, 512), ("max_chunk", 0, 512, 512),
+    ("flags", 64, 512, 512), ("search_radius", 16, 52, 512), ("search_radius", 16, 0, 512),
+])
+def test_create_rejects_bad_parameters(vimg, field, value, H, W):
+    p = vimg.default_params()
+    setattr(p, field, value)
+    h = vimg.lib.vimg_create(H, W, ctypes.byref(p))
+    assert not h
+    assert len(vimg.lib.vimg_last_error(None)) > 0
+
+
+def test_null_handle_calls(vimg):
+    L = vimg.lib
+    L.vimg_destroy(None)
+    assert L.vimg_process(None, None, 0, None, None, None) == vimg.ERR_ARG
+    assert L.vimg_set_template(None, None) == vimg.ERR_ARG
+    assert L.vimg_reset(None) == vimg.ERR_ARG
+    assert L.vimg_frames_seen(None) == -1
+    assert b"sm_103a" in L.vimg_version()
