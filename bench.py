@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Frame-stream benchmark: rigid ZNCC motion correction fused with the segment
+summaries, on a synthetic 512x512 uint16 voltage-imaging video of 10,000
+frames (the paper-scale workload; content model in paper_2403_16438_gb300.synth).
+
+One step = the whole video through vimg_process (full-window FP32 ZNCC over
++-16 px, 484 patches, resampling, L = 50 summaries), stream state reset between
+steps so every step does identical work.  The video (5.2 GB) is resident in HBM
+and larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vimg|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s (×realtime) and HBM fraction, 1 GB300, ≤0.05 px shift err"
+UNIT = "frames/s"
+RECORD_FPS = 741.0  # Fig. 1 video: 10,000 frames recorded in 13.5 s
+H = W = 512
+R = 16
+P = 21
+L = 50
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": SM_MAX_MHZ_NOMINAL}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_max_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x max SM clock
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def corr_flops_per_frame():
+    ny = nx = (H - 2 * R) // P
+    return 2.0 * ny * nx * P * P * (2 * R + 1) ** 2
+
+
+def temporal_bytes_per_frame():
+    # read u16 frame, write f32 corrected frame, write S and T once per L frames
+    return H * W * (2 + 4 + 8.0 / L)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    smax.append(float(c[2]))
+                    power.append(float(c[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_traffic(kernel, source):
+    """dram bytes per launch from the committed ncu summary, or None when the
+    kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    with open(os.path.join(ROOT, "paper_2403_16438_gb300", "csrc", source), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if d.get("source_sha") != sha:
+        return None
+    return d
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_fps(frames_cpu, template, budget_s=15.0, max_frames=64):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the workload's frames through the whole pipeline."""
+    import oracle
+    import numpy as np
+    o = oracle.Oracle(H, W, R=R)
+    o.set_template(template.double().numpy())
+    t0 = time.perf_counter()
+    o.process(frames_cpu[:1].numpy(), want_summary=False)
+    t1 = time.perf_counter() - t0
+    n = int(max(2, min(max_frames, budget_s / max(t1, 1e-3))))
+    n = min(n, frames_cpu.shape[0])
+    o2 = oracle.Oracle(H, W, R=R)
+    o2.set_template(template.double().numpy())
+    t0 = time.perf_counter()
+    o2.process(np.ascontiguousarray(frames_cpu[:n].numpy()))
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    from paper_2403_16438_gb300 import synth
+    cfg = synth.paper_scale_config()
+    frames, _, T = synth.make_video(cfg, 128)
+    import oracle
+    o = oracle.Oracle(H, W, R=R)
+    o.set_template(T.double().numpy())
+    t0 = time.perf_counter()
+    o.process(frames[:1].numpy(), want_summary=False)
+    t1 = time.perf_counter() - t0
+    # each step: a bounded sample sized so warmup + steps end within ~3 minutes
+    per_step = int(max(1, min(64, 150.0 / max(1, args.steps + args.warmup) / max(t1, 1e-3))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        o = oracle.Oracle(H, W, R=R)
+        o.set_template(T.double().numpy())
+        t0 = time.perf_counter()
+        o.process(frames[:per_step].numpy())
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * len(times) / total
+    sample = (f"{per_step} frames of the 512x512 paper-scale video per step "
+              f"(full pipeline, FP64 direct sums)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "512x512 uint16 video, full-window ZNCC +-16 px, L=50 summaries",
+                   "frames_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_vimg(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2403_16438_gb300 import synth, vimg
+
+    n = args.frames
+    cfg = synth.paper_scale_config(seed=1002 + rank)
+    frames, planted, T = synth.make_video(cfg, n, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk)
+    h.set_template(T)
+    shifts = torch.empty((n, 2), device=dev)
+    corrected = torch.empty((n, H, W), device=dev)
+    k_max = n // L
+    summary = torch.empty((max(1, k_max), 2, H, W), device=dev)
+
+    def step():
+        h.reset()
+        k = h.process(frames, shifts=shifts, corrected=corrected, summary=summary)
+        assert k == k_max
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # shift error against the planted drift (content model; parity is in the tests)
+    err_planted = (shifts.double().cpu() - planted).abs()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    h.profile(True)
+    h.profile_read(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = h.profile_read(reset=True)
+    h.profile(False)
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    total_frames = n * args.steps * ws
+    value = total_frames / (ms / 1000.0)
+
+    pk, pk_kind = peaks()
+    smax = pk.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL)
+    corr_ms, corr_launches = prof["corr"]
+    corr_flops = corr_flops_per_frame() * n * args.steps
+    achieved = corr_flops / (corr_ms / 1000.0) / 1e12 if corr_ms > 0 else None
+    alu_peak = fp32_alu_peak_tflops(smax)
+    tr = kernel_traffic("k_corr_f32", "motion.cu")
+    roofline = {
+        "kernel": "k_corr_f32", "bound": "alu", "achieved": achieved,
+        "peak": alu_peak, "unit": "TFLOP/s",
+        "frac": achieved / alu_peak if achieved else None,
+        "traffic": tr["dram_bytes_per_launch"] if tr else None,
+        "per_launch_frames": round(n * args.steps / max(1, corr_launches), 3),
+        "avg_launch_ms": corr_ms / max(1, corr_launches),
+        "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {smax:.0f} MHz",
+    }
+    temp_ms, temp_launches = prof["temporal"]
+    temp_gbs = temporal_bytes_per_frame() * n * args.steps / (temp_ms / 1000.0) / 1e9 \
+        if temp_ms > 0 else None
+    kernel_launches = sum(prof[s][1] for s in ("stats", "corr", "peak", "temporal", "proposal"))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": "paper-scale synthetic video: 512x512 uint16, 10,000 frames per step, "
+                        "full-window FP32 ZNCC +-16 px (484 patches x 1089 shifts), bilinear "
+                        "resampling, L=50 mean and max-median summaries",
+            "frames_per_step": n, "H": H, "W": W, "search_radius": R, "segment_len": L,
+            "l2": "no flush: each step reads 5.2 GB of frames, larger than L2",
+            "parallelism": f"replicas{ws}" if ws > 1 else "single",
+            "x_realtime_741fps": value / RECORD_FPS / ws,
+        },
+        "x_realtime": value / RECORD_FPS / ws,
+        "hbm_fraction": {"kernel": "k_temporal (fused resample+summaries)",
+                         "achieved_gbs": temp_gbs, "peak_gbs": pk["hbm_gbs"],
+                         "frac": temp_gbs / pk["hbm_gbs"] if temp_gbs else None,
+                         "peak_kind": pk_kind},
+        "roofline": roofline,
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "stage_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "gpu_launches": kernel_launches,
+        "clocks": clk,
+        "shift_err_vs_planted_px": {"mean": float(err_planted.mean()),
+                                    "p99": float(err_planted.flatten().quantile(0.99)),
+                                    "max": float(err_planted.max())},
+        "paper_context": {"mc_stage_fps_2080ti_450x138": 10000 / 5.5,
+                          "source": "Fig. 1: MC 5.5 s for 10,000 frames on 1 RTX 2080 Ti"},
+    }
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        ke = max(1, min(args.steps, args.e2e_steps))
+        fh = torch.empty((n, H, W), dtype=torch.uint16, pin_memory=True)
+        fh.copy_(frames.cpu())
+        sh_h = torch.empty((n, 2), pin_memory=True)
+        sm_h = torch.empty((max(1, k_max), 2, H, W), pin_memory=True)
+        h.reset()
+        h.process_host(fh, shifts_host=sh_h, summary_host=sm_h, corrected=corrected)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            h.reset()
+            h.process_host(fh, shifts_host=sh_h, summary_host=sm_h, corrected=corrected)
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = t.item()
+        line["e2e"] = {"value": n * ke * ws / te, "unit": UNIT,
+                       "h2d_bytes_per_step": n * H * W * 2,
+                       "d2h_bytes_per_step": n * 2 * 4 + k_max * 2 * H * W * 4,
+                       "steps": ke,
+                       "note": "vimg_process_host: pinned host frames in, shifts and summaries "
+                               "out; corrected frames stay in device memory"}
+        del fh
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        fps, nf, dt, cores = cpu_oracle_fps(frames[:64].cpu(), T.cpu(), budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{nf} frames of the same video, full pipeline, "
+                                          f"{dt:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["vimg", "reference"], default="vimg")
+    ap.add_argument("--frames", type=int, default=10000)
+    ap.add_argument("--chunk", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_vimg(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,19 @@ int vimg_reset(vimg_handle* h);
  * this host thread when h is NULL.  Never NULL. */
 const char* vimg_last_error(const vimg_handle* h);
 
+/* Per-stage timing with CUDA events recorded around each of the library's
+ * launches on params.stream (off by default).  Stages:
+ *   0 window statistics, 1 correlation numerators, 2 peak + refinement,
+ *   3 fused temporal pass, 4 learned proposal, 5 carry copies (not a kernel).
+ * vimg_profile_read synchronises the stream, writes the summed milliseconds
+ * and the launch counts of each stage into ms[VIMG_NSTAGES] and
+ * launches[VIMG_NSTAGES] (either may be NULL), and clears them when reset != 0.
+ * At most 65,536 launches are recorded between reads; later ones are counted
+ * but not timed.  Returns VIMG_OK or an error. */
+#define VIMG_NSTAGES 6
+int vimg_profile_enable(vimg_handle* h, int on);
+int vimg_profile_read(vimg_handle* h, double* ms, long long* launches, int reset);
+
 /* Library version string. */
 const char* vimg_version(void);
 

@@ -22,7 +22,18 @@ using namespace vimg;
 
 namespace {
 constexpr int kMotionBatch = 16;
+constexpr int kProfSlots = 65536;
 thread_local std::string g_create_error;
+
+// Event pairs around launches, summed per stage when read.
+struct Prof {
+  bool on = false;
+  cudaEvent_t* ev = nullptr;  // [kProfSlots][2]
+  int* stage = nullptr;       // [kProfSlots]
+  int used = 0;
+  double ms[VIMG_NSTAGES] = {};
+  long long launches[VIMG_NSTAGES] = {};
+};
 }  // namespace
 
 struct vimg_handle {
@@ -35,7 +46,7 @@ struct vimg_handle {
   TemplateDev td{};
   bool have_template = false;
   float gw[2 * kGaussMaxRadius + 1] = {};
-  float* inv = nullptr;                 // [kMotionBatch][np][w][kInvStride]
+  float* inv = nullptr;                 // [kMotionBatch][stats map] 1/sqrt(SF) per window
   unsigned long long* csum = nullptr;   // [max_chunk][nwin]
   float* shift_tmp = nullptr;           // [max_chunk][2]
   uint16_t* carry[2] = {nullptr, nullptr};
@@ -49,9 +60,26 @@ struct vimg_handle {
   cudaStream_t copy_st = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_used[2] = {nullptr, nullptr};
+  Prof prof;
   int sticky = 0;
   std::string err;
 };
+
+// Records the start of a stage's launch; returns the slot or -1.
+static int prof_begin(vimg_handle* h, int stage) {
+  Prof& p = h->prof;
+  if (!p.on) return -1;
+  p.launches[stage]++;
+  if (p.used >= kProfSlots) return -1;
+  const int s = p.used++;
+  p.stage[s] = stage;
+  cudaEventRecord(p.ev[2 * s], h->st);
+  return s;
+}
+
+static void prof_end(vimg_handle* h, int slot) {
+  if (slot >= 0) cudaEventRecord(h->prof.ev[2 * slot + 1], h->st);
+}
 
 static int fail(vimg_handle* h, int code, const std::string& msg) {
   if (h) {
@@ -111,6 +139,12 @@ static void free_all(vimg_handle* h) {
     if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
   }
   if (h->copy_st) cudaStreamDestroy(h->copy_st);
+  if (h->prof.ev) {
+    for (int i = 0; i < 2 * kProfSlots; ++i)
+      if (h->prof.ev[i]) cudaEventDestroy(h->prof.ev[i]);
+    delete[] h->prof.ev;
+    delete[] h->prof.stage;
+  }
 }
 
 extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
@@ -182,7 +216,7 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
   ALLOC(h->td.tc, sizeof(float) * h->np * kPatch * kTplStride);
   ALLOC(h->td.tn2, sizeof(float) * h->np);
   ALLOC(h->td.coff, sizeof(int) * h->np);
-  ALLOC(h->inv, sizeof(float) * (size_t)kMotionBatch * h->np * h->w * kInvStride);
+  ALLOC(h->inv, sizeof(float) * (size_t)kMotionBatch * stats_map_floats(g, p.search_radius));
   ALLOC(h->csum, sizeof(unsigned long long) * (size_t)p.max_chunk * h->nwin);
   ALLOC(h->shift_tmp, sizeof(float) * 2 * (size_t)p.max_chunk);
   for (int i = 0; i < 2; ++i) {
@@ -240,13 +274,19 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
      "surface reset");
   for (int f0 = 0; f0 < nf; f0 += kMotionBatch) {
     const int m = std::min(kMotionBatch, nf - f0);
+    int ps = prof_begin(h, 0);
     CK(launch_stats(frames + HW * f0, m, h->H, h->W, h->g, R, h->td, h->inv, h->st),
        "window statistics launch");
+    prof_end(h, ps);
+    ps = prof_begin(h, 1);
     CK(launch_corr_f32(frames + HW * f0, m, h->H, h->W, h->g, R, h->td, h->inv,
                        h->csum + (size_t)f0 * h->nwin, h->st),
        "correlation launch");
+    prof_end(h, ps);
   }
+  int ps = prof_begin(h, 2);
   CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, surface, h->st), "peak launch");
+  prof_end(h, ps);
   return VIMG_OK;
 }
 
@@ -282,7 +322,11 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
   a.out_hp = (h->p.flags & VIMG_OUT_HIGHPASS) ? 1 : 0;
   a.corrected = io.corrected;
   a.summary = io.summary ? io.summary + (size_t)k_before * 2 * HW : nullptr;
-  if (io.corrected || io.summary) CK(launch_temporal(a, h->st), "temporal launch");
+  if (io.corrected || io.summary) {
+    const int ps = prof_begin(h, 3);
+    CK(launch_temporal(a, h->st), "temporal launch");
+    prof_end(h, ps);
+  }
   const int k = (c + n) / L;
   // New carry: the last K' frames of (carry ++ batch).
   const long long seen2 = seen + n;
@@ -292,6 +336,7 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
   if (K > seen2) K = (int)seen2;
   const int nv = h->carry_n + n, nxt = 1 - h->carry_cur;
   int dst = 0;
+  const int pcs = K > 0 ? prof_begin(h, 5) : -1;
   for (int v = nv - K; v < nv;) {
     const bool in_carry = v < h->carry_n;
     const int run = in_carry ? std::min(h->carry_n - v, nv - v) : nv - v;
@@ -306,6 +351,7 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
     dst += run;
     v += run;
   }
+  prof_end(h, pcs);
   h->carry_cur = nxt;
   h->carry_n = K;
   h->frames_seen = seen2;
@@ -407,4 +453,38 @@ extern "C" int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n
   }
   CK(cudaStreamSynchronize(h->st), "stream sync");
   return k_total;
+}
+
+extern "C" int vimg_profile_enable(vimg_handle* h, int on) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  Prof& p = h->prof;
+  if (on && !p.ev) {
+    p.ev = new cudaEvent_t[2 * kProfSlots]();
+    p.stage = new int[kProfSlots]();
+    for (int i = 0; i < 2 * kProfSlots; ++i) CK(cudaEventCreate(&p.ev[i]), "event create");
+  }
+  p.on = on != 0;
+  return VIMG_OK;
+}
+
+extern "C" int vimg_profile_read(vimg_handle* h, double* ms, long long* launches, int reset) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  Prof& p = h->prof;
+  if (p.used > 0) {
+    CK(cudaStreamSynchronize(h->st), "stream sync");
+    for (int s = 0; s < p.used; ++s) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, p.ev[2 * s], p.ev[2 * s + 1]), "event time");
+      p.ms[p.stage[s]] += t;
+    }
+    p.used = 0;
+  }
+  for (int i = 0; i < VIMG_NSTAGES; ++i) {
+    if (ms) ms[i] = p.ms[i];
+    if (launches) launches[i] = p.launches[i];
+    if (reset) p.ms[i] = 0.0, p.launches[i] = 0;
+  }
+  return VIMG_OK;
 }

@@ -69,98 +69,141 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 }
 
 // ---------------------------------------------------------------------------
-// Window statistics ("table-based area sums" of Sec. II, kept local): for each
-// frame, patch and displacement the exact integers S1 = sum F, S2 = sum F^2 over
-// the 21x21 window, and the normalisation factor
-//   inv(d) = 21 / sqrt(|Tc|^2 * (441 S2 - S1^2))       (0 if either factor is 0)
-// so that ZNCC = numerator * inv.  One CTA per (patch, frame); row sums slide
-// along x, window sums slide along y.
-constexpr int kStatThreads = 256;
+// Window statistics ("table-based area sums" of Sec. II).  For every window
+// top-left position (y, x) of the search region, the exact integers
+//   S1 = sum F,  S2 = sum F^2  over the 21x21 window,  SF = 441 S2 - S1^2,
+// give isf(y, x) = 1 / sqrt(SF) (0 when SF = 0).  isf does not depend on the
+// patch; the patch enters as the scalar 21 / |Tc_p|, so
+//   ZNCC_p(d) = numerator_p(d) * 21 / |Tc_p| * isf(ty_p + dy, tx_p + dx).
+// The map covers the top-left positions of all windows of all patches:
+// rows y0 - R .. y0 + 21 (ny - 1) + R, likewise for columns.  One CTA per
+// 32 x 32 block of positions per frame: row sums slide along x, window sums
+// slide along y, all in 64-bit integers.
+constexpr int kBoxRows = 64, kBoxCols = 32, kBoxThreads = 256;
+constexpr int kBoxIR = kBoxRows + kPatch - 1, kBoxIC = kBoxCols + kPatch - 1;  // 84 x 52 inputs
+constexpr int kBoxLoads = (kBoxIR * kBoxIC + kBoxThreads - 1) / kBoxThreads;     // 18
 
-__global__ void __launch_bounds__(kStatThreads)
-    k_stats(const uint16_t* __restrict__ frames, int H, int W, PatchGrid g, int R,
-            const float* __restrict__ tn2, float* __restrict__ inv) {
-  const int p = blockIdx.x, f = blockIdx.y, np = g.ny * g.nx;
-  const int w = 2 * R + 1, side = kPatch + 2 * R;
-  const int ty = g.y0 + (p / g.nx) * kPatch - R, tx = g.x0 + (p % g.nx) * kPatch - R;
-  __shared__ int reg[53 * 53];
-  __shared__ int rs1[53 * kMaxWin];
-  __shared__ long long rs2[53 * kMaxWin];
+__global__ void __launch_bounds__(kBoxThreads)
+    k_boxstats(const uint16_t* __restrict__ frames, int H, int W, int oy, int ox, int sh, int sw,
+               float* __restrict__ isf) {
+  const int f = blockIdx.z;
+  const int by = blockIdx.y * kBoxRows, bx = blockIdx.x * kBoxCols;
+  __shared__ unsigned short in[kBoxIR * kBoxIC];
+  __shared__ int rs1[kBoxIR * kBoxCols];
+  __shared__ long long rs2[kBoxIR * kBoxCols];
   const uint16_t* F = frames + (size_t)f * H * W;
-  for (int i = threadIdx.x; i < side * side; i += blockDim.x)
-    reg[i] = F[(size_t)(ty + i / side) * W + tx + i % side];
+  {
+    // all loads in flight at once, then the shared stores
+    unsigned v[kBoxLoads];
+#pragma unroll
+    for (int k = 0; k < kBoxLoads; ++k) {
+      const int i = threadIdx.x + k * kBoxThreads;
+      const int r = i / kBoxIC, c = i - r * kBoxIC;
+      const int y = min(oy + by + r, H - 1), x = min(ox + bx + c, W - 1);
+      v[k] = i < kBoxIR * kBoxIC ? __ldg(F + (size_t)y * W + x) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kBoxLoads; ++k) {
+      const int i = threadIdx.x + k * kBoxThreads;
+      if (i < kBoxIR * kBoxIC) in[i] = (unsigned short)v[k];
+    }
+  }
   __syncthreads();
-  // Row sums: thread (r, quarter) slides over its quarter of the displacements.
-  const int qlen = (w + 3) / 4;
-  for (int job = threadIdx.x; job < side * 4; job += blockDim.x) {
-    const int r = job >> 2, d0 = (job & 3) * qlen, d1 = min(w, d0 + qlen);
-    if (d0 >= d1) continue;
-    const int* row = reg + r * side;
+  // row sums: 84 rows x 4 chunks of 8 positions
+  for (int job = threadIdx.x; job < kBoxIR * 4; job += kBoxThreads) {
+    const int r = job >> 2, c0 = (job & 3) * 8;
+    const unsigned short* row = in + r * kBoxIC;
     int s1 = 0;
     long long s2 = 0;
+#pragma unroll
     for (int k = 0; k < kPatch; ++k) {
-      const int v = row[d0 + k];
+      const int v = row[c0 + k];
       s1 += v;
       s2 += (long long)v * v;
     }
-    for (int d = d0; d < d1; ++d) {
-      rs1[r * kMaxWin + d] = s1;
-      rs2[r * kMaxWin + d] = s2;
-      if (d + 1 < d1) {
-        const int a = row[d + kPatch], b = row[d];
+#pragma unroll
+    for (int c = c0; c < c0 + 8; ++c) {
+      rs1[r * kBoxCols + c] = s1;
+      rs2[r * kBoxCols + c] = s2;
+      if (c + 1 < c0 + 8) {
+        const int a = row[c + kPatch], b = row[c];
         s1 += a - b;
         s2 += (long long)a * a - (long long)b * b;
       }
     }
   }
   __syncthreads();
-  const float t2 = tn2[p];
-  float* out = inv + (size_t)(f * np + p) * w * kInvStride;
-  for (int job = threadIdx.x; job < w * 4; job += blockDim.x) {
-    const int dx = job >> 2, y0 = (job & 3) * qlen, y1 = min(w, y0 + qlen);
-    if (y0 >= y1) continue;
-    long long s1 = 0, s2 = 0;
-    for (int k = 0; k < kPatch; ++k) {
-      s1 += rs1[(y0 + k) * kMaxWin + dx];
-      s2 += rs2[(y0 + k) * kMaxWin + dx];
-    }
-    for (int dy = y0; dy < y1; ++dy) {
-      const long long sf = (long long)kPatchArea * s2 - s1 * s1;
-      float v = 0.f;
-      if (sf > 0 && t2 > 0.f) v = (float)kPatch * rsqrtf(t2 * (float)sf);
-      out[dy * kInvStride + dx] = v;
-      if (dy + 1 < y1) {
-        s1 += rs1[(dy + kPatch) * kMaxWin + dx] - rs1[dy * kMaxWin + dx];
-        s2 += rs2[(dy + kPatch) * kMaxWin + dx] - rs2[dy * kMaxWin + dx];
-      }
+  // window sums: 32 columns x 8 chunks of 8 rows
+  const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 8;
+  long long s1 = 0, s2 = 0;
+#pragma unroll
+  for (int k = 0; k < kPatch; ++k) {
+    s1 += rs1[(r0 + k) * kBoxCols + c];
+    s2 += rs2[(r0 + k) * kBoxCols + c];
+  }
+  float* out = isf + (size_t)f * sh * sw;
+#pragma unroll
+  for (int r = r0; r < r0 + 8; ++r) {
+    const int y = by + r, x = bx + c;
+    const long long sf = (long long)kPatchArea * s2 - s1 * s1;
+    if (y < sh && x < sw) out[(size_t)y * sw + x] = sf > 0 ? rsqrtf((float)sf) : 0.f;
+    if (r + 1 < r0 + 8) {
+      s1 += rs1[(r + kPatch) * kBoxCols + c] - rs1[r * kBoxCols + c];
+      s2 += rs2[(r + kPatch) * kBoxCols + c] - rs2[r * kBoxCols + c];
     }
   }
 }
 
+// Stats-map geometry for a patch grid.
+__host__ __device__ inline void stats_map_dims(PatchGrid g, int R, int* oy, int* ox, int* sh,
+                                               int* sw) {
+  *oy = g.y0 - R;
+  *ox = g.x0 - R;
+  *sh = kPatch * (g.ny - 1) + 2 * R + 1;
+  *sw = kPatch * (g.nx - 1) + 2 * R + 1;
+}
+
+size_t stats_map_floats(PatchGrid g, int R) {
+  int oy, ox, sh, sw;
+  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+  return (size_t)sh * sw;
+}
+
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
-                         const TemplateDev& td, float* inv, cudaStream_t st) {
+                         const TemplateDev& td, float* isf, cudaStream_t st) {
+  (void)td;
   if (nf <= 0) return cudaSuccess;
-  k_stats<<<dim3(g.ny * g.nx, nf), kStatThreads, 0, st>>>(frames, H, W, g, R, td.tn2, inv);
+  int oy, ox, sh, sw;
+  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+  dim3 grid((sw + kBoxCols - 1) / kBoxCols, (sh + kBoxRows - 1) / kBoxRows, nf);
+  k_boxstats<<<grid, kBoxThreads, 0, st>>>(frames, H, W, oy, ox, sh, sw, isf);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // FP32 correlation numerators on CUDA cores.
 //
-// CTA = (frame, patch row, group of up to kGroup patches).  The union of the
-// group's search regions (53 rows x (21 G + 2R) cols) is staged once in shared
-// memory as exact fp32 integers F - c.  Work is a list of output ROWS (patch u,
-// displacement row dy), each 2R+1 displacements wide, accumulated in registers:
-//   main pass u:      lane = dy in 0..31, every lane on patch u (template loads
-//                     are warp-uniform broadcasts, frame rows distinct);
-//   remainder pass:   lane = u, dy = 32 (only when 2R+1 = 33).
+// CTA = (frame, patch row, group of up to kGroup = 11 patches), 12 warps.  The
+// union of the group's search regions (53 rows x (21 G + 2R) cols) is staged in
+// shared memory as exact fp32 integers F - c, with the block of the isf map
+// those windows use.  Each warp owns one output-row pass:
+//   pass u < G:   lane = dy in 0..31, all lanes on patch u (template loads are
+//                 warp-uniform, frame rows distinct);
+//   pass G:       lane = u, dy = 32 (the 33rd displacement row, when 2R+1 = 33).
 // A lane streams the 21 frame rows it needs: per row 53 shared loads feed
-// 21 x 33 FMAs.  Each finished row is normalised and added to a per-CTA int64
-// surface in shared memory; the CTA then adds that surface to the frame's
-// global sums.
-constexpr int kGroup = 15;
+// 21 x 33 FMAs into 33 register accumulators.  Each finished row is normalised
+// and added in 2^-40 fixed point to a per-CTA int64 surface in shared memory,
+// which the CTA finally adds to the frame's global sums.
+constexpr int kGroup = 11;
 constexpr int kCsEntries = kMaxWin * kMaxWin + 1;  // keeps what follows 16-byte aligned
-constexpr int kCorrWarps = 8;
+constexpr int kRegionRows = kPatch + 2 * kMaxR;                     // 53
+constexpr int kRegionStride = (kGroup * kPatch + 2 * kMaxR) | 1;    // 263
+constexpr int kIsfCols = (kGroup - 1) * kPatch + kMaxWin;           // 243
+
+// floor(i / d) as a multiply-high by m = ceil(2^32 / d): exact for i < 2^32 / d,
+// far above any index here (d <= 263, i < 14,000).
+__device__ __forceinline__ unsigned fast_div(unsigned i, unsigned m) { return __umulhi(i, m); }
+constexpr int kCorrWarps = kGroup + 1;
 constexpr int kCorrThreads = kCorrWarps * 32;
 
 template <int NX>
@@ -176,7 +219,7 @@ __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
     float t[kTplStride];
 #pragma unroll
     for (int i = 0; i < kTplStride; i += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(trow + i);
+      const float4 v = __ldg(reinterpret_cast<const float4*>(trow + i));
       t[i] = v.x, t[i + 1] = v.y, t[i + 2] = v.z, t[i + 3] = v.w;
     }
 #pragma unroll
@@ -191,33 +234,70 @@ __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
 template <int NX>
 __global__ void __launch_bounds__(kCorrThreads, 2)
     k_corr_f32(const uint16_t* __restrict__ frames, int H, int W, PatchGrid g, int R,
-               const float* __restrict__ tc, const int* __restrict__ coff,
-               const float* __restrict__ inv, unsigned long long* __restrict__ csum) {
+               const float* __restrict__ tc, const float* __restrict__ tn2,
+               const int* __restrict__ coff, const float* __restrict__ isf,
+               unsigned long long* __restrict__ csum) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int f = blockIdx.y, np = g.ny * g.nx, w = 2 * R + 1;
+  const int f = blockIdx.y, w = 2 * R + 1;
   const int groups_per_row = (g.nx + kGroup - 1) / kGroup;
   const int py = blockIdx.x / groups_per_row, gx = blockIdx.x % groups_per_row;
   const int px0 = gx * kGroup, G = min(kGroup, g.nx - px0);
   const int rows = kPatch + 2 * R, cols = G * kPatch + 2 * R;
   // Rows are allocated for the widest window (a lane always reads 53 values) and
   // given an odd stride so that lanes on different rows hit distinct banks.
-  const int rs = (G * kPatch + 2 * kMaxR) | 1;
+  const int rs = (G * kPatch + 2 * kMaxR) | 1;  // <= kRegionStride
+  const int scols = (G - 1) * kPatch + w;  // isf columns this CTA uses
   const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
+  int oy, ox, sh, sw;
+  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
 
   unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem);      // [w][w]
-  float* tsm = reinterpret_cast<float*>(cs + kCsEntries);                    // [G][21][24]
-  float* reg = tsm + kGroup * kPatch * kTplStride;                           // [rows][rs]
+  float* ism = reinterpret_cast<float*>(cs + kCsEntries);                    // [w][scols]
+  float* reg = ism + kMaxWin * kIsfCols;                                     // [rows][rs]
 
   const int p0 = py * g.nx + px0;
   const float c = (float)coff[p0];
   for (int i = threadIdx.x; i < w * w; i += blockDim.x) cs[i] = 0ull;
-  for (int i = threadIdx.x * 4; i < G * kPatch * kTplStride; i += blockDim.x * 4)
-    *reinterpret_cast<float4*>(tsm + i) =
-        *reinterpret_cast<const float4*>(tc + (size_t)p0 * kPatch * kTplStride + i);
-  const uint16_t* F = frames + (size_t)f * H * W;
-  for (int i = threadIdx.x; i < rows * rs; i += blockDim.x) {
-    const int r = i / rs, x = i - r * rs;
-    reg[i] = x < cols ? (float)F[(size_t)(ry + r) * W + rx + x] - c : 0.f;
+  // Stage the frame region and the isf block.  Every thread first issues all of
+  // its global loads (one round trip), then converts and stores.
+  const float* isf_f = isf + (size_t)f * sh * sw + (size_t)(ry - oy) * sw + (rx - ox);
+  const uint16_t* F = frames + (size_t)f * H * W + (size_t)ry * W + rx;
+  {
+    constexpr int kRegLoads = (kRegionRows * kRegionStride + kCorrThreads - 1) / kCorrThreads;
+    constexpr int kHalf = (kRegLoads + 1) / 2;  // two batches keep the registers in budget
+    const unsigned m = 0xffffffffu / (unsigned)rs + 1u;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      unsigned short v[kHalf];
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) {
+        const int i = threadIdx.x + (b * kHalf + k) * kCorrThreads;
+        const int r = (int)fast_div((unsigned)i, m), x = i - r * rs;
+        v[k] = (i < rows * rs && x < cols) ? __ldg(F + (size_t)r * W + x) : (unsigned short)0;
+      }
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) {
+        const int i = threadIdx.x + (b * kHalf + k) * kCorrThreads;
+        const int x = i - (int)fast_div((unsigned)i, m) * rs;
+        if (i < rows * rs) reg[i] = x < cols ? (float)v[k] - c : 0.f;
+      }
+    }
+  }
+  {
+    constexpr int kIsfLoads = (kMaxWin * kIsfCols + kCorrThreads - 1) / kCorrThreads;  // 21
+    const unsigned m = 0xffffffffu / (unsigned)scols + 1u;
+    float v[kIsfLoads];
+#pragma unroll
+    for (int k = 0; k < kIsfLoads; ++k) {
+      const int i = threadIdx.x + k * kCorrThreads;
+      const int r = (int)fast_div((unsigned)i, m), x = i - r * scols;
+      v[k] = i < w * scols ? __ldg(isf_f + (size_t)r * sw + x) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kIsfLoads; ++k) {
+      const int i = threadIdx.x + k * kCorrThreads;
+      if (i < w * scols) ism[i] = v[k];
+    }
   }
   __syncthreads();
 
@@ -235,14 +315,17 @@ __global__ void __launch_bounds__(kCorrThreads, 2)
     const bool active = u < G && dy < w;
     const int uu = active ? u : 0, dd = active ? dy : 0;
     float acc[NX];
-    corr_row<NX>(reg + dd * rs + uu * kPatch, rs, tsm + uu * kPatch * kTplStride, acc);
+    corr_row<NX>(reg + dd * rs + uu * kPatch, rs, tc + (size_t)(p0 + uu) * kPatch * kTplStride,
+                 acc);
     if (active) {
-      const float* iv = inv + ((size_t)(f * np + p0 + uu) * w + dd) * kInvStride;
+      const float t2 = __ldg(tn2 + p0 + uu);
+      const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+      const float* iv = ism + dd * scols + uu * kPatch;
       unsigned long long* crow = cs + dd * w;
 #pragma unroll
       for (int j = 0; j < NX; ++j) {
         if (j < w) {
-          const float z = acc[j] * __ldg(iv + j);
+          const float z = acc[j] * pscale * iv[j];
           atomicAdd(crow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
         }
       }
@@ -254,13 +337,13 @@ __global__ void __launch_bounds__(kCorrThreads, 2)
 }
 
 static size_t corr_smem_bytes(int R) {
-  const int rows = kPatch + 2 * R, rs = (kGroup * kPatch + 2 * kMaxR) | 1;
-  return sizeof(unsigned long long) * kCsEntries +
-         sizeof(float) * (size_t)kGroup * kPatch * kTplStride + sizeof(float) * rows * rs;
+  const int rows = kPatch + 2 * R;
+  return sizeof(unsigned long long) * kCsEntries + sizeof(float) * kMaxWin * kIsfCols +
+         sizeof(float) * rows * kRegionStride;
 }
 
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
-                            const TemplateDev& td, const float* inv,
+                            const TemplateDev& td, const float* isf,
                             unsigned long long* csum, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   const size_t smem = corr_smem_bytes(R);
@@ -273,8 +356,8 @@ cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchG
     attr_set = true;
   }
   const int groups = g.ny * ((g.nx + kGroup - 1) / kGroup);
-  k_corr_f32<kMaxWin><<<dim3(groups, nf), kCorrThreads, smem, st>>>(frames, H, W, g, R, td.tc,
-                                                                    td.coff, inv, csum);
+  k_corr_f32<kMaxWin><<<dim3(groups, nf), kCorrThreads, smem, st>>>(
+      frames, H, W, g, R, td.tc, td.tn2, td.coff, isf, csum);
   return cudaGetLastError();
 }
 

@@ -111,12 +111,38 @@ __device__ __forceinline__ Split split_shift(float s) {
   return {(int)fl, s - fl};
 }
 
+// Mirror index for the Gaussian border ("d c b a | a b c d"), then clamped into
+// the image: indices more than 12 past the border only feed outputs outside it.
 __device__ __forceinline__ int mirror_idx(int i, int n) {
-  return i < 0 ? -i - 1 : (i >= n ? 2 * n - i - 1 : i);
+  i = i < 0 ? -i - 1 : (i >= n ? 2 * n - i - 1 : i);
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Range [lo, hi] of mirror_idx over the integers a..b (a <= b).
+__device__ __forceinline__ void mirror_range(int a, int b, int n, int& lo, int& hi) {
+  lo = n - 1;
+  hi = 0;
+  if (a <= -1) {  // decreasing piece: -y-1
+    const int e = b < -1 ? b : -1;
+    lo = min(lo, -e - 1);
+    hi = max(hi, -a - 1);
+  }
+  if (b >= 0 && a <= n - 1) {  // identity piece
+    lo = min(lo, a > 0 ? a : 0);
+    hi = max(hi, b < n - 1 ? b : n - 1);
+  }
+  if (b >= n) {  // decreasing piece: 2n-y-1
+    const int s = a > n ? a : n;
+    lo = min(lo, 2 * n - b - 1);
+    hi = max(hi, 2 * n - s - 1);
+  }
+  lo = max(0, min(n - 1, lo));
+  hi = max(0, min(n - 1, hi));
 }
 
 // V(y, x) = F(y + s_y, x + s_x), bilinear, coordinates clamped to the image.
-// s = i + f with 0 <= f < 1 keeps every weight exact.
+// s = i + f with 0 <= f < 1 keeps every weight exact.  Global-memory form (used
+// for the few high-pass samples outside the staged tile).
 __device__ __forceinline__ float bilin(const uint16_t* __restrict__ F, int H, int W, int y, int x,
                                        Split sy, Split sx) {
   int r0, r1, c0, c1;
@@ -150,6 +176,49 @@ __device__ __forceinline__ float bilin(const uint16_t* __restrict__ F, int H, in
   return fmaf(wy, bot - top, top);
 }
 
+// One axis of the bilinear sample for tile coordinate i (halo-extended):
+// packed (first source index - base) | (second - first) << 8 | (weight != 0) << 9.
+__device__ __forceinline__ unsigned short axis_entry(int i0, int n, Split s, int base) {
+  const int v = mirror_idx(i0, n) + s.i;
+  int a, d, wf;
+  if (v < 0) {
+    a = 0, d = 0, wf = 0;
+  } else if (v >= n - 1) {
+    a = n - 1, d = 0, wf = 0;
+  } else {
+    a = v, d = 1, wf = s.f != 0.f;
+  }
+  return (unsigned short)((a - base) | (d << 8) | (wf << 9));
+}
+
+// Source rectangle of the staged frame tile: rows/cols whose pixels any
+// halo-extended tile coordinate can touch.  lo/hi are the tile's mirrored
+// coordinate ranges (frame independent); the shift moves them.
+struct StageGeom {
+  Split sy, sx;
+  int r0, c0, nr, nc;
+  bool plain;  // no mirroring and no clamping: source = tile coordinate + shift
+};
+
+struct TileRange {
+  int ylo, yhi, xlo, xhi;
+  bool inner;  // the halo-extended tile lies inside the image
+};
+
+__device__ __forceinline__ StageGeom stage_geom(Split sy, Split sx, const TileRange& tr, int H,
+                                                int W) {
+  StageGeom g;
+  g.sy = sy;
+  g.sx = sx;
+  g.r0 = max(0, min(H - 1, tr.ylo + sy.i));
+  g.nr = max(0, min(H - 1, tr.yhi + sy.i + 1)) - g.r0 + 1;
+  g.c0 = max(0, min(W - 1, tr.xlo + sx.i));
+  g.nc = max(0, min(W - 1, tr.xhi + sx.i + 1)) - g.c0 + 1;
+  g.plain = tr.inner && tr.ylo + sy.i >= 0 && tr.yhi + sy.i + 1 <= H - 1 &&
+            tr.xlo + sx.i >= 0 && tr.xhi + sx.i + 1 <= W - 1;
+  return g;
+}
+
 __device__ __forceinline__ void frame_at(const FrameSource& s, long long t, const uint16_t*& F,
                                          Split& sy, Split& sx, int HW) {
   long long v = t - s.t_first;
@@ -170,12 +239,20 @@ __device__ __forceinline__ void frame_at(const FrameSource& s, long long t, cons
 __device__ __forceinline__ long long hp_q(float v) { return __float2ll_rn(v * kHpScale); }
 
 // ---- the fused kernel ------------------------------------------------------------
+constexpr int kFst = 58;                 // staged frame row stride (uint16), >= 57 columns
+constexpr int kFstRows = 57;
+constexpr int kPfRows = (kFstRows + 7) / 8;  // prefetch: 64 columns x 8 rows per pass
+
 __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
   extern __shared__ __align__(16) float sm[];
-  float* vext = sm;                  // [56][56] resampled tile + halo
-  float* hbuf = vext + kExt * kExt;  // [56][32] row-smoothed
-  float* hist = hbuf + kExt * kTile; // [L][1024] smoothed history
   const int H = a.H, W = a.W, L = a.L, HW = H * W;
+  float* vext = sm;                            // [56][56] resampled tile + halo
+  float* hbuf = vext + kExt * kExt;            // [56][32] row-smoothed
+  float* hist = hbuf + kExt * kTile;           // [L][1024] smoothed history
+  float* shs = hist + (size_t)L * kTile * kTile;  // [L][2] shifts of the slot's frames
+  unsigned short* fst = reinterpret_cast<unsigned short*>(shs + 2 * kMaxL);
+  unsigned short* rtab = fst + kFstRows * kFst;  // [56] row entries
+  unsigned short* ctab = rtab + kExt;            // [56] column entries
   const int ntx = (W + kTile - 1) / kTile;
   const int ty0 = (blockIdx.x / ntx) * kTile, tx0 = (blockIdx.x % ntx) * kTile;
   const int tid = threadIdx.x, lx = tid & 31, ly0 = (tid >> 5) * 2;
@@ -185,11 +262,36 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
   const long long t_end = src.t_first + src.n_carry + src.n_batch;
   const long long s0 = a.seg_base + (long long)blockIdx.y * L;
   const long long s1 = s0 + L < t_end ? s0 + L : t_end;
+  const int nfr = (int)(s1 - s0);
   const bool complete = s0 + L <= t_end;
+
+  TileRange tr;
+  mirror_range(ty0 - kGaussMaxRadius, ty0 + kTile + kGaussMaxRadius - 1, H, tr.ylo, tr.yhi);
+  mirror_range(tx0 - kGaussMaxRadius, tx0 + kTile + kGaussMaxRadius - 1, W, tr.xlo, tr.xhi);
+  tr.inner = ty0 - kGaussMaxRadius >= 0 && ty0 + kTile + kGaussMaxRadius <= H &&
+             tx0 - kGaussMaxRadius >= 0 && tx0 + kTile + kGaussMaxRadius <= W;
 
   float w[kTaps];
 #pragma unroll
   for (int i = 0; i < kTaps; ++i) w[i] = a.gw[i];
+
+  // shifts of the slot's frames
+  for (int i = tid; i < 2 * nfr; i += kTempThreads) {
+    const long long v = s0 + (i >> 1) - src.t_first;
+    shs[i] = v < src.n_carry ? src.carry_shift[2 * v + (i & 1)]
+                             : src.batch_shift[2 * (v - src.n_carry) + (i & 1)];
+  }
+  __syncthreads();
+
+  auto frame_ptr = [&](long long t) -> const uint16_t* {
+    const long long v = t - src.t_first;
+    return v < src.n_carry ? src.carry + (size_t)v * HW : src.batch + (size_t)(v - src.n_carry) * HW;
+  };
+  auto geom_of = [&](int fi) {
+    return stage_geom(split_shift(shs[2 * fi]), split_shift(shs[2 * fi + 1]), tr, H, W);
+  };
+  // prefetch pattern: column pc of rows pr, pr + 8, ... (no division)
+  const int pc = tid & 63, pr = tid >> 6;
 
   float sum_a = 0.f, sum_b = 0.f, mx_a = -FLT_MAX, mx_b = -FLT_MAX;
   long long hs_a = 0, hs_b = 0;
@@ -197,19 +299,79 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
   const bool do_hp = a.out_hp && a.hp_w > 0 && a.corrected;
   const float hp_inv = 1.0f / ((float)a.hp_w * kHpScale);
 
-  for (long long t = s0; t < s1; ++t) {
-    const uint16_t* F;
-    Split sy, sx;
-    frame_at(src, t, F, sy, sx, HW);
-    for (int i = tid; i < kExt * kExt; i += kTempThreads) {
-      const int ry = i / kExt, rx = i - ry * kExt;
-      const int yy = mirror_idx(ty0 - kGaussMaxRadius + ry, H);
-      const int xx = mirror_idx(tx0 - kGaussMaxRadius + rx, W);
-      vext[i] = bilin(F, H, W, yy, xx, sy, sx);
+  // Stage the slot's first frame (blocking) and its tables.
+  StageGeom gcur = geom_of(0);
+  {
+    const uint16_t* F = frame_ptr(s0);
+#pragma unroll
+    for (int k = 0; k < kPfRows; ++k) {
+      const int r = pr + 8 * k;
+      if (r < gcur.nr && pc < gcur.nc)
+        fst[r * kFst + pc] = __ldg(F + (size_t)(gcur.r0 + r) * W + gcur.c0 + pc);
+    }
+    if (tid < kExt) rtab[tid] = axis_entry(ty0 - kGaussMaxRadius + tid, H, gcur.sy, gcur.r0);
+    else if (tid < 2 * kExt)
+      ctab[tid - kExt] = axis_entry(tx0 - kGaussMaxRadius + tid - kExt, W, gcur.sx, gcur.c0);
+  }
+  __syncthreads();
+
+  for (int fi = 0; fi < nfr; ++fi) {
+    const long long t = s0 + fi;
+    // 0. issue the next frame's loads now; they land while this frame computes
+    const bool more = fi + 1 < nfr;
+    StageGeom gnext = gcur;
+    unsigned short pf[kPfRows];
+    if (more) {
+      gnext = geom_of(fi + 1);
+      const uint16_t* F = frame_ptr(t + 1);
+#pragma unroll
+      for (int k = 0; k < kPfRows; ++k) {
+        const int r = pr + 8 * k;
+        pf[k] = (r < gnext.nr && pc < gnext.nc)
+                    ? __ldg(F + (size_t)(gnext.r0 + r) * W + gnext.c0 + pc)
+                    : (unsigned short)0;
+      }
+    }
+    // 1. resample the tile + halo from the staged frame
+    {
+      const float fy = gcur.sy.f, fx = gcur.sx.f;
+      if (gcur.plain) {
+        // source (r, c) = tile coordinate + shift - staging origin, constant weights
+        const int oy = tr.ylo + gcur.sy.i - gcur.r0, ox = tr.xlo + gcur.sx.i - gcur.c0;
+        if (tid < kExt * 8) {
+          const int ry = tid >> 3, c0 = (tid & 7) * 7;
+          const unsigned short* top = fst + (ry + oy) * kFst + c0 + ox;
+          const unsigned short* bot = top + kFst;
+          float tp[8], bt[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            tp[k] = top[k];
+            bt[k] = bot[k];
+          }
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            const float u = fmaf(fx, tp[k + 1] - tp[k], tp[k]);
+            const float d = fmaf(fx, bt[k + 1] - bt[k], bt[k]);
+            vext[ry * kExt + c0 + k] = fmaf(fy, d - u, u);
+          }
+        }
+      } else {
+        for (int i = tid; i < kExt * kExt; i += kTempThreads) {
+          const int ry = i / kExt, rx = i - ry * kExt;
+          const unsigned re = rtab[ry], ce = ctab[rx];
+          const int o0 = (re & 255) * kFst + (ce & 255);
+          const int od = ((re >> 8) & 1) * kFst, oc = (ce >> 8) & 1;
+          const float wy = (re >> 9) ? fy : 0.f, wx = (ce >> 9) ? fx : 0.f;
+          const float p = fst[o0], q = fst[o0 + oc], r = fst[o0 + od], u = fst[o0 + od + oc];
+          const float top = fmaf(wx, q - p, p), bot = fmaf(wx, u - r, r);
+          vext[i] = fmaf(wy, bot - top, top);
+        }
+      }
     }
     __syncthreads();
     const float v_a = vext[(ly0 + kGaussMaxRadius) * kExt + lx + kGaussMaxRadius];
     const float v_b = vext[(ly0 + 1 + kGaussMaxRadius) * kExt + lx + kGaussMaxRadius];
+    // 2. corrected (or high-passed) output of frames new to this call
     if (t >= src.t_new && a.corrected) {
       float* out = a.corrected + (size_t)(t - src.t_new) * HW;
       float o_a = v_a, o_b = v_b;
@@ -242,7 +404,7 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
       if (va) out[(size_t)ya * W + x] = o_a;
       if (vb) out[(size_t)yb * W + x] = o_b;
     }
-    // row pass: 56 rows x 8 groups of 4 output columns
+    // 3. row pass of the Gaussian: 56 rows x 8 groups of 4 output columns
     if (tid < kExt * 8) {
       const int r = tid >> 3, cg = tid & 7;
       const float* in = vext + r * kExt + cg * 4;
@@ -259,8 +421,21 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
         for (int j = 0; j < 4; ++j) o[j] = fmaf(w[m], v[j + m], o[j]);
       *reinterpret_cast<float4*>(hbuf + r * kTile + cg * 4) = make_float4(o[0], o[1], o[2], o[3]);
     }
+    // 4. stage the next frame (the current one was consumed before the barrier)
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < kPfRows; ++k) {
+        const int r = pr + 8 * k;
+        if (r < gnext.nr && pc < gnext.nc) fst[r * kFst + pc] = pf[k];
+      }
+      if (tid < kExt) rtab[tid] = axis_entry(ty0 - kGaussMaxRadius + tid, H, gnext.sy, gnext.r0);
+      else if (tid < 2 * kExt)
+        ctab[tid - kExt] =
+            axis_entry(tx0 - kGaussMaxRadius + tid - kExt, W, gnext.sx, gnext.c0);
+      gcur = gnext;
+    }
     __syncthreads();
-    // column pass: two output rows per thread
+    // 5. column pass: two output rows per thread, then the segment accumulators
     float col[kTaps + 1];
 #pragma unroll
     for (int k = 0; k < kTaps + 1; ++k) col[k] = hbuf[(ly0 + k) * kTile + lx];
@@ -274,7 +449,7 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
     sum_b += v_b;
     mx_a = fmaxf(mx_a, b_a);
     mx_b = fmaxf(mx_b, b_b);
-    float* hrow = hist + (size_t)(t - s0) * (kTile * kTile) + ly0 * kTile + lx;
+    float* hrow = hist + (size_t)fi * (kTile * kTile) + ly0 * kTile + lx;
     hrow[0] = b_a;
     hrow[kTile] = b_b;
   }
@@ -294,7 +469,9 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
 }
 
 static size_t temporal_smem(int L) {
-  return sizeof(float) * ((size_t)kExt * kExt + (size_t)kExt * kTile + (size_t)L * kTile * kTile);
+  return sizeof(float) * ((size_t)kExt * kExt + (size_t)kExt * kTile + (size_t)L * kTile * kTile +
+                          2 * kMaxL) +
+         sizeof(unsigned short) * (kFstRows * kFst + 2 * kExt);
 }
 
 cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st) {

@@ -59,10 +59,11 @@ struct TemporalArgs {
 // ---- launchers (each enqueues on `st`; returns cudaGetLastError()) ----------
 cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, TemplateDev td,
                                  cudaStream_t st);
+size_t stats_map_floats(PatchGrid g, int R);  // per frame
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
-                         const TemplateDev& td, float* inv, cudaStream_t st);
+                         const TemplateDev& td, float* isf, cudaStream_t st);
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
-                            const TemplateDev& td, const float* inv,
+                            const TemplateDev& td, const float* isf,
                             unsigned long long* csum, cudaStream_t st);
 cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, float* shifts,
                         float* peak_info, double* surface, cudaStream_t st);

@@ -50,8 +50,10 @@ class IO(ctypes.Structure):
 EXPORTS = [
     "vimg_default_params", "vimg_create", "vimg_destroy", "vimg_set_template", "vimg_process",
     "vimg_process_io", "vimg_process_host", "vimg_frames_seen", "vimg_reset", "vimg_last_error",
-    "vimg_version",
+    "vimg_version", "vimg_profile_enable", "vimg_profile_read",
 ]
+NSTAGES = 6
+STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
 
 
 def _load():
@@ -79,6 +81,10 @@ def _load():
     L.vimg_reset.restype = i
     L.vimg_last_error.argtypes = [vp]
     L.vimg_last_error.restype = ctypes.c_char_p
+    L.vimg_profile_enable.argtypes = [vp, i]
+    L.vimg_profile_enable.restype = i
+    L.vimg_profile_read.argtypes = [vp, vp, vp, i]
+    L.vimg_profile_read.restype = i
     L.vimg_version.argtypes = []
     L.vimg_version.restype = ctypes.c_char_p
     return L
@@ -173,6 +179,17 @@ class Handle:
         return self._check(lib.vimg_process_host(self._h, _ptr(frames_host), n,
                                                  _ptr(shifts_host), _ptr(summary_host),
                                                  _ptr(corrected)))
+
+
+    def profile(self, on: bool = True):
+        self._check(lib.vimg_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True):
+        """{stage: (ms, launches)} summed since the last reset."""
+        ms = (ctypes.c_double * NSTAGES)()
+        cnt = (ctypes.c_longlong * NSTAGES)()
+        self._check(lib.vimg_profile_read(self._h, ms, cnt, 1 if reset else 0))
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(NSTAGES)}
 
 
 def version() -> str:
