@@ -164,6 +164,30 @@ const char* vimg_last_error(const vimg_handle* h);
 int vimg_profile_enable(vimg_handle* h, int on);
 int vimg_profile_read(vimg_handle* h, double* ms, long long* launches, int reset);
 
+/* Motion estimate with no allocation at all, for callers that cannot allocate
+ * device memory when they need shifts: code inside a CUDA-graph capture that
+ * must not grow the memory pool, real-time acquisition loops that forbid
+ * allocator calls (an allocation can block on the driver and miss the frame
+ * deadline), and hosts that have already reserved all device memory for frame
+ * buffers.  The paper has no counterpart; it is an interface of this library.
+ *
+ * Computes, for n frames (device uint16 [n][H][W]) against the template
+ * (device float32 [H][W]), the same shifts as vimg_process's motion estimate:
+ * d_shifts_out device float32 [n][2] (dy, dx); d_peak_info (optional) device
+ * float32 [n][4] as in vimg_io.  No handle, no stream state.  All scratch lives
+ * in one 12 MiB array in the library's static device memory, which every GPU
+ * that loads the library holds until the process exits.  Frames up to
+ * 1024 x 1024 (search_radius <= 16) fit; larger ones return VIMG_ERR_SIZE with
+ * nothing enqueued.  The first call on a device looks up the array's device
+ * address with that device current: make it before any stream capture.  Every
+ * call shares the array (and clears what must start at zero); calls whose work
+ * overlaps on the GPU race and give wrong results, so serialise them.  Work is
+ * enqueued on `stream` (NULL = default stream).  Returns VIMG_OK or an error
+ * code (VIMG_ERR_ARG, VIMG_ERR_SIZE, VIMG_ERR_CUDA). */
+int vimg_motion_noalloc(const float* d_template, const uint16_t* d_frames, int n, int H, int W,
+                        int search_radius, float* d_shifts_out, float* d_peak_info,
+                        void* stream);
+
 /* Library version string. */
 const char* vimg_version(void);
 

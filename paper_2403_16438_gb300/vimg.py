@@ -50,7 +50,7 @@ class IO(ctypes.Structure):
 EXPORTS = [
     "vimg_default_params", "vimg_create", "vimg_destroy", "vimg_set_template", "vimg_process",
     "vimg_process_io", "vimg_process_host", "vimg_frames_seen", "vimg_reset", "vimg_last_error",
-    "vimg_version", "vimg_profile_enable", "vimg_profile_read",
+    "vimg_version", "vimg_profile_enable", "vimg_profile_read", "vimg_motion_noalloc",
 ]
 NSTAGES = 6
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
@@ -85,6 +85,8 @@ def _load():
     L.vimg_profile_enable.restype = i
     L.vimg_profile_read.argtypes = [vp, vp, vp, i]
     L.vimg_profile_read.restype = i
+    L.vimg_motion_noalloc.argtypes = [vp, vp, i, i, i, i, vp, vp, vp]
+    L.vimg_motion_noalloc.restype = i
     L.vimg_version.argtypes = []
     L.vimg_version.restype = ctypes.c_char_p
     return L
