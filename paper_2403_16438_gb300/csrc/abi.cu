@@ -4,9 +4,8 @@
 // Per internal batch of at most max_chunk frames (batches end on segment
 // boundaries whenever possible, so the batch's raw frames are still in L2 when
 // the temporal pass reads them again):
-//   1. motion estimate in sub-batches of kMotionBatch frames:
-//      zero the fixed-point surfaces, window statistics, correlation numerators
-//      (FP32 CUDA cores, or BF16 tensor cores), integer peak + parabola;
+//   1. motion estimate of the whole batch: zero the fixed-point surfaces, window
+//      statistics, correlation numerators, integer peak + parabola;
 //   2. one fused temporal launch over every segment slot the batch touches;
 //   3. the raw frames and shifts still needed later (the open segment and the
 //      high-pass history) are copied into the handle's carry buffer.
@@ -21,7 +20,6 @@
 using namespace vimg;
 
 namespace {
-constexpr int kMotionBatch = 16;
 constexpr int kProfSlots = 65536;
 thread_local std::string g_create_error;
 
@@ -46,7 +44,7 @@ struct vimg_handle {
   TemplateDev td{};
   bool have_template = false;
   float gw[2 * kGaussMaxRadius + 1] = {};
-  float* inv = nullptr;                 // [kMotionBatch][stats map] 1/sqrt(SF) per window
+  float* inv = nullptr;                 // [max_chunk][stats map] 1/sqrt(SF) per window
   unsigned long long* csum = nullptr;   // [max_chunk][nwin]
   float* shift_tmp = nullptr;           // [max_chunk][2]
   uint16_t* carry[2] = {nullptr, nullptr};
@@ -216,7 +214,7 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
   ALLOC(h->td.tc, sizeof(float) * h->np * kPatch * kTplStride);
   ALLOC(h->td.tn2, sizeof(float) * h->np);
   ALLOC(h->td.coff, sizeof(int) * h->np);
-  ALLOC(h->inv, sizeof(float) * (size_t)kMotionBatch * stats_map_floats(g, p.search_radius));
+  ALLOC(h->inv, sizeof(float) * (size_t)p.max_chunk * stats_map_floats(g, p.search_radius));
   ALLOC(h->csum, sizeof(unsigned long long) * (size_t)p.max_chunk * h->nwin);
   ALLOC(h->shift_tmp, sizeof(float) * 2 * (size_t)p.max_chunk);
   for (int i = 0; i < 2; ++i) {
@@ -268,23 +266,20 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
 // Motion estimate of nf frames (nf <= max_chunk) into shifts[nf][2].
 static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shifts,
                     float* peak_info, double* surface) {
-  const size_t HW = (size_t)h->H * h->W;
   const int R = h->p.search_radius;
   CK(cudaMemsetAsync(h->csum, 0, sizeof(unsigned long long) * (size_t)nf * h->nwin, h->st),
      "surface reset");
-  for (int f0 = 0; f0 < nf; f0 += kMotionBatch) {
-    const int m = std::min(kMotionBatch, nf - f0);
-    int ps = prof_begin(h, 0);
-    CK(launch_stats(frames + HW * f0, m, h->H, h->W, h->g, R, h->td, h->inv, h->st),
-       "window statistics launch");
-    prof_end(h, ps);
-    ps = prof_begin(h, 1);
-    CK(launch_corr_f32(frames + HW * f0, m, h->H, h->W, h->g, R, h->td, h->inv,
-                       h->csum + (size_t)f0 * h->nwin, h->st),
-       "correlation launch");
-    prof_end(h, ps);
-  }
-  int ps = prof_begin(h, 2);
+  // One launch per stage for the whole batch: thousands of CTAs, so the last
+  // partial wave costs little.
+  int ps = prof_begin(h, 0);
+  CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st),
+     "window statistics launch");
+  prof_end(h, ps);
+  ps = prof_begin(h, 1);
+  CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st),
+     "correlation launch");
+  prof_end(h, ps);
+  ps = prof_begin(h, 2);
   CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, surface, h->st), "peak launch");
   prof_end(h, ps);
   return VIMG_OK;

@@ -11,6 +11,7 @@
 // int64), so N*sum F^2 - (sum F)^2 carries no rounding at all.  Patch values are
 // summed over patches in 2^-40 fixed point with 64-bit integer atomics: the sum
 // is exact and independent of the order in which CTAs finish.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 
@@ -77,20 +78,22 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 //   ZNCC_p(d) = numerator_p(d) * 21 / |Tc_p| * isf(ty_p + dy, tx_p + dx).
 // The map covers the top-left positions of all windows of all patches:
 // rows y0 - R .. y0 + 21 (ny - 1) + R, likewise for columns.  One CTA per
-// 32 x 32 block of positions per frame: row sums slide along x, window sums
+// 56 x 32 block of positions per frame: row sums slide along x, window sums
 // slide along y, all in 64-bit integers.
-constexpr int kBoxRows = 64, kBoxCols = 32, kBoxThreads = 256;
-constexpr int kBoxIR = kBoxRows + kPatch - 1, kBoxIC = kBoxCols + kPatch - 1;  // 84 x 52 inputs
-constexpr int kBoxLoads = (kBoxIR * kBoxIC + kBoxThreads - 1) / kBoxThreads;     // 18
+constexpr int kBoxRows = 56, kBoxCols = 32, kBoxThreads = 256;
+constexpr int kBoxIR = kBoxRows + kPatch - 1, kBoxIC = kBoxCols + kPatch - 1;  // 76 x 52 inputs
+constexpr int kBoxInStride = kBoxIC + 1;     // 53: odd, so rows fall in distinct banks
+constexpr int kBoxRsStride = kBoxCols + 1;   // 33
+constexpr int kBoxLoads = (kBoxIR * kBoxIC + kBoxThreads - 1) / kBoxThreads;     // 16
 
 __global__ void __launch_bounds__(kBoxThreads)
     k_boxstats(const uint16_t* __restrict__ frames, int H, int W, int oy, int ox, int sh, int sw,
                float* __restrict__ isf) {
   const int f = blockIdx.z;
   const int by = blockIdx.y * kBoxRows, bx = blockIdx.x * kBoxCols;
-  __shared__ unsigned short in[kBoxIR * kBoxIC];
-  __shared__ int rs1[kBoxIR * kBoxCols];
-  __shared__ long long rs2[kBoxIR * kBoxCols];
+  __shared__ int in[kBoxIR * kBoxInStride];
+  __shared__ int rs1[kBoxIR * kBoxRsStride];
+  __shared__ long long rs2[kBoxIR * kBoxRsStride];
   const uint16_t* F = frames + (size_t)f * H * W;
   {
     // all loads in flight at once, then the shared stores
@@ -105,14 +108,15 @@ __global__ void __launch_bounds__(kBoxThreads)
 #pragma unroll
     for (int k = 0; k < kBoxLoads; ++k) {
       const int i = threadIdx.x + k * kBoxThreads;
-      if (i < kBoxIR * kBoxIC) in[i] = (unsigned short)v[k];
+      const int r = i / kBoxIC, c = i - r * kBoxIC;
+      if (i < kBoxIR * kBoxIC) in[r * kBoxInStride + c] = (int)v[k];
     }
   }
   __syncthreads();
-  // row sums: 84 rows x 4 chunks of 8 positions
+  // row sums: 76 rows x 4 chunks of 8 positions
   for (int job = threadIdx.x; job < kBoxIR * 4; job += kBoxThreads) {
     const int r = job >> 2, c0 = (job & 3) * 8;
-    const unsigned short* row = in + r * kBoxIC;
+    const int* row = in + r * kBoxInStride;
     int s1 = 0;
     long long s2 = 0;
 #pragma unroll
@@ -123,8 +127,8 @@ __global__ void __launch_bounds__(kBoxThreads)
     }
 #pragma unroll
     for (int c = c0; c < c0 + 8; ++c) {
-      rs1[r * kBoxCols + c] = s1;
-      rs2[r * kBoxCols + c] = s2;
+      rs1[r * kBoxRsStride + c] = s1;
+      rs2[r * kBoxRsStride + c] = s2;
       if (c + 1 < c0 + 8) {
         const int a = row[c + kPatch], b = row[c];
         s1 += a - b;
@@ -133,23 +137,23 @@ __global__ void __launch_bounds__(kBoxThreads)
     }
   }
   __syncthreads();
-  // window sums: 32 columns x 8 chunks of 8 rows
-  const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 8;
+  // window sums: 32 columns x 8 chunks of 7 rows
+  const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 7;
   long long s1 = 0, s2 = 0;
 #pragma unroll
   for (int k = 0; k < kPatch; ++k) {
-    s1 += rs1[(r0 + k) * kBoxCols + c];
-    s2 += rs2[(r0 + k) * kBoxCols + c];
+    s1 += rs1[(r0 + k) * kBoxRsStride + c];
+    s2 += rs2[(r0 + k) * kBoxRsStride + c];
   }
   float* out = isf + (size_t)f * sh * sw;
 #pragma unroll
-  for (int r = r0; r < r0 + 8; ++r) {
+  for (int r = r0; r < r0 + 7; ++r) {
     const int y = by + r, x = bx + c;
     const long long sf = (long long)kPatchArea * s2 - s1 * s1;
     if (y < sh && x < sw) out[(size_t)y * sw + x] = sf > 0 ? rsqrtf((float)sf) : 0.f;
-    if (r + 1 < r0 + 8) {
-      s1 += rs1[(r + kPatch) * kBoxCols + c] - rs1[r * kBoxCols + c];
-      s2 += rs2[(r + kPatch) * kBoxCols + c] - rs2[r * kBoxCols + c];
+    if (r + 1 < r0 + 7) {
+      s1 += rs1[(r + kPatch) * kBoxRsStride + c] - rs1[r * kBoxRsStride + c];
+      s2 += rs2[(r + kPatch) * kBoxRsStride + c] - rs2[r * kBoxRsStride + c];
     }
   }
 }
@@ -183,28 +187,41 @@ cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid
 // ---------------------------------------------------------------------------
 // FP32 correlation numerators on CUDA cores.
 //
-// CTA = (frame, patch row, group of up to kGroup = 11 patches), 12 warps.  The
-// union of the group's search regions (53 rows x (21 G + 2R) cols) is staged in
-// shared memory as exact fp32 integers F - c, with the block of the isf map
-// those windows use.  Each warp owns one output-row pass:
+// Work item = (frame, patch row, group of up to kGroup = 11 patches).  The union
+// of the group's search regions (53 rows x (21 G + 2R) cols) is staged in shared
+// memory as exact fp32 integers F - c, with the block of the isf map those
+// windows use.  Twelve warps then each own one output-row pass:
 //   pass u < G:   lane = dy in 0..31, all lanes on patch u (template loads are
 //                 warp-uniform, frame rows distinct);
 //   pass G:       lane = u, dy = 32 (the 33rd displacement row, when 2R+1 = 33).
 // A lane streams the 21 frame rows it needs: per row 53 shared loads feed
 // 21 x 33 FMAs into 33 register accumulators.  Each finished row is normalised
-// and added in 2^-40 fixed point to a per-CTA int64 surface in shared memory,
-// which the CTA finally adds to the frame's global sums.
+// and added in 2^-40 fixed point to the item's int64 surface in shared memory,
+// which is finally added to the frame's global sums.
+//
+// The kernel is persistent: one CTA per SM with two 12-warp consumer groups,
+// each with its own shared buffers.  Group 1 starts once group 0 has staged its
+// first item, so from then on one group's staging (global-memory latency) runs
+// while the other group computes, and the SM's FMA pipes stay busy.
 constexpr int kGroup = 11;
 constexpr int kCsEntries = kMaxWin * kMaxWin + 1;  // keeps what follows 16-byte aligned
 constexpr int kRegionRows = kPatch + 2 * kMaxR;                     // 53
 constexpr int kRegionStride = (kGroup * kPatch + 2 * kMaxR) | 1;    // 263
 constexpr int kIsfCols = (kGroup - 1) * kPatch + kMaxWin;           // 243
+constexpr int kGroupWarps = kGroup + 1;
+constexpr int kGroupThreads = kGroupWarps * 32;                     // 384
+constexpr int kCorrThreads = 2 * kGroupThreads;                     // 768
+constexpr size_t kGroupSmem = sizeof(unsigned long long) * kCsEntries +
+                              sizeof(float) * kMaxWin * kIsfCols +
+                              sizeof(float) * kRegionRows * kRegionStride;
 
 // floor(i / d) as a multiply-high by m = ceil(2^32 / d): exact for i < 2^32 / d,
 // far above any index here (d <= 263, i < 14,000).
 __device__ __forceinline__ unsigned fast_div(unsigned i, unsigned m) { return __umulhi(i, m); }
-constexpr int kCorrWarps = kGroup + 1;
-constexpr int kCorrThreads = kCorrWarps * 32;
+
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kGroupThreads) : "memory");
+}
 
 template <int NX>
 __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
@@ -232,132 +249,152 @@ __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
 }
 
 template <int NX>
-__global__ void __launch_bounds__(kCorrThreads, 2)
-    k_corr_f32(const uint16_t* __restrict__ frames, int H, int W, PatchGrid g, int R,
+__global__ void __launch_bounds__(kCorrThreads, 1)
+    k_corr_f32(const uint16_t* __restrict__ frames, int nf, int H, int W, PatchGrid g, int R,
                const float* __restrict__ tc, const float* __restrict__ tn2,
                const int* __restrict__ coff, const float* __restrict__ isf,
                unsigned long long* __restrict__ csum) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int f = blockIdx.y, w = 2 * R + 1;
+  const int grp = threadIdx.x / kGroupThreads, gtid = threadIdx.x - grp * kGroupThreads;
+  const int lane = gtid & 31, gwarp = gtid >> 5;
+  unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem + grp * kGroupSmem);
+  float* ism = reinterpret_cast<float*>(cs + kCsEntries);  // [w][scols]
+  float* reg = ism + kMaxWin * kIsfCols;                   // [rows][rs]
+  const int w = 2 * R + 1, rows = kPatch + 2 * R;
   const int groups_per_row = (g.nx + kGroup - 1) / kGroup;
-  const int py = blockIdx.x / groups_per_row, gx = blockIdx.x % groups_per_row;
-  const int px0 = gx * kGroup, G = min(kGroup, g.nx - px0);
-  const int rows = kPatch + 2 * R, cols = G * kPatch + 2 * R;
-  // Rows are allocated for the widest window (a lane always reads 53 values) and
-  // given an odd stride so that lanes on different rows hit distinct banks.
-  const int rs = (G * kPatch + 2 * kMaxR) | 1;  // <= kRegionStride
-  const int scols = (G - 1) * kPatch + w;  // isf columns this CTA uses
-  const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
+  const int items_per_frame = g.ny * groups_per_row, n_items = nf * items_per_frame;
   int oy, ox, sh, sw;
   stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+  const int bar = 1 + grp;  // named barrier of this group (0 is __syncthreads)
 
-  unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem);      // [w][w]
-  float* ism = reinterpret_cast<float*>(cs + kCsEntries);                    // [w][scols]
-  float* reg = ism + kMaxWin * kIsfCols;                                     // [rows][rs]
+  if (grp == 1) asm volatile("bar.sync 3, %0;" ::"r"(kCorrThreads) : "memory");
+  bool released = false;
+  for (int k = grp;; k += 2) {
+    const int item = blockIdx.x + k * gridDim.x;
+    if (item >= n_items) break;
+    const int f = item / items_per_frame, rem = item - f * items_per_frame;
+    const int py = rem / groups_per_row, gx = rem - py * groups_per_row;
+    const int px0 = gx * kGroup, G = min(kGroup, g.nx - px0);
+    const int cols = G * kPatch + 2 * R;
+    // Rows are allocated for the widest window (a lane always reads 53 values) and
+    // given an odd stride so that lanes on different rows hit distinct banks.
+    const int rs = (G * kPatch + 2 * kMaxR) | 1;  // <= kRegionStride
+    const int scols = (G - 1) * kPatch + w;       // isf columns this item uses
+    const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
+    const int p0 = py * g.nx + px0;
+    const float c = (float)coff[p0];
 
-  const int p0 = py * g.nx + px0;
-  const float c = (float)coff[p0];
-  for (int i = threadIdx.x; i < w * w; i += blockDim.x) cs[i] = 0ull;
-  // Stage the frame region and the isf block.  Every thread first issues all of
-  // its global loads (one round trip), then converts and stores.
-  const float* isf_f = isf + (size_t)f * sh * sw + (size_t)(ry - oy) * sw + (rx - ox);
-  const uint16_t* F = frames + (size_t)f * H * W + (size_t)ry * W + rx;
-  {
-    constexpr int kRegLoads = (kRegionRows * kRegionStride + kCorrThreads - 1) / kCorrThreads;
-    constexpr int kHalf = (kRegLoads + 1) / 2;  // two batches keep the registers in budget
-    const unsigned m = 0xffffffffu / (unsigned)rs + 1u;
+    // Stage: every thread first issues its global loads (one round trip per
+    // batch), then converts and stores.
+    for (int i = gtid; i < w * w; i += kGroupThreads) cs[i] = 0ull;
+    const float* isf_f = isf + (size_t)f * sh * sw + (size_t)(ry - oy) * sw + (rx - ox);
+    const uint16_t* F = frames + (size_t)f * H * W + (size_t)ry * W + rx;
+    {
+      constexpr int kRegLoads = (kRegionRows * kRegionStride + kGroupThreads - 1) / kGroupThreads;
+      constexpr int kBatches = 3;  // batches of loads keep the registers in budget
+      constexpr int kHalf = (kRegLoads + kBatches - 1) / kBatches;
+      const unsigned m = 0xffffffffu / (unsigned)rs + 1u;
+#pragma unroll 1
+      for (int b = 0; b < kBatches; ++b) {
+        unsigned short v[kHalf];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      unsigned short v[kHalf];
+        for (int q = 0; q < kHalf; ++q) {
+          const int i = gtid + (b * kHalf + q) * kGroupThreads;
+          const int r = (int)fast_div((unsigned)i, m), x = i - r * rs;
+          v[q] = (i < rows * rs && x < cols) ? __ldg(F + (size_t)r * W + x) : (unsigned short)0;
+        }
 #pragma unroll
-      for (int k = 0; k < kHalf; ++k) {
-        const int i = threadIdx.x + (b * kHalf + k) * kCorrThreads;
-        const int r = (int)fast_div((unsigned)i, m), x = i - r * rs;
-        v[k] = (i < rows * rs && x < cols) ? __ldg(F + (size_t)r * W + x) : (unsigned short)0;
-      }
-#pragma unroll
-      for (int k = 0; k < kHalf; ++k) {
-        const int i = threadIdx.x + (b * kHalf + k) * kCorrThreads;
-        const int x = i - (int)fast_div((unsigned)i, m) * rs;
-        if (i < rows * rs) reg[i] = x < cols ? (float)v[k] - c : 0.f;
-      }
-    }
-  }
-  {
-    constexpr int kIsfLoads = (kMaxWin * kIsfCols + kCorrThreads - 1) / kCorrThreads;  // 21
-    const unsigned m = 0xffffffffu / (unsigned)scols + 1u;
-    float v[kIsfLoads];
-#pragma unroll
-    for (int k = 0; k < kIsfLoads; ++k) {
-      const int i = threadIdx.x + k * kCorrThreads;
-      const int r = (int)fast_div((unsigned)i, m), x = i - r * scols;
-      v[k] = i < w * scols ? __ldg(isf_f + (size_t)r * sw + x) : 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < kIsfLoads; ++k) {
-      const int i = threadIdx.x + k * kCorrThreads;
-      if (i < w * scols) ism[i] = v[k];
-    }
-  }
-  __syncthreads();
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n_pass = G + (w > 32 ? 1 : 0);
-  for (int pass = warp; pass < n_pass; pass += kCorrWarps) {
-    int u, dy;
-    if (pass < G) {
-      u = pass;
-      dy = lane;
-    } else {
-      u = lane;
-      dy = 32;
-    }
-    const bool active = u < G && dy < w;
-    const int uu = active ? u : 0, dd = active ? dy : 0;
-    float acc[NX];
-    corr_row<NX>(reg + dd * rs + uu * kPatch, rs, tc + (size_t)(p0 + uu) * kPatch * kTplStride,
-                 acc);
-    if (active) {
-      const float t2 = __ldg(tn2 + p0 + uu);
-      const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
-      const float* iv = ism + dd * scols + uu * kPatch;
-      unsigned long long* crow = cs + dd * w;
-#pragma unroll
-      for (int j = 0; j < NX; ++j) {
-        if (j < w) {
-          const float z = acc[j] * pscale * iv[j];
-          atomicAdd(crow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
+        for (int q = 0; q < kHalf; ++q) {
+          const int i = gtid + (b * kHalf + q) * kGroupThreads;
+          const int x = i - (int)fast_div((unsigned)i, m) * rs;
+          if (i < rows * rs) reg[i] = x < cols ? (float)v[q] - c : 0.f;
         }
       }
     }
+    {
+      constexpr int kIsfLoads = (kMaxWin * kIsfCols + kGroupThreads - 1) / kGroupThreads;
+      constexpr int kIsfHalf = (kIsfLoads + 1) / 2;
+      const unsigned m = 0xffffffffu / (unsigned)scols + 1u;
+#pragma unroll 1
+      for (int b = 0; b < 2; ++b) {
+        float v[kIsfHalf];
+#pragma unroll
+        for (int q = 0; q < kIsfHalf; ++q) {
+          const int i = gtid + (b * kIsfHalf + q) * kGroupThreads;
+          const int r = (int)fast_div((unsigned)i, m), x = i - r * scols;
+          v[q] = i < w * scols ? __ldg(isf_f + (size_t)r * sw + x) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kIsfHalf; ++q) {
+          const int i = gtid + (b * kIsfHalf + q) * kGroupThreads;
+          if (i < w * scols) ism[i] = v[q];
+        }
+      }
+    }
+    group_sync(bar);
+    if (grp == 0 && !released) {  // let group 1 start staging now
+      asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
+      released = true;
+    }
+    // One output-row pass per warp.
+    const int n_pass = G + (w > 32 ? 1 : 0);
+    for (int pass = gwarp; pass < n_pass; pass += kGroupWarps) {
+      int u, dy;
+      if (pass < G) {
+        u = pass;
+        dy = lane;
+      } else {
+        u = lane;
+        dy = 32;
+      }
+      const bool active = u < G && dy < w;
+      const int uu = active ? u : 0, dd = active ? dy : 0;
+      float acc[NX];
+      corr_row<NX>(reg + dd * rs + uu * kPatch, rs, tc + (size_t)(p0 + uu) * kPatch * kTplStride,
+                   acc);
+      if (active) {
+        const float t2 = __ldg(tn2 + p0 + uu);
+        const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+        const float* iv = ism + dd * scols + uu * kPatch;
+        unsigned long long* crow = cs + dd * w;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          if (j < w) {
+            const float z = acc[j] * pscale * iv[j];
+            atomicAdd(crow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
+          }
+        }
+      }
+    }
+    group_sync(bar);
+    unsigned long long* out = csum + (size_t)f * w * w;
+    for (int i = gtid; i < w * w; i += kGroupThreads) atomicAdd(out + i, cs[i]);
+    group_sync(bar);
   }
-  __syncthreads();
-  unsigned long long* out = csum + (size_t)f * w * w;
-  for (int i = threadIdx.x; i < w * w; i += blockDim.x) atomicAdd(out + i, cs[i]);
-}
-
-static size_t corr_smem_bytes(int R) {
-  const int rows = kPatch + 2 * R;
-  return sizeof(unsigned long long) * kCsEntries + sizeof(float) * kMaxWin * kIsfCols +
-         sizeof(float) * rows * kRegionStride;
+  if (grp == 0 && !released) asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
 }
 
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
                             unsigned long long* csum, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
-  const size_t smem = corr_smem_bytes(R);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)corr_smem_bytes(kMaxR));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(2 * kGroupSmem));
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
   }
-  const int groups = g.ny * ((g.nx + kGroup - 1) / kGroup);
-  k_corr_f32<kMaxWin><<<dim3(groups, nf), kCorrThreads, smem, st>>>(
-      frames, H, W, g, R, td.tc, td.tn2, td.coff, isf, csum);
+  const int items = nf * g.ny * ((g.nx + kGroup - 1) / kGroup);
+  const int grid = std::min(sms, (items + 1) / 2);
+  k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(frames, nf, H, W, g, R, td.tc,
+                                                                  td.tn2, td.coff, isf, csum);
   return cudaGetLastError();
 }
 
