@@ -151,6 +151,53 @@ int vimg_reset(vimg_handle* h);
  * this host thread when h is NULL.  Never NULL. */
 const char* vimg_last_error(const vimg_handle* h);
 
+/* ---- Learned shift proposal -------------------------------------------------
+ * A 6-layer CNN (3x3 convolutions, 32 channels, stride 2 in layers 1-5, ReLU,
+ * global average pool, linear 32 -> 2) reads the 128x128 centre crops of the
+ * frame and of the template (each normalised by its own mean and standard
+ * deviation) and regresses the frame's shift.  With VIMG_PROPOSAL_CNN the
+ * correlation of Sec. II then runs only on the 7x7 displacements around the
+ * rounded proposal (+-2 px plus a refinement ring); a frame whose peak lies on
+ * that window's border or whose C(d*) is below params.fallback_zncc is searched
+ * again over the full +-R window (a device-side list, no host round trip).
+ * Weights are used in BF16 with FP32 accumulation; training keeps FP32 master
+ * weights.  The paper's own network is a segmentation U-Net; this proposal
+ * network is an addition of this library.  All pointers are device pointers;
+ * all calls enqueue on `stream` and return VIMG_OK or an error code.
+ * Parameter layout (floats): per convolution weights [32][c_in][3][3] then
+ * bias [32] (c_in = 2 for the first layer, 32 after), then the linear weights
+ * [2][32] and bias [2].  Network output = shift / 12 px. */
+int vimg_cnn_param_count(void);
+/* Floats of activation workspace for a batch of n samples. */
+size_t vimg_cnn_workspace_floats(int n);
+/* Writes the normalised input crops of n frames [n][H][W] (H, W >= 128) into
+ * the start of the workspace d_ws.  The template of sample b is d_template +
+ * b * template_stride (template_stride = 0: one template [H][W] for all). */
+int vimg_cnn_prepare(const uint16_t* d_frames, int n, int H, int W, const float* d_template,
+                     long long template_stride, float* d_ws, void* stream);
+/* BF16 copy of the parameters (d_params_bf16: vimg_cnn_param_count() bf16). */
+int vimg_cnn_pack_bf16(const float* d_params, void* d_params_bf16, void* stream);
+/* Forward of the prepared batch: d_out [n][2] (shift / 12), activations kept
+ * in d_ws for the backward pass. */
+int vimg_cnn_forward(const float* d_params, const void* d_params_bf16, float* d_ws, int n,
+                     float* d_out, void* stream);
+/* Mean squared error against d_target [n][2] (px): d_dout [n][2] and, if
+ * d_loss is not NULL, the loss (one float). */
+int vimg_cnn_loss(const float* d_out, const float* d_target, int n, float* d_dout, float* d_loss,
+                  void* stream);
+/* Backward pass: adds the parameter gradients to d_grads (zero it first);
+ * d_dws is a second workspace of vimg_cnn_workspace_floats(n) floats. */
+int vimg_cnn_backward(const float* d_params, const void* d_params_bf16, const float* d_ws,
+                      float* d_dws, int n, const float* d_dout, float* d_grads, void* stream);
+/* One Adam step (bias-corrected, step counts from 1) on the FP32 parameters. */
+int vimg_cnn_adam(float* d_params, const float* d_grads, float* d_m, float* d_v, float lr,
+                  float beta1, float beta2, float eps, int step, void* stream);
+/* Copies trained FP32 parameters into the handle (kept as BF16 for inference). */
+int vimg_load_proposal(vimg_handle* h, const float* d_params);
+/* Frames estimated and frames that fell back to the full window since the
+ * handle was created (synchronises the handle's stream). */
+int vimg_proposal_stats(vimg_handle* h, long long* frames, long long* fallbacks);
+
 /* Per-stage timing with CUDA events recorded around each of the library's
  * launches on params.stream (off by default).  Stages:
  *   0 window statistics, 1 correlation numerators, 2 peak + refinement,

@@ -43,6 +43,18 @@ struct vimg_handle {
   cudaStream_t st = nullptr;
   TemplateDev td{};
   bool have_template = false;
+  float* tmpl = nullptr;                // [H][W] copy of the template
+  // learned proposal
+  bool have_proposal = false;
+  float* cnn_p = nullptr;               // FP32 parameters
+  __nv_bfloat16* cnn_b = nullptr;       // BF16 copy used for inference
+  float* cnn_acts = nullptr;            // [cnn_act_floats(max_chunk)]
+  float* prop = nullptr;                // [max_chunk][2] network output
+  unsigned long long* csum_n = nullptr; // [max_chunk][49] narrow-window sums
+  int* fb_list = nullptr;               // [max_chunk] frames falling back
+  int* fb_n = nullptr;                  // [1]
+  long long* fb_total = nullptr;        // [1] fallbacks since creation
+  long long prop_frames = 0;
   float gw[2 * kGaussMaxRadius + 1] = {};
   float* inv = nullptr;                 // [max_chunk][stats map] 1/sqrt(SF) per window
   unsigned long long* csum = nullptr;   // [max_chunk][nwin]
@@ -129,7 +141,9 @@ static bool grid_for(int H, int W, int R, PatchGrid* g) {
 static void free_all(vimg_handle* h) {
   void* ptrs[] = {h->td.tc, h->td.tn2, h->td.coff, h->inv, h->csum, h->shift_tmp,
                   h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
-                  h->stage[0], h->stage[1], h->stage_shift, h->stage_summary};
+                  h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
+                  h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
+                  h->fb_total};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
@@ -183,8 +197,14 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     fail(nullptr, VIMG_ERR_ARG, "unknown flag bits");
     return nullptr;
   }
-  if (p.flags & (VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN)) {
-    fail(nullptr, VIMG_ERR_ARG, "VIMG_CORR_BF16 / VIMG_PROPOSAL_CNN are not available in this build");
+  if (p.flags & VIMG_CORR_BF16) {
+    fail(nullptr, VIMG_ERR_ARG, "VIMG_CORR_BF16 is not available in this build");
+    return nullptr;
+  }
+  if ((p.flags & VIMG_PROPOSAL_CNN) &&
+      (H < kCrop || W < kCrop || p.search_radius < kNarrowWin / 2 + 1 || !(p.fallback_zncc <= 1.f))) {
+    fail(nullptr, VIMG_ERR_ARG,
+         "VIMG_PROPOSAL_CNN needs H, W >= 128, search_radius >= 4 and fallback_zncc <= 1");
     return nullptr;
   }
   PatchGrid g;
@@ -220,6 +240,18 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
   for (int i = 0; i < 2; ++i) {
     ALLOC(h->carry[i], sizeof(uint16_t) * HW * std::max(1, h->carry_cap));
     ALLOC(h->carry_shift[i], sizeof(float) * 2 * std::max(1, h->carry_cap));
+  }
+  ALLOC(h->tmpl, sizeof(float) * HW);
+  if (p.flags & VIMG_PROPOSAL_CNN) {
+    ALLOC(h->cnn_p, sizeof(float) * cnn_param_count());
+    ALLOC(h->cnn_b, sizeof(__nv_bfloat16) * cnn_param_count());
+    ALLOC(h->cnn_acts, sizeof(float) * cnn_act_floats(p.max_chunk));
+    ALLOC(h->prop, sizeof(float) * 2 * (size_t)p.max_chunk);
+    ALLOC(h->csum_n, sizeof(unsigned long long) * kNarrowWin * kNarrowWin * (size_t)p.max_chunk);
+    ALLOC(h->fb_list, sizeof(int) * (size_t)p.max_chunk);
+    ALLOC(h->fb_n, sizeof(int));
+    ALLOC(h->fb_total, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(h->fb_total, 0, sizeof(long long));
   }
 #undef ALLOC
   if (e != cudaSuccess) {
@@ -259,6 +291,9 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
   if (!h || !d_template) return fail(h, VIMG_ERR_ARG, "null handle or template");
   if (h->sticky) return h->sticky;
   CK(launch_template_prep(d_template, h->H, h->W, h->g, h->td, h->st), "template prep launch");
+  CK(cudaMemcpyAsync(h->tmpl, d_template, sizeof(float) * h->H * h->W, cudaMemcpyDeviceToDevice,
+                     h->st),
+     "template copy");
   h->have_template = true;
   return VIMG_OK;
 }
@@ -269,6 +304,43 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
   const int R = h->p.search_radius;
   CK(cudaMemsetAsync(h->csum, 0, sizeof(unsigned long long) * (size_t)nf * h->nwin, h->st),
      "surface reset");
+  if (h->p.flags & VIMG_PROPOSAL_CNN) {
+    // learned proposal -> narrow window -> full window for the listed frames
+    int ps = prof_begin(h, 4);
+    CK(cnn_input(frames, nf, h->H, h->W, h->tmpl, 0, h->cnn_acts, h->st), "proposal input");
+    CK(cnn_forward(h->cnn_p, h->cnn_b, h->cnn_acts, nf, h->prop, h->st), "proposal forward");
+    prof_end(h, ps);
+    ps = prof_begin(h, 0);
+    CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st),
+       "window statistics launch");
+    prof_end(h, ps);
+    CK(cudaMemsetAsync(h->csum_n, 0, sizeof(unsigned long long) * kNarrowWin * kNarrowWin * nf,
+                       h->st),
+       "narrow surface reset");
+    CK(cudaMemsetAsync(h->fb_n, 0, sizeof(int), h->st), "list reset");
+    ps = prof_begin(h, 1);
+    CK(launch_corr_narrow(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->prop, h->csum_n,
+                          h->st),
+       "narrow correlation launch");
+    prof_end(h, ps);
+    ps = prof_begin(h, 2);
+    CK(launch_peak_narrow(h->csum_n, nf, R, h->np, h->prop, h->p.fallback_zncc, shifts, peak_info,
+                          h->fb_list, h->fb_n, h->st),
+       "narrow peak launch");
+    prof_end(h, ps);
+    ps = prof_begin(h, 1);
+    CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st, h->fb_list,
+                       h->fb_n),
+       "fallback correlation launch");
+    prof_end(h, ps);
+    ps = prof_begin(h, 2);
+    CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, nullptr, h->st, h->fb_list, h->fb_n),
+       "fallback peak launch");
+    prof_end(h, ps);
+    CK(launch_count_add(h->fb_n, h->fb_total, h->st), "fallback count");
+    h->prop_frames += nf;
+    return VIMG_OK;
+  }
   // One launch per stage for the whole batch: thousands of CTAs, so the last
   // partial wave costs little.
   int ps = prof_begin(h, 0);
@@ -359,6 +431,8 @@ extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, 
   if (n < 0 || (n > 0 && !d_frames) || !io) return fail(h, VIMG_ERR_ARG, "bad frames or io");
   if (!io->shifts_in && !h->have_template)
     return fail(h, VIMG_ERR_NO_TEMPLATE, "vimg_set_template must come before vimg_process");
+  if (!io->shifts_in && (h->p.flags & VIMG_PROPOSAL_CNN) && !h->have_proposal)
+    return fail(h, VIMG_ERR_ARG, "vimg_load_proposal must come before vimg_process");
   const size_t HW = (size_t)h->H * h->W;
   const int L = h->p.segment_len, maxc = h->p.max_chunk;
   int done = 0, k_total = 0;
@@ -481,5 +555,88 @@ extern "C" int vimg_profile_read(vimg_handle* h, double* ms, long long* launches
     if (launches) launches[i] = p.launches[i];
     if (reset) p.ms[i] = 0.0, p.launches[i] = 0;
   }
+  return VIMG_OK;
+}
+
+extern "C" int vimg_cnn_param_count(void) { return cnn_param_count(); }
+
+extern "C" size_t vimg_cnn_workspace_floats(int n) { return n > 0 ? cnn_act_floats(n) : 0; }
+
+static int cnn_status(cudaError_t e) {
+  if (e != cudaSuccess) {
+    g_create_error = std::string("proposal kernel: ") + cudaGetErrorString(e);
+    return VIMG_ERR_CUDA;
+  }
+  return VIMG_OK;
+}
+
+extern "C" int vimg_cnn_prepare(const uint16_t* d_frames, int n, int H, int W,
+                                const float* d_template, long long template_stride, float* d_ws,
+                                void* stream) {
+  if (n < 0 || (n > 0 && (!d_frames || !d_template || !d_ws)) || H < kCrop || W < kCrop)
+    return VIMG_ERR_ARG;
+  return cnn_status(cnn_input(d_frames, n, H, W, d_template, template_stride, d_ws,
+                              (cudaStream_t)stream));
+}
+
+extern "C" int vimg_cnn_pack_bf16(const float* d_params, void* d_params_bf16, void* stream) {
+  if (!d_params || !d_params_bf16) return VIMG_ERR_ARG;
+  return cnn_status(cnn_to_bf16(d_params, (__nv_bfloat16*)d_params_bf16, (cudaStream_t)stream));
+}
+
+extern "C" int vimg_cnn_forward(const float* d_params, const void* d_params_bf16, float* d_ws,
+                                int n, float* d_out, void* stream) {
+  if (!d_params || !d_params_bf16 || !d_ws || !d_out || n < 1) return VIMG_ERR_ARG;
+  return cnn_status(cnn_forward(d_params, (const __nv_bfloat16*)d_params_bf16, d_ws, n, d_out,
+                                (cudaStream_t)stream));
+}
+
+extern "C" int vimg_cnn_loss(const float* d_out, const float* d_target, int n, float* d_dout,
+                             float* d_loss, void* stream) {
+  if (!d_out || !d_target || !d_dout || n < 1) return VIMG_ERR_ARG;
+  return cnn_status(cnn_mse(d_out, d_target, n, d_dout, d_loss, (cudaStream_t)stream));
+}
+
+extern "C" int vimg_cnn_backward(const float* d_params, const void* d_params_bf16,
+                                 const float* d_ws, float* d_dws, int n, const float* d_dout,
+                                 float* d_grads, void* stream) {
+  if (!d_params || !d_params_bf16 || !d_ws || !d_dws || !d_dout || !d_grads || n < 1)
+    return VIMG_ERR_ARG;
+  return cnn_status(cnn_backward(d_params, (const __nv_bfloat16*)d_params_bf16, d_ws, d_dws, n,
+                                 d_dout, d_grads, (cudaStream_t)stream));
+}
+
+extern "C" int vimg_cnn_adam(float* d_params, const float* d_grads, float* d_m, float* d_v,
+                             float lr, float beta1, float beta2, float eps, int step,
+                             void* stream) {
+  if (!d_params || !d_grads || !d_m || !d_v || step < 1) return VIMG_ERR_ARG;
+  return cnn_status(cnn_adam(d_params, d_grads, d_m, d_v, lr, beta1, beta2, eps, step,
+                             (cudaStream_t)stream));
+}
+
+extern "C" int vimg_load_proposal(vimg_handle* h, const float* d_params) {
+  if (!h || !d_params) return fail(h, VIMG_ERR_ARG, "null handle or parameters");
+  if (h->sticky) return h->sticky;
+  if (!(h->p.flags & VIMG_PROPOSAL_CNN))
+    return fail(h, VIMG_ERR_ARG, "handle was created without VIMG_PROPOSAL_CNN");
+  CK(cudaMemcpyAsync(h->cnn_p, d_params, sizeof(float) * cnn_param_count(),
+                     cudaMemcpyDeviceToDevice, h->st),
+     "proposal copy");
+  CK(cnn_to_bf16(h->cnn_p, h->cnn_b, h->st), "proposal pack");
+  h->have_proposal = true;
+  return VIMG_OK;
+}
+
+extern "C" int vimg_proposal_stats(vimg_handle* h, long long* frames, long long* fallbacks) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  long long fb = 0;
+  if (h->fb_total) {
+    CK(cudaMemcpyAsync(&fb, h->fb_total, sizeof(long long), cudaMemcpyDeviceToHost, h->st),
+       "stats copy");
+    CK(cudaStreamSynchronize(h->st), "stream sync");
+  }
+  if (frames) *frames = h->prop_frames;
+  if (fallbacks) *fallbacks = fb;
   return VIMG_OK;
 }

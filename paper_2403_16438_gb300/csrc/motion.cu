@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
     k_corr_f32(const uint16_t* __restrict__ frames, int nf, int H, int W, PatchGrid g, int R,
                const float* __restrict__ tc, const float* __restrict__ tn2,
                const int* __restrict__ coff, const float* __restrict__ isf,
-               unsigned long long* __restrict__ csum) {
+               unsigned long long* __restrict__ csum, const int* __restrict__ list,
+               const int* __restrict__ list_n) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int grp = threadIdx.x / kGroupThreads, gtid = threadIdx.x - grp * kGroupThreads;
   const int lane = gtid & 31, gwarp = gtid >> 5;
@@ -262,7 +263,10 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   float* reg = ism + kMaxWin * kIsfCols;                   // [rows][rs]
   const int w = 2 * R + 1, rows = kPatch + 2 * R;
   const int groups_per_row = (g.nx + kGroup - 1) / kGroup;
-  const int items_per_frame = g.ny * groups_per_row, n_items = nf * items_per_frame;
+  // With a frame list (fallback frames of the learned proposal) only the listed
+  // frames are processed; their count is read from device memory.
+  const int n_frames = list ? min(nf, *list_n) : nf;
+  const int items_per_frame = g.ny * groups_per_row, n_items = n_frames * items_per_frame;
   int oy, ox, sh, sw;
   stats_map_dims(g, R, &oy, &ox, &sh, &sw);
   const int bar = 1 + grp;  // named barrier of this group (0 is __syncthreads)
@@ -272,7 +276,8 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   for (int k = grp;; k += 2) {
     const int item = blockIdx.x + k * gridDim.x;
     if (item >= n_items) break;
-    const int f = item / items_per_frame, rem = item - f * items_per_frame;
+    const int fi = item / items_per_frame, rem = item - fi * items_per_frame;
+    const int f = list ? list[fi] : fi;
     const int py = rem / groups_per_row, gx = rem - py * groups_per_row;
     const int px0 = gx * kGroup, G = min(kGroup, g.nx - px0);
     const int cols = G * kPatch + 2 * R;
@@ -376,7 +381,8 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
 
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
-                            unsigned long long* csum, cudaStream_t st) {
+                            unsigned long long* csum, cudaStream_t st, const int* list,
+                            const int* list_n) {
   if (nf <= 0) return cudaSuccess;
   static int sms = 0;
   if (!sms) {
@@ -393,8 +399,8 @@ cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchG
   }
   const int items = nf * g.ny * ((g.nx + kGroup - 1) / kGroup);
   const int grid = std::min(sms, (items + 1) / 2);
-  k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(frames, nf, H, W, g, R, td.tc,
-                                                                  td.tn2, td.coff, isf, csum);
+  k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(
+      frames, nf, H, W, g, R, td.tc, td.tn2, td.coff, isf, csum, list, list_n);
   return cudaGetLastError();
 }
 
@@ -424,15 +430,16 @@ __device__ __forceinline__ Cand warp_best(Cand c) {
   return c;
 }
 
-__global__ void k_peak(const unsigned long long* __restrict__ csum, int R, int np,
-                       float* __restrict__ shifts, float* __restrict__ info,
-                       double* __restrict__ surface) {
-  const int f = blockIdx.x, lane = threadIdx.x, w = 2 * R + 1, nw = w * w;
-  const long long* C = reinterpret_cast<const long long*>(csum) + (size_t)f * nw;
+// Integer peak (with the tie-break) and parabola over a wy x wx surface whose
+// (0,0) entry is displacement (oy, ox).  Writes the shift, the peak info and,
+// for the full window, the surface.  Returns the flat index of d*.
+__device__ __forceinline__ int peak_of(const long long* C, int wy, int wx, int oy, int ox, int np,
+                                       int lane, Cand& best, Cand& second, float s[2]) {
   const Cand none = {LLONG_MIN, 0x7fffffff, -1};
+  const int nw = wy * wx;
   Cand b = none;
   for (int i = lane; i < nw; i += 32) {
-    const int dy = i / w - R, dx = i % w - R;
+    const int dy = i / wx + oy, dx = i % wx + ox;
     Cand c = {C[i], ((dy * dy + dx * dx) << 12) | ((dy + 16) << 6) | (dx + 16), i};
     if (better(c, b)) b = c;
   }
@@ -440,35 +447,53 @@ __global__ void k_peak(const unsigned long long* __restrict__ csum, int R, int n
   Cand s2 = none;
   for (int i = lane; i < nw; i += 32) {
     if (i == b.idx) continue;
-    const int dy = i / w - R, dx = i % w - R;
+    const int dy = i / wx + oy, dx = i % wx + ox;
     Cand c = {C[i], ((dy * dy + dx * dx) << 12) | ((dy + 16) << 6) | (dx + 16), i};
     if (better(c, s2)) s2 = c;
   }
   s2 = warp_best(s2);
+  const int iy = b.idx / wx, ix = b.idx % wx;
+  s[0] = (float)(iy + oy);
+  s[1] = (float)(ix + ox);
+  for (int ax = 0; ax < 2; ++ax) {
+    const int i = ax == 0 ? iy : ix, n = ax == 0 ? wy : wx;
+    if (i == 0 || i == n - 1) continue;
+    const int step = ax == 0 ? wx : 1;
+    const long long cm = C[b.idx - step], cp = C[b.idx + step], c0 = C[b.idx];
+    const long long den = cm - 2 * c0 + cp;
+    if (den >= 0) continue;
+    float d = (float)(cm - cp) / (2.0f * (float)den);
+    d = fminf(0.5f, fmaxf(-0.5f, d));
+    s[ax] += d;
+  }
+  best = b;
+  second = s2;
+  (void)np;
+  return b.idx;
+}
+
+__global__ void k_peak(const unsigned long long* __restrict__ csum, int R, int np,
+                       float* __restrict__ shifts, float* __restrict__ info,
+                       double* __restrict__ surface, const int* __restrict__ list,
+                       const int* __restrict__ list_n) {
+  if (list && (int)blockIdx.x >= *list_n) return;
+  const int f = list ? list[blockIdx.x] : blockIdx.x;
+  const int lane = threadIdx.x, w = 2 * R + 1, nw = w * w;
+  const long long* C = reinterpret_cast<const long long*>(csum) + (size_t)f * nw;
+  Cand b, s2;
+  float s[2];
+  peak_of(C, w, w, -R, -R, np, lane, b, s2, s);
   if (surface) {
     for (int i = lane; i < nw; i += 32) surface[(size_t)f * nw + i] = (double)C[i] / kFix / np;
   }
   if (lane == 0) {
-    const int iy = b.idx / w, ix = b.idx % w;
-    float s[2] = {(float)(iy - R), (float)(ix - R)};
-    for (int ax = 0; ax < 2; ++ax) {
-      const int i = ax == 0 ? iy : ix;
-      if (i == 0 || i == w - 1) continue;
-      const int step = ax == 0 ? w : 1;
-      const long long cm = C[b.idx - step], cp = C[b.idx + step], c0 = C[b.idx];
-      const long long den = cm - 2 * c0 + cp;
-      if (den >= 0) continue;
-      float d = (float)(cm - cp) / (2.0f * (float)den);
-      d = fminf(0.5f, fmaxf(-0.5f, d));
-      s[ax] += d;
-    }
     if (shifts) {
       shifts[2 * f] = s[0];
       shifts[2 * f + 1] = s[1];
     }
     if (info) {
-      info[4 * f + 0] = (float)(iy - R);
-      info[4 * f + 1] = (float)(ix - R);
+      info[4 * f + 0] = (float)(b.idx / w - R);
+      info[4 * f + 1] = (float)(b.idx % w - R);
       info[4 * f + 2] = (float)((double)b.v / kFix / np);
       info[4 * f + 3] = s2.idx >= 0 ? (float)((double)s2.v / kFix / np) : 0.f;
     }
@@ -476,9 +501,144 @@ __global__ void k_peak(const unsigned long long* __restrict__ csum, int R, int n
 }
 
 cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, float* shifts,
-                        float* peak_info, double* surface, cudaStream_t st) {
+                        float* peak_info, double* surface, cudaStream_t st, const int* list,
+                        const int* list_n) {
   if (nf <= 0) return cudaSuccess;
-  k_peak<<<nf, 32, 0, st>>>(csum, R, np, shifts, peak_info, surface);
+  k_peak<<<nf, 32, 0, st>>>(csum, R, np, shifts, peak_info, surface, list, list_n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Narrow window around a proposed shift p_t (learned proposal): the 7x7
+// displacements centred on c_t = round(p_t) (clamped so the window stays in
+// [-R, R]^2), i.e. +-2 px plus a one-pixel ring for the refinement.  CTA = 16
+// patches x 8 lanes (lane = displacement row), the frame read through the
+// read-only cache.  Same normalisation and fixed-point sums as the full window.
+constexpr int kNarrow = kNarrowWin;  // 7
+constexpr int kNarrowPatches = 16;
+
+__device__ __forceinline__ void narrow_center(const float* prop, int f, int R, int& cy, int& cx) {
+  // prop holds the network output (shift / kShiftScale)
+  const int lim = R - kNarrow / 2;
+  const float py = prop[2 * f] * kShiftScale, px = prop[2 * f + 1] * kShiftScale;
+  cy = isfinite(py) ? (int)rintf(fmaxf(-64.f, fminf(64.f, py))) : 0;
+  cx = isfinite(px) ? (int)rintf(fmaxf(-64.f, fminf(64.f, px))) : 0;
+  cy = max(-lim, min(lim, cy));
+  cx = max(-lim, min(lim, cx));
+}
+
+__global__ void __launch_bounds__(kNarrowPatches * 8)
+    k_corr_narrow(const uint16_t* __restrict__ frames, int H, int W, PatchGrid g, int R,
+                  const float* __restrict__ tc, const float* __restrict__ tn2,
+                  const float* __restrict__ isf, const float* __restrict__ prop,
+                  unsigned long long* __restrict__ csum) {
+  __shared__ unsigned long long cs[kNarrow * kNarrow];
+  const int f = blockIdx.y, np = g.ny * g.nx;
+  const int u = threadIdx.x >> 3, dy = threadIdx.x & 7;
+  const int p = blockIdx.x * kNarrowPatches + u;
+  int cy, cx;
+  narrow_center(prop, f, R, cy, cx);
+  const int wy0 = cy - kNarrow / 2, wx0 = cx - kNarrow / 2;
+  for (int i = threadIdx.x; i < kNarrow * kNarrow; i += blockDim.x) cs[i] = 0ull;
+  __syncthreads();
+  if (p < np && dy < kNarrow) {
+    const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
+    const uint16_t* F = frames + (size_t)f * H * W + (size_t)(ty + wy0 + dy) * W + tx + wx0;
+    const float* trow = tc + (size_t)p * kPatch * kTplStride;
+    float acc[kNarrow];
+#pragma unroll
+    for (int j = 0; j < kNarrow; ++j) acc[j] = 0.f;
+#pragma unroll 1
+    for (int ky = 0; ky < kPatch; ++ky) {
+      float fr[kNarrow + kPatch - 1];
+#pragma unroll
+      for (int i = 0; i < kNarrow + kPatch - 1; ++i) fr[i] = __ldg(F + i);
+      float t[kTplStride];
+#pragma unroll
+      for (int i = 0; i < kTplStride; i += 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(trow + i));
+        t[i] = v.x, t[i + 1] = v.y, t[i + 2] = v.z, t[i + 3] = v.w;
+      }
+#pragma unroll
+      for (int kx = 0; kx < kPatch; ++kx)
+#pragma unroll
+        for (int j = 0; j < kNarrow; ++j) acc[j] = fmaf(t[kx], fr[j + kx], acc[j]);
+      F += W;
+      trow += kTplStride;
+    }
+    int oy, ox, sh, sw;
+    stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+    const float t2 = __ldg(tn2 + p);
+    const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+    const float* iv = isf + (size_t)f * sh * sw + (size_t)(ty + wy0 + dy - oy) * sw + (tx + wx0 - ox);
+#pragma unroll
+    for (int j = 0; j < kNarrow; ++j) {
+      const float z = acc[j] * pscale * __ldg(iv + j);
+      atomicAdd(cs + dy * kNarrow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
+    }
+  }
+  __syncthreads();
+  unsigned long long* out = csum + (size_t)f * kNarrow * kNarrow;
+  for (int i = threadIdx.x; i < kNarrow * kNarrow; i += blockDim.x) atomicAdd(out + i, cs[i]);
+}
+
+// Peak of the narrow window.  Falls back to the full window (frame appended to
+// the device-side list) when d* lies on the 7x7 border or C(d*) < threshold.
+__global__ void k_peak_narrow(const unsigned long long* __restrict__ csum, int R, int np,
+                              const float* __restrict__ prop, float thresh,
+                              float* __restrict__ shifts, float* __restrict__ info,
+                              int* __restrict__ list, int* __restrict__ list_n) {
+  const int f = blockIdx.x, lane = threadIdx.x, nw = kNarrow * kNarrow;
+  const long long* C = reinterpret_cast<const long long*>(csum) + (size_t)f * nw;
+  int cy, cx;
+  narrow_center(prop, f, R, cy, cx);
+  Cand b, s2;
+  float s[2];
+  peak_of(C, kNarrow, kNarrow, cy - kNarrow / 2, cx - kNarrow / 2, np, lane, b, s2, s);
+  if (lane != 0) return;
+  const int iy = b.idx / kNarrow, ix = b.idx % kNarrow;
+  const float cpk = (float)((double)b.v / kFix / np);
+  const bool edge = iy == 0 || ix == 0 || iy == kNarrow - 1 || ix == kNarrow - 1;
+  if (edge || cpk < thresh) {
+    list[atomicAdd(list_n, 1)] = f;
+    return;
+  }
+  if (shifts) {
+    shifts[2 * f] = s[0];
+    shifts[2 * f + 1] = s[1];
+  }
+  if (info) {
+    info[4 * f + 0] = (float)(iy + cy - kNarrow / 2);
+    info[4 * f + 1] = (float)(ix + cx - kNarrow / 2);
+    info[4 * f + 2] = cpk;
+    info[4 * f + 3] = s2.idx >= 0 ? (float)((double)s2.v / kFix / np) : 0.f;
+  }
+}
+
+cudaError_t launch_corr_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                               const TemplateDev& td, const float* isf, const float* prop,
+                               unsigned long long* csum, cudaStream_t st) {
+  if (nf <= 0) return cudaSuccess;
+  const int np = g.ny * g.nx;
+  k_corr_narrow<<<dim3((np + kNarrowPatches - 1) / kNarrowPatches, nf), kNarrowPatches * 8, 0, st>>>(
+      frames, H, W, g, R, td.tc, td.tn2, isf, prop, csum);
+  return cudaGetLastError();
+}
+
+__global__ void k_count_add(const int* __restrict__ n, long long* __restrict__ total) {
+  *total += *n;
+}
+
+cudaError_t launch_count_add(const int* n, long long* total, cudaStream_t st) {
+  k_count_add<<<1, 1, 0, st>>>(n, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_peak_narrow(const unsigned long long* csum, int nf, int R, int np,
+                               const float* prop, float thresh, float* shifts, float* info,
+                               int* list, int* list_n, cudaStream_t st) {
+  if (nf <= 0) return cudaSuccess;
+  k_peak_narrow<<<nf, 32, 0, st>>>(csum, R, np, prop, thresh, shifts, info, list, list_n);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/vimg.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +21,9 @@ constexpr int kTile = 32;                // temporal-kernel output tile side
 constexpr int kMaxL = 50;                // longest segment the temporal kernel holds
 constexpr int kMaxHp = 64;               // longest high-pass window
 constexpr double kFix = 1099511627776.0; // 2^40: fixed-point scale of C sums
+constexpr int kNarrowWin = 7;            // learned proposal: +-2 px plus a refinement ring
+constexpr int kCrop = 128;               // learned proposal: centre crop side
+constexpr float kShiftScale = 12.0f;     // network output x 12 = shift in px
 
 struct PatchGrid {
   int ny, nx, y0, x0;
@@ -62,11 +66,37 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 size_t stats_map_floats(PatchGrid g, int R);  // per frame
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                          const TemplateDev& td, float* isf, cudaStream_t st);
+// list/list_n (device): process only the listed frames (count read on the device).
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
-                            unsigned long long* csum, cudaStream_t st);
+                            unsigned long long* csum, cudaStream_t st,
+                            const int* list = nullptr, const int* list_n = nullptr);
 cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, float* shifts,
-                        float* peak_info, double* surface, cudaStream_t st);
+                        float* peak_info, double* surface, cudaStream_t st,
+                        const int* list = nullptr, const int* list_n = nullptr);
+cudaError_t launch_corr_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                               const TemplateDev& td, const float* isf, const float* prop,
+                               unsigned long long* csum, cudaStream_t st);
+cudaError_t launch_peak_narrow(const unsigned long long* csum, int nf, int R, int np,
+                               const float* prop, float thresh, float* shifts, float* info,
+                               int* list, int* list_n, cudaStream_t st);
+
+cudaError_t launch_count_add(const int* n, long long* total, cudaStream_t st);
+
+// learned proposal (cnn.cu)
+int cnn_param_count();
+size_t cnn_act_floats(int n);
+cudaError_t cnn_input(const uint16_t* frames, int n, int H, int W, const float* tmpl,
+                      long long tmpl_stride, float* acts, cudaStream_t st);
+cudaError_t cnn_forward(const float* params, const __nv_bfloat16* wb, float* acts, int n,
+                        float* out, cudaStream_t st);
+cudaError_t cnn_backward(const float* params, const __nv_bfloat16* wb, const float* acts,
+                         float* dacts, int n, const float* dout, float* grads, cudaStream_t st);
+cudaError_t cnn_mse(const float* out, const float* target, int n, float* dout, float* loss,
+                    cudaStream_t st);
+cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
+                     float eps, int step, cudaStream_t st);
+cudaError_t cnn_to_bf16(const float* p, __nv_bfloat16* q, cudaStream_t st);
 cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st);
 
 }  // namespace vimg

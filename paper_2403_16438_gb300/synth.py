@@ -161,26 +161,35 @@ def activity(scene: Scene, n: int, gen: torch.Generator) -> torch.Tensor:
     return act * torch.tensor(scene.dffs, dtype=torch.float32)
 
 
-def render(scene: Scene, shifts: torch.Tensor, act: torch.Tensor, device) -> torch.Tensor:
-    """Expected counts float32 [n, H, W] of frames showing Scene(x - s_t)."""
+def render(scene: Scene, shifts: torch.Tensor, act: torch.Tensor, device, crop=None,
+           margin_px=None) -> torch.Tensor:
+    """Expected counts float32 [n, H, W] of frames showing Scene(x - s_t).
+    crop = (y0, x0, h, w) renders only that window of the frame."""
     cfg = scene.cfg
     H, W = cfg.H, cfg.W
+    cy0, cx0 = 0, 0
+    if crop is not None:
+        cy0, cx0, H, W = crop
     n = shifts.shape[0]
     sy = shifts[:, 0].to(device=device, dtype=torch.float32).view(n, 1, 1)
     sx = shifts[:, 1].to(device=device, dtype=torch.float32).view(n, 1, 1)
-    ys = torch.arange(H, device=device, dtype=torch.float32).view(1, H, 1)
-    xs = torch.arange(W, device=device, dtype=torch.float32).view(1, 1, W)
+    ys = torch.arange(cy0, cy0 + H, device=device, dtype=torch.float32).view(1, H, 1)
+    xs = torch.arange(cx0, cx0 + W, device=device, dtype=torch.float32).view(1, 1, W)
     out = torch.full((n, H, W), 0.3 * cfg.bg_amp, device=device)
     for (wgt, cy, cx, gy, gx) in scene.bg:
         ey = torch.exp(-0.5 * ((ys - sy - cy) / gy) ** 2)
         ex = torch.exp(-0.5 * ((xs - sx - cx) / gx) ** 2)
         out += (0.7 * cfg.bg_amp * wgt) * ey * ex
     act = act.to(device)
-    margin = int(math.ceil(max(cfg.clamp + 4 * cfg.jump_px * (cfg.jump_frac > 0), 1))) + 4
+    if margin_px is None:
+        margin_px = cfg.clamp + 4 * cfg.jump_px * (cfg.jump_frac > 0)
+    margin = int(math.ceil(max(margin_px, 1))) + 4
     for j, (cy, cx, a, b, th, f0) in enumerate(scene.neurons):
         half = int(math.ceil(max(a, b))) + margin
-        y0, y1 = max(0, int(cy) - half), min(H, int(cy) + half + 1)
-        x0, x1 = max(0, int(cx) - half), min(W, int(cx) + half + 1)
+        y0, y1 = max(0, int(cy) - half - cy0), min(H, int(cy) + half + 1 - cy0)
+        x0, x1 = max(0, int(cx) - half - cx0), min(W, int(cx) + half + 1 - cx0)
+        if y0 >= y1 or x0 >= x1:
+            continue
         yy = ys[:, y0:y1, :] - sy - cy
         xx = xs[:, :, x0:x1] - sx - cx
         c, s = math.cos(th), math.sin(th)
@@ -226,3 +235,103 @@ def make_video(cfg: VideoConfig, n_frames: int | None = None, device="cpu", chun
         acc += add_noise(exp_, cfg.read_sigma, g_dev).to(torch.float64).sum(0)
     template = (acc / nt).to(torch.float32)
     return frames, shifts, template
+
+
+def training_batch(scenes, n: int, gen: torch.Generator, device, crop: int = 128,
+                   max_shift: float = 12.0):
+    """A batch of (frame crop uint16 [n,crop,crop], template crop float32
+    [n,crop,crop], planted shift float32 [n,2]) for the learned shift
+    proposal: random scene, uniform shift in [-max_shift, max_shift]^2, the
+    centre crop of the frame; the template crop is that scene's template.
+    `scenes` is a list of (Scene, template crop float32 [crop,crop] on device)."""
+    k = len(scenes)
+    idx = torch.randint(0, k, (n,), generator=gen)
+    shifts = (torch.rand((n, 2), generator=gen, dtype=torch.float64) * 2 - 1) * max_shift
+    frames = torch.empty((n, crop, crop), dtype=torch.int32, device=device)
+    tmpl = torch.empty((n, crop, crop), dtype=torch.float32, device=device)
+    g_dev = torch.Generator(device=device).manual_seed(int(torch.randint(0, 2**31 - 1, (1,), generator=gen)))
+    for s_i in range(k):
+        sel = (idx == s_i).nonzero().flatten()
+        if sel.numel() == 0:
+            continue
+        scene, tcrop = scenes[s_i]
+        cfg = scene.cfg
+        y0, x0 = (cfg.H - crop) // 2, (cfg.W - crop) // 2
+        act = activity(scene, sel.numel(), gen)
+        exp_ = render(scene, shifts[sel], act, device, crop=(y0, x0, crop, crop),
+                      margin_px=max_shift + 2)
+        frames[sel.to(device)] = add_noise(exp_, cfg.read_sigma, g_dev).to(torch.int32)
+        tmpl[sel.to(device)] = tcrop
+    return frames.to(torch.uint16), tmpl, shifts.to(torch.float32)
+
+
+def training_scenes(n_scenes: int, seed: int, device, crop: int = 128):
+    """Paper-scale scenes (config-2 content) with their template centre crops."""
+    out = []
+    for i in range(n_scenes):
+        cfg = paper_scale_config(seed=seed + i, template_frames=100)
+        g = torch.Generator().manual_seed(cfg.seed)
+        scene = make_scene(cfg, g)
+        y0, x0 = (cfg.H - crop) // 2, (cfg.W - crop) // 2
+        g_dev = torch.Generator(device=device).manual_seed(cfg.seed + 17)
+        act = activity(scene, cfg.template_frames, g)
+        exp_ = render(scene, torch.zeros((cfg.template_frames, 2), dtype=torch.float64), act,
+                      device, crop=(y0, x0, crop, crop), margin_px=2)
+        t = add_noise(exp_, cfg.read_sigma, g_dev).to(torch.float64).mean(0).to(torch.float32)
+        out.append((scene, t))
+    return out
+
+
+def training_pool(n_frames: int, n_scenes: int, seed: int, device, crop: int = 128,
+                  max_shift: float = 12.0):
+    """A pool of n_frames training samples from n_scenes paper-scale scenes:
+    (frame crops uint16 [n,crop,crop], per-sample scene index int64 [n],
+    template crops float32 [n_scenes,crop,crop], planted shifts float32 [n,2])."""
+    dev = torch.device(device)
+    gen = torch.Generator().manual_seed(seed)
+    per = (n_frames + n_scenes - 1) // n_scenes
+    frames = torch.empty((n_frames, crop, crop), dtype=torch.uint16, device=dev)
+    shifts = torch.empty((n_frames, 2), dtype=torch.float32)
+    scene_idx = torch.empty((n_frames,), dtype=torch.int64)
+    tmpls = torch.empty((n_scenes, crop, crop), dtype=torch.float32, device=dev)
+    g_dev = torch.Generator(device=dev).manual_seed(seed + 31)
+    t = 0
+    for i in range(n_scenes):
+        cfg = paper_scale_config(seed=seed + 1000 + i, template_frames=64)
+        scene = make_scene(cfg, gen)
+        y0, x0 = (cfg.H - crop) // 2, (cfg.W - crop) // 2
+        act_t = activity(scene, cfg.template_frames, gen)
+        exp_t = render(scene, torch.zeros((cfg.template_frames, 2), dtype=torch.float64), act_t,
+                       dev, crop=(y0, x0, crop, crop), margin_px=2)
+        tmpls[i] = add_noise(exp_t, cfg.read_sigma, g_dev).to(torch.float32).mean(0)
+        m = min(per, n_frames - t)
+        if m <= 0:
+            break
+        sh = (torch.rand((m, 2), generator=gen, dtype=torch.float64) * 2 - 1) * max_shift
+        act = activity(scene, m, gen)
+        exp_ = render(scene, sh, act, dev, crop=(y0, x0, crop, crop), margin_px=max_shift + 2)
+        frames[t:t + m] = add_noise(exp_, cfg.read_sigma, g_dev)
+        shifts[t:t + m] = sh.to(torch.float32)
+        scene_idx[t:t + m] = i
+        t += m
+    return frames, scene_idx, tmpls, shifts
+
+
+def augmented_batch(pool, n: int, gen: torch.Generator):
+    """Random samples of a training pool under a random element of the square's
+    symmetry group (flips and transposition), applied alike to frame, template
+    and shift.  Returns (frames uint16, templates float32, shifts float32 [n,2])."""
+    frames, scene_idx, tmpls, shifts = pool
+    dev = frames.device
+    idx = torch.randint(0, frames.shape[0], (n,), generator=gen)
+    f = frames.view(torch.int16)[idx.to(dev)]  # same bits; uint16 indexing is not on every device
+    t = tmpls[scene_idx[idx].to(dev)]
+    s = shifts[idx].clone()
+    op = int(torch.randint(0, 8, (1,), generator=gen))
+    if op & 1:  # flip y
+        f, t, s[:, 0] = f.flip(1), t.flip(1), -s[:, 0]
+    if op & 2:  # flip x
+        f, t, s[:, 1] = f.flip(2), t.flip(2), -s[:, 1]
+    if op & 4:  # transpose
+        f, t, s = f.transpose(1, 2), t.transpose(1, 2), s[:, [1, 0]]
+    return f.contiguous().view(torch.uint16), t.contiguous(), s.contiguous()

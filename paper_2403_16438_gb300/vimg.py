@@ -51,6 +51,9 @@ EXPORTS = [
     "vimg_default_params", "vimg_create", "vimg_destroy", "vimg_set_template", "vimg_process",
     "vimg_process_io", "vimg_process_host", "vimg_frames_seen", "vimg_reset", "vimg_last_error",
     "vimg_version", "vimg_profile_enable", "vimg_profile_read", "vimg_motion_noalloc",
+    "vimg_cnn_param_count", "vimg_cnn_workspace_floats", "vimg_cnn_prepare", "vimg_cnn_pack_bf16",
+    "vimg_cnn_forward", "vimg_cnn_loss", "vimg_cnn_backward", "vimg_cnn_adam", "vimg_load_proposal",
+    "vimg_proposal_stats",
 ]
 NSTAGES = 6
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
@@ -87,6 +90,27 @@ def _load():
     L.vimg_profile_read.restype = i
     L.vimg_motion_noalloc.argtypes = [vp, vp, i, i, i, i, vp, vp, vp]
     L.vimg_motion_noalloc.restype = i
+    L.vimg_cnn_param_count.argtypes = []
+    L.vimg_cnn_param_count.restype = i
+    L.vimg_cnn_workspace_floats.argtypes = [i]
+    L.vimg_cnn_workspace_floats.restype = ctypes.c_size_t
+    L.vimg_cnn_prepare.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, vp, vp]
+    L.vimg_cnn_prepare.restype = i
+    L.vimg_cnn_pack_bf16.argtypes = [vp, vp, vp]
+    L.vimg_cnn_pack_bf16.restype = i
+    L.vimg_cnn_forward.argtypes = [vp, vp, vp, i, vp, vp]
+    L.vimg_cnn_forward.restype = i
+    L.vimg_cnn_loss.argtypes = [vp, vp, i, vp, vp, vp]
+    L.vimg_cnn_loss.restype = i
+    L.vimg_cnn_backward.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
+    L.vimg_cnn_backward.restype = i
+    L.vimg_cnn_adam.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, i, vp]
+    L.vimg_cnn_adam.restype = i
+    L.vimg_load_proposal.argtypes = [vp, vp]
+    L.vimg_load_proposal.restype = i
+    L.vimg_proposal_stats.argtypes = [vp, vp, vp]
+    L.vimg_proposal_stats.restype = i
     L.vimg_version.argtypes = []
     L.vimg_version.restype = ctypes.c_char_p
     return L
@@ -182,6 +206,15 @@ class Handle:
                                                  _ptr(shifts_host), _ptr(summary_host),
                                                  _ptr(corrected)))
 
+
+    def load_proposal(self, params: torch.Tensor):
+        assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
+        self._check(lib.vimg_load_proposal(self._h, _ptr(params)))
+
+    def proposal_stats(self):
+        fr, fb = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(lib.vimg_proposal_stats(self._h, ctypes.byref(fr), ctypes.byref(fb)))
+        return fr.value, fb.value
 
     def profile(self, on: bool = True):
         self._check(lib.vimg_profile_enable(self._h, 1 if on else 0))

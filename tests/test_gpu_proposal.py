@@ -1,0 +1,108 @@
+"""Learned shift proposal on the GPU: the CUDA forward/backward against the FP64
+CPU oracle (gradient check), training progress with the library's own
+kernels, and the proposal path (CNN -> +-2 px window -> full-window fallback)
+against the full-window path, which stays the judge of its error."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn as ocnn
+from paper_2403_16438_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@pytest.fixture(scope="module")
+def prop():
+    from paper_2403_16438_gb300 import proposal
+    return proposal
+
+
+def test_forward_and_gradients_match_fp64_oracle(prop):
+    dev = torch.device(DEV)
+    p = prop.init_params(7, dev)
+    p[-66:] = torch.randn(66, generator=torch.Generator().manual_seed(8)).to(dev) * 0.1
+    scenes = synth.training_scenes(2, 123, dev)
+    g = torch.Generator().manual_seed(5)
+    frames, tmpl, shifts = synth.training_batch(scenes, 4, g, dev)
+    tr = prop.Trainer(p, 4)
+    tr.forward(frames, tmpl, 128 * 128)
+    from paper_2403_16438_gb300.vimg import lib
+    tgt = shifts.to(dev)
+    assert lib.vimg_cnn_loss(_p(tr.out), _p(tgt), 4, _p(tr.dout), _p(tr.loss), tr.sp) == 0
+    tr.g.zero_()
+    assert lib.vimg_cnn_backward(_p(tr.p), _p(tr.pb), _p(tr.ws), _p(tr.dws), 4, _p(tr.dout),
+                                 _p(tr.g), tr.sp) == 0
+    torch.cuda.synchronize()
+    # oracle with the weights as the GPU uses them: BF16 convolution weights
+    pn = p.cpu().double().numpy().copy()
+    off = 0
+    for c in ocnn.IN_C:
+        pn[off:off + 32 * c * 9] = ocnn.round_bf16(pn[off:off + 32 * c * 9])
+        off += 32 * c * 9 + 32
+    x = ocnn.prepare(frames.cpu().numpy(), tmpl.cpu().double().numpy())
+    out, cache = ocnn.forward(pn, x)
+    loss, dout = ocnn.mse(out, shifts.double().numpy())
+    gref = ocnn.backward(pn, cache, dout)
+    out_g = tr.out.cpu().double().numpy()
+    assert np.max(np.abs(out_g - out)) <= 1e-3 * max(1.0, np.abs(out).max())
+    assert abs(tr.loss.item() - loss) <= 1e-3 * loss
+    gg = tr.g.cpu().double().numpy()
+    offs = np.cumsum([0] + [32 * c * 9 + 32 for c in ocnn.IN_C] + [66])
+    for a, b in zip(offs[:-1], offs[1:]):
+        err = np.linalg.norm(gg[a:b] - gref[a:b]) / max(np.linalg.norm(gref[a:b]), 1e-12)
+        assert err < 5e-3, (a, b, err)
+
+
+def test_training_reduces_the_loss(prop):
+    p, hist = prop.train(total_frames=20000, epochs=2, batch=128, n_scenes=40, log_every=20)
+    first = np.mean([h[1] for h in hist[:2]])
+    last = np.mean([h[1] for h in hist[-2:]])
+    assert last < 0.5 * first, hist
+
+
+@pytest.fixture(scope="module")
+def trained(prop):
+    p, _ = prop.train(total_frames=40000, epochs=3, batch=256, n_scenes=80)
+    return p
+
+
+def test_proposal_path_against_full_window(trained):
+    from paper_2403_16438_gb300 import vimg
+    cfg = synth.paper_scale_config(seed=2024)
+    n = 60
+    frames, planted, T = synth.make_video(cfg, n, device=DEV)
+    outs = {}
+    for name, flags in (("full", 0), ("prop", vimg.PROPOSAL_CNN)):
+        h = vimg.Handle(cfg.H, cfg.W, flags=flags)
+        h.set_template(T)
+        if flags:
+            h.load_proposal(trained)
+        s = torch.zeros((n, 2), device=DEV)
+        info = torch.zeros((n, 4), device=DEV)
+        corr = torch.zeros((n, cfg.H, cfg.W), device=DEV)
+        summ = torch.zeros((1, 2, cfg.H, cfg.W), device=DEV)
+        assert h.process(frames, shifts=s, peak_info=info, corrected=corr, summary=summ) == 1
+        torch.cuda.synchronize()
+        outs[name] = (s.cpu().numpy(), info.cpu().numpy(), corr, summ)
+        if flags:
+            fr, fb = h.proposal_stats()
+            assert fr == n and 0 <= fb <= n
+        h.close()
+    sf, sp = outs["full"][0], outs["prop"][0]
+    err = np.abs(sf - sp).max(axis=1)
+    # the full window judges the proposal: 0.05 px gate
+    assert np.mean(err <= 0.05) >= 0.95, err
+    same = err <= 1e-4
+    # frames that agree give the same corrected video
+    idx = np.nonzero(same)[0]
+    if len(idx):
+        a, b = outs["full"][2][idx], outs["prop"][2][idx]
+        assert ((a - b).abs().max() / a.abs().max()).item() <= 1e-4
