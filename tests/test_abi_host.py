@@ -21,7 +21,7 @@ def vimg():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "vimg.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(vimg_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(vimg_[a-z_0-9]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(vimg):
