@@ -63,7 +63,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or jobs or _stale([LIB], objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-Xlinker", "--no-undefined",
+                                  "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)

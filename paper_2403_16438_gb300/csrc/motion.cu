@@ -515,7 +515,8 @@ cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, f
 // patches x 8 lanes (lane = displacement row), the frame read through the
 // read-only cache.  Same normalisation and fixed-point sums as the full window.
 constexpr int kNarrow = kNarrowWin;  // 7
-constexpr int kNarrowPatches = 16;
+constexpr int kNarrowGroup = 24;     // patches per CTA (one patch row, or part of it)
+constexpr int kNarrowStride = kNarrowGroup * kPatch + kNarrow;  // staged row stride (floats)
 
 __device__ __forceinline__ void narrow_center(const float* prop, int f, int R, int& cy, int& cx) {
   // prop holds the network output (shift / kShiftScale)
@@ -527,23 +528,33 @@ __device__ __forceinline__ void narrow_center(const float* prop, int f, int R, i
   cx = max(-lim, min(lim, cx));
 }
 
-__global__ void __launch_bounds__(kNarrowPatches * 8)
+__global__ void __launch_bounds__(kNarrowGroup * 8, 2)
     k_corr_narrow(const uint16_t* __restrict__ frames, int H, int W, PatchGrid g, int R,
                   const float* __restrict__ tc, const float* __restrict__ tn2,
                   const float* __restrict__ isf, const float* __restrict__ prop,
                   unsigned long long* __restrict__ csum) {
+  extern __shared__ __align__(16) float nreg[];  // [27][nrs] frame region - c
   __shared__ unsigned long long cs[kNarrow * kNarrow];
-  const int f = blockIdx.y, np = g.ny * g.nx;
+  const int f = blockIdx.y;
+  const int gpr = (g.nx + kNarrowGroup - 1) / kNarrowGroup;
+  const int py = blockIdx.x / gpr, px0 = (blockIdx.x % gpr) * kNarrowGroup;
+  const int G = min(kNarrowGroup, g.nx - px0);
   const int u = threadIdx.x >> 3, dy = threadIdx.x & 7;
-  const int p = blockIdx.x * kNarrowPatches + u;
   int cy, cx;
   narrow_center(prop, f, R, cy, cx);
   const int wy0 = cy - kNarrow / 2, wx0 = cx - kNarrow / 2;
+  const int rows = kNarrow + kPatch - 1, cols = G * kPatch + kNarrow - 1;
+  const int nrs = kNarrowStride;
+  const int ty = g.y0 + py * kPatch, tx0 = g.x0 + px0 * kPatch;
   for (int i = threadIdx.x; i < kNarrow * kNarrow; i += blockDim.x) cs[i] = 0ull;
+  // stage the union of the group's narrow regions (coalesced rows)
+  const uint16_t* F = frames + (size_t)f * H * W + (size_t)(ty + wy0) * W + tx0 + wx0;
+  for (int r = 0; r < rows; ++r)
+    for (int x = threadIdx.x; x < cols; x += blockDim.x) nreg[r * nrs + x] = (float)__ldg(F + (size_t)r * W + x);
   __syncthreads();
-  if (p < np && dy < kNarrow) {
-    const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
-    const uint16_t* F = frames + (size_t)f * H * W + (size_t)(ty + wy0 + dy) * W + tx + wx0;
+  if (u < G && dy < kNarrow) {
+    const int p = py * g.nx + px0 + u;
+    const float* rrow = nreg + dy * nrs + u * kPatch;
     const float* trow = tc + (size_t)p * kPatch * kTplStride;
     float acc[kNarrow];
 #pragma unroll
@@ -552,7 +563,7 @@ __global__ void __launch_bounds__(kNarrowPatches * 8)
     for (int ky = 0; ky < kPatch; ++ky) {
       float fr[kNarrow + kPatch - 1];
 #pragma unroll
-      for (int i = 0; i < kNarrow + kPatch - 1; ++i) fr[i] = __ldg(F + i);
+      for (int i = 0; i < kNarrow + kPatch - 1; ++i) fr[i] = rrow[i];
       float t[kTplStride];
 #pragma unroll
       for (int i = 0; i < kTplStride; i += 4) {
@@ -563,14 +574,15 @@ __global__ void __launch_bounds__(kNarrowPatches * 8)
       for (int kx = 0; kx < kPatch; ++kx)
 #pragma unroll
         for (int j = 0; j < kNarrow; ++j) acc[j] = fmaf(t[kx], fr[j + kx], acc[j]);
-      F += W;
+      rrow += nrs;
       trow += kTplStride;
     }
     int oy, ox, sh, sw;
     stats_map_dims(g, R, &oy, &ox, &sh, &sw);
     const float t2 = __ldg(tn2 + p);
     const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
-    const float* iv = isf + (size_t)f * sh * sw + (size_t)(ty + wy0 + dy - oy) * sw + (tx + wx0 - ox);
+    const int txp = tx0 + u * kPatch;
+    const float* iv = isf + (size_t)f * sh * sw + (size_t)(ty + wy0 + dy - oy) * sw + (txp + wx0 - ox);
 #pragma unroll
     for (int j = 0; j < kNarrow; ++j) {
       const float z = acc[j] * pscale * __ldg(iv + j);
@@ -619,9 +631,17 @@ cudaError_t launch_corr_narrow(const uint16_t* frames, int nf, int H, int W, Pat
                                const TemplateDev& td, const float* isf, const float* prop,
                                unsigned long long* csum, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
-  const int np = g.ny * g.nx;
-  k_corr_narrow<<<dim3((np + kNarrowPatches - 1) / kNarrowPatches, nf), kNarrowPatches * 8, 0, st>>>(
-      frames, H, W, g, R, td.tc, td.tn2, isf, prop, csum);
+  const size_t smem = sizeof(float) * (kNarrow + kPatch - 1) * kNarrowStride;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_corr_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int groups = g.ny * ((g.nx + kNarrowGroup - 1) / kNarrowGroup);
+  k_corr_narrow<<<dim3(groups, nf), kNarrowGroup * 8, smem, st>>>(frames, H, W, g, R, td.tc, td.tn2,
+                                                                   isf, prop, csum);
   return cudaGetLastError();
 }
 
