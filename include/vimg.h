@@ -59,7 +59,11 @@ extern "C" {
 #define VIMG_ERR_SIZE (-6)        /* H or W below 2R + patch, or above limits    */
 
 /* params.flags */
-#define VIMG_CORR_BF16 1      /* BF16 tensor-core correlation numerators         */
+#define VIMG_CORR_BF16 1      /* BF16 tensor-core (tcgen05) correlation numerators:
+                                 the frame minus the rounded template and the
+                                 centred template go through BF16 with FP32
+                                 accumulation; needs search_radius 16; not with
+                                 VIMG_PROPOSAL_CNN                               */
 #define VIMG_PROPOSAL_CNN 2   /* learned shift proposal + narrow window          */
 #define VIMG_OUT_HIGHPASS 4   /* corrected output holds the high-passed video    */
 
@@ -139,6 +143,12 @@ int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_
  * Synchronises before returning.  Returns k or an error. */
 int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n, float* h_shifts_out,
                       float* h_summary_out, float* d_corrected_out);
+
+/* Waits for the handle's stream and reports device-side failures: returns
+ * VIMG_ERR_TIMEOUT (sticky) if a kernel's bounded wait gave up (the kernel then
+ * stopped issuing work and returned), VIMG_ERR_CUDA on a CUDA error, else
+ * VIMG_OK. */
+int vimg_synchronize(vimg_handle* h);
 
 /* Frames seen by the handle so far (host-side counter; no device sync). */
 long long vimg_frames_seen(const vimg_handle* h);

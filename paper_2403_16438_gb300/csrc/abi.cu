@@ -55,6 +55,13 @@ struct vimg_handle {
   int* fb_n = nullptr;                  // [1]
   long long* fb_total = nullptr;        // [1] fallbacks since creation
   long long prop_frames = 0;
+  // BF16 tensor-core correlation
+  float* tround = nullptr;              // [H][W] rounded template
+  __nv_bfloat16* bt = nullptr;          // per-patch Toeplitz template blocks
+  float* bgc = nullptr;                 // [np][w*w] background correlation
+  __nv_bfloat16* fc = nullptr;          // [max_chunk][H][Wp] frame - rounded template
+  alignas(64) unsigned char tmap[128];  // tensor map over fc
+  int* dev_err = nullptr;               // device-side wait timeouts (sticky)
   float gw[2 * kGaussMaxRadius + 1] = {};
   float* inv = nullptr;                 // [max_chunk][stats map] 1/sqrt(SF) per window
   unsigned long long* csum = nullptr;   // [max_chunk][nwin]
@@ -143,7 +150,7 @@ static void free_all(vimg_handle* h) {
                   h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
                   h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
                   h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
-                  h->fb_total};
+                  h->fb_total, h->tround, h->bt, h->bgc, h->fc, h->dev_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
@@ -197,8 +204,12 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     fail(nullptr, VIMG_ERR_ARG, "unknown flag bits");
     return nullptr;
   }
-  if (p.flags & VIMG_CORR_BF16) {
-    fail(nullptr, VIMG_ERR_ARG, "VIMG_CORR_BF16 is not available in this build");
+  if ((p.flags & VIMG_CORR_BF16) && (p.flags & VIMG_PROPOSAL_CNN)) {
+    fail(nullptr, VIMG_ERR_ARG, "VIMG_CORR_BF16 and VIMG_PROPOSAL_CNN cannot be combined");
+    return nullptr;
+  }
+  if ((p.flags & VIMG_CORR_BF16) && p.search_radius != kMaxR) {
+    fail(nullptr, VIMG_ERR_ARG, "VIMG_CORR_BF16 needs search_radius 16");
     return nullptr;
   }
   if ((p.flags & VIMG_PROPOSAL_CNN) &&
@@ -242,6 +253,16 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     ALLOC(h->carry_shift[i], sizeof(float) * 2 * std::max(1, h->carry_cap));
   }
   ALLOC(h->tmpl, sizeof(float) * HW);
+  ALLOC(h->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
+  if (p.flags & VIMG_CORR_BF16) {
+    ALLOC(h->tround, sizeof(float) * HW);
+    ALLOC(h->bt, bf16_bt_bytes(g));
+    ALLOC(h->bgc, sizeof(float) * h->np * h->nwin);
+    ALLOC(h->fc, sizeof(__nv_bfloat16) * (size_t)p.max_chunk * H * bf16_row_pitch(W));
+    if (e == cudaSuccess && bf16_tensor_map(h->tmap, h->fc, p.max_chunk, H, W) != 0)
+      e = cudaErrorNotSupported;
+  }
   if (p.flags & VIMG_PROPOSAL_CNN) {
     ALLOC(h->cnn_p, sizeof(float) * cnn_param_count());
     ALLOC(h->cnn_b, sizeof(__nv_bfloat16) * cnn_param_count());
@@ -294,6 +315,10 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
   CK(cudaMemcpyAsync(h->tmpl, d_template, sizeof(float) * h->H * h->W, cudaMemcpyDeviceToDevice,
                      h->st),
      "template copy");
+  if (h->p.flags & VIMG_CORR_BF16)
+    CK(bf16_template_prep(d_template, h->H, h->W, h->g, h->p.search_radius, h->td, h->tround,
+                          h->bt, h->bgc, h->st),
+       "tensor-core template prep");
   h->have_template = true;
   return VIMG_OK;
 }
@@ -348,8 +373,15 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
      "window statistics launch");
   prof_end(h, ps);
   ps = prof_begin(h, 1);
-  CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st),
-     "correlation launch");
+  if (h->p.flags & VIMG_CORR_BF16) {
+    CK(bf16_make_fc(frames, nf, h->H, h->W, h->tround, h->fc, h->st), "frame offset images");
+    CK(launch_corr_bf16(h->tmap, nf, R, h->g, h->bt, h->bgc, h->td, h->inv, h->csum, h->dev_err,
+                        h->st),
+       "tensor-core correlation launch");
+  } else {
+    CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st),
+       "correlation launch");
+  }
   prof_end(h, ps);
   ps = prof_begin(h, 2);
   CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, surface, h->st), "peak launch");
@@ -638,5 +670,15 @@ extern "C" int vimg_proposal_stats(vimg_handle* h, long long* frames, long long*
   }
   if (frames) *frames = h->prop_frames;
   if (fallbacks) *fallbacks = fb;
+  return VIMG_OK;
+}
+
+extern "C" int vimg_synchronize(vimg_handle* h) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  int derr = 0;
+  CK(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->st), "status copy");
+  CK(cudaStreamSynchronize(h->st), "stream sync");
+  if (derr) return fail(h, VIMG_ERR_TIMEOUT, "a device-side wait gave up");
   return VIMG_OK;
 }

@@ -53,7 +53,7 @@ EXPORTS = [
     "vimg_version", "vimg_profile_enable", "vimg_profile_read", "vimg_motion_noalloc",
     "vimg_cnn_param_count", "vimg_cnn_workspace_floats", "vimg_cnn_prepare", "vimg_cnn_pack_bf16",
     "vimg_cnn_forward", "vimg_cnn_loss", "vimg_cnn_backward", "vimg_cnn_adam", "vimg_load_proposal",
-    "vimg_proposal_stats",
+    "vimg_proposal_stats", "vimg_synchronize",
 ]
 NSTAGES = 6
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
@@ -111,6 +111,8 @@ def _load():
     L.vimg_load_proposal.restype = i
     L.vimg_proposal_stats.argtypes = [vp, vp, vp]
     L.vimg_proposal_stats.restype = i
+    L.vimg_synchronize.argtypes = [vp]
+    L.vimg_synchronize.restype = i
     L.vimg_version.argtypes = []
     L.vimg_version.restype = ctypes.c_char_p
     return L
@@ -215,6 +217,9 @@ class Handle:
         fr, fb = ctypes.c_longlong(), ctypes.c_longlong()
         self._check(lib.vimg_proposal_stats(self._h, ctypes.byref(fr), ctypes.byref(fb)))
         return fr.value, fb.value
+
+    def synchronize(self):
+        return self._check(lib.vimg_synchronize(self._h))
 
     def profile(self, on: bool = True):
         self._check(lib.vimg_profile_enable(self._h, 1 if on else 0))
