@@ -397,6 +397,32 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     n = frames.shape[0]
     out = {}
     ref = ref_shifts.clone()
+    # BF16 tensor-core correlation (tcgen05), FP32 accumulation
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk, flags=vimg.CORR_BF16)
+    h.set_template(T)
+    sh = torch.empty_like(ref)
+    ms, prof = time_variant(h, frames, (sh, corrected, summary), args.steps, args.warmup, stream)
+    h.synchronize()
+    h.close()
+    d = (sh - ref).abs().max(dim=1).values.double().cpu()
+    value = n * args.steps * ws / (ms / 1000.0)
+    corr_ms = prof["corr"][0]
+    pk, _ = peaks()
+    tflops = corr_flops_per_frame() * n * args.steps / (corr_ms / 1000.0) / 1e12
+    out["bf16_tensor_core"] = {
+        "value": value, "unit": UNIT, "x_realtime": value / RECORD_FPS / ws,
+        "ms_per_step": ms / args.steps,
+        "shift_err_vs_fp32_full_window_px": {"max": float(d.max()), "p99": float(d.quantile(0.99)),
+                                             "frac_le_0.05": float((d <= 0.05).double().mean())},
+        "corr_roofline": {"kernel": "k_corr_bf16 (+ frame offset pre-pass)", "bound": "tensor",
+                          "achieved_useful_tflops": tflops,
+                          "peak_tflops": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                          "frac_useful": tflops / pk["bf16_tflops_sustained"],
+                          "note": "useful = 2 x 484 x 441 x 1089 FLOP per frame; the implicit GEMM "
+                                  "executes 4x that (padding of dy, dx and the x-Toeplitz)"},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": sum(prof[s][1] for s in ("stats", "corr", "peak", "temporal", "proposal")),
+    }
     # learned proposal: trained here, on the GPU, by the library's own kernels
     t0 = time.time()
     params, hist = proposal.train(log_every=500)

@@ -60,6 +60,7 @@ struct vimg_handle {
   __nv_bfloat16* bt = nullptr;          // per-patch Toeplitz template blocks
   float* bgc = nullptr;                 // [np][w*w] background correlation
   __nv_bfloat16* fc = nullptr;          // [max_chunk][H][Wp] frame - rounded template
+  float* num = nullptr;                 // [max_chunk][np][w*w] per-patch numerators
   alignas(64) unsigned char tmap[128];  // tensor map over fc
   int* dev_err = nullptr;               // device-side wait timeouts (sticky)
   float gw[2 * kGaussMaxRadius + 1] = {};
@@ -150,7 +151,7 @@ static void free_all(vimg_handle* h) {
                   h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
                   h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
                   h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
-                  h->fb_total, h->tround, h->bt, h->bgc, h->fc, h->dev_err};
+                  h->fb_total, h->tround, h->bt, h->bgc, h->fc, h->dev_err, h->num};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
@@ -260,6 +261,7 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     ALLOC(h->bt, bf16_bt_bytes(g));
     ALLOC(h->bgc, sizeof(float) * h->np * h->nwin);
     ALLOC(h->fc, sizeof(__nv_bfloat16) * (size_t)p.max_chunk * H * bf16_row_pitch(W));
+    ALLOC(h->num, sizeof(float) * (size_t)p.max_chunk * h->np * h->nwin);
     if (e == cudaSuccess && bf16_tensor_map(h->tmap, h->fc, p.max_chunk, H, W) != 0)
       e = cudaErrorNotSupported;
   }
@@ -375,8 +377,8 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
   ps = prof_begin(h, 1);
   if (h->p.flags & VIMG_CORR_BF16) {
     CK(bf16_make_fc(frames, nf, h->H, h->W, h->tround, h->fc, h->st), "frame offset images");
-    CK(launch_corr_bf16(h->tmap, nf, R, h->g, h->bt, h->bgc, h->td, h->inv, h->csum, h->dev_err,
-                        h->st),
+    CK(launch_corr_bf16(h->tmap, nf, R, h->g, h->bt, h->bgc, h->td, h->inv, h->num, h->csum,
+                        h->dev_err, h->st),
        "tensor-core correlation launch");
   } else {
     CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st),

@@ -17,11 +17,16 @@
 // per patch (o_p = 8-alignment offset of the patch's window).  5 x 3 blocks of
 // (8 dy x 16 dx) cover the 33 x 33 window; K = 21 rows x 48 columns.
 //
-// Each CTA (one per SM, persistent) takes a group of 16 frames and a range of
-// patches, normalises each patch's numerators into ZNCC values, accumulates them
-// in tensor memory (FP32, fixed order) and finally adds the sums to the frames'
-// int64 fixed-point surfaces.  Every wait is bounded: on timeout the CTA records
-// an error and stops issuing work.
+// N = 32: the template is split into a BF16 high part and a BF16 remainder (16 dx
+// columns each), so it enters with ~16 significant bits; only Fc is rounded.
+//
+// Each CTA (one per SM, persistent) walks (frame group, patch) work units.  One
+// thread waits for the unit's TMA loads, issues its 945 MMAs and commits them to
+// an mbarrier; as soon as they complete the next unit's loads are issued, so the
+// epilogue (hi + lo + background term -> per-patch numerators in global memory)
+// overlaps them.  k_zncc_reduce then forms C(d) = sum_p ZNCC_p(d) per frame in
+// patch order (deterministic) as 2^-40 fixed point.  Every wait is bounded: on
+// timeout the CTA records an error and stops issuing work.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -38,15 +43,14 @@ constexpr int kFr = 16;           // frames per group (M = 128 = 16 x 8)
 constexpr int kRowsA = 60;        // staged rows: 5 dy blocks x 8 + 20
 constexpr int kColBlk = 10;       // staged column blocks of 8 (80 columns)
 constexpr int kDyBlk = 5, kDxBlk = 3, kKq = 3;  // K chunks of 16 columns per template row
-constexpr int kN = 16;
+constexpr int kJx = 16;                       // displacement columns per block
+constexpr int kN = 2 * kJx;                   // N = [template hi part | lo part]
 constexpr uint32_t kAColBytes = kFr * kRowsA * 16;               // 15,360 B per column block
 constexpr uint32_t kABytes = kColBlk * kAColBytes;              // 153,600 B
-constexpr uint32_t kBtBytesPerRow = 6 * 2 * 128;                // 6 K-blocks x 2 N-blocks
-constexpr uint32_t kBtBytes = kPatch * kBtBytesPerRow;          // 32,256 B per patch
+constexpr uint32_t kBtBytesPerRow = 6 * 4 * 128;                // 6 K-blocks x 4 N-blocks
+constexpr uint32_t kBtBytes = kPatch * kBtBytesPerRow;          // 64,512 B per patch
 constexpr int kThreads = 128;
 constexpr int kTmemCols = 512;
-constexpr int kDCols = kDyBlk * kDxBlk * kN;  // 240
-constexpr int kCOff = 256;                    // partial sums live at columns 256..495
 constexpr long long kSpin = 1LL << 22;  // bounded waits (seconds at most)
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -84,35 +88,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15])));
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     k_corr_bf16(const __grid_constant__ CUtensorMap tmap, int nf, int R, PatchGrid g,
                 const __nv_bfloat16* __restrict__ bt, const float* __restrict__ bgc,
-                const float* __restrict__ tn2, const float* __restrict__ isf, int sh, int sw,
-                int oy, int ox, int prange, unsigned long long* __restrict__ csum,
-                int* __restrict__ err) {
+                float* __restrict__ num, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                 // [10 col blocks][16 frames][60 rows][16 B]
-  unsigned char* sB = smem + kABytes;       // [21][6][2][8][8] bf16
+  unsigned char* sB = smem + kABytes;       // [21][6 K blocks][4 N blocks][8][8] bf16
   __shared__ __align__(8) uint64_t bar_load, bar_mma;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int np = g.ny * g.nx, w = 2 * R + 1;
+  const int np = g.ny * g.nx, w = 2 * R + 1, nw = w * w;
   const int n_groups = (nf + kFr - 1) / kFr;
-  const int n_ranges = (np + prange - 1) / prange;
-  const int n_items = n_groups * n_ranges;
+  const int n_work = n_groups * np;  // (frame group, patch) pairs, patch fastest
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
@@ -131,47 +120,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_base;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   uint32_t ph_load = 0, ph_mma = 0;
-  // this thread's accumulator row: frame f_loc, displacement row jy
   const int f_loc = (warp * 32 + lane) >> 3, jy = lane & 7;
 
-  for (int item = blockIdx.x; item < n_items && !abort_flag; item += gridDim.x) {
-    const int grp = item / n_ranges, rng = item - grp * n_ranges;
-    const int f0 = grp * kFr, p_begin = rng * prange, p_end = min(np, p_begin + prange);
-    // zero the partial sums
-    {
-      float z[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) z[i] = 0.f;
-      for (int c = 0; c < kDCols; c += 16) tmem_st16(tmem + lane_base + kCOff + c, z);
-    }
-    for (int p = p_begin; p < p_end; ++p) {
-      const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
-      const int xs = tx - R, xa = xs & ~7;  // 16-byte aligned start column (may be negative)
-      // 1. loads: 10 TMA boxes of Fc (8 cols x 60 rows x 16 frames) + the patch's Bt
-      if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bar_load)),
-                     "r"(kABytes + kBtBytes));
-        for (int cb = 0; cb < kColBlk; ++cb) {
-          asm volatile(
-              "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-                  su32(sA + cb * kAColBytes)),
-              "l"(&tmap), "r"(xa + 8 * cb), "r"(ty - R), "r"(f0), "r"(su32(&bar_load))
-              : "memory");
-        }
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(sB)),
-            "l"(bt + (size_t)p * (kBtBytes / 2)), "r"(kBtBytes), "r"(su32(&bar_load))
-            : "memory");
-      }
+  // loads of one (frame group, patch) work unit: 10 TMA boxes of Fc + the patch's Bt
+  auto issue_loads = [&](int wk) {
+    const int grp = wk / np, p = wk - grp * np;
+    const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
+    const int xa = (tx - R) & ~7;  // 16-byte aligned start column
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bar_load)),
+                 "r"(kABytes + kBtBytes));
+    for (int cb = 0; cb < kColBlk; ++cb)
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+              su32(sA + cb * kAColBytes)),
+          "l"(&tmap), "r"(xa + 8 * cb), "r"(ty - R), "r"(grp * kFr), "r"(su32(&bar_load))
+          : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(sB)),
+        "l"(bt + (size_t)p * (kBtBytes / 2)), "r"(kBtBytes), "r"(su32(&bar_load))
+        : "memory");
+  };
+
+  if (tid == 0 && (int)blockIdx.x < n_work) issue_loads(blockIdx.x);
+  for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x) {
+    const int grp = wk / np, p = wk - grp * np;
+    // 1. operands of this unit have landed -> MMAs: 5 x 3 blocks x 21 rows x 3 chunks
+    if (tid == 0) {
       if (!mbar_wait(&bar_load, ph_load)) {
         atomicExch(err, 1);
         abort_flag = 1;
-      }
-      ph_load ^= 1;
-      __syncthreads();
-      if (abort_flag) break;
-      // 2. MMAs: 5 x 3 blocks x 21 template rows x 3 column chunks
-      if (tid == 0) {
+      } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t a0 = su32(sA), b0 = su32(sB);
         for (int by = 0; by < kDyBlk; ++by)
@@ -182,8 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t aaddr = a0 + (uint32_t)(2 * bx + 2 * q) * kAColBytes +
                                        (uint32_t)(8 * by + rho) * 16;
                 const uint64_t ad = desc(aaddr, kAColBytes, kRowsA * 16);
-                const uint64_t bd =
-                    desc(b0 + (uint32_t)(rho * 6 + 2 * q) * 256, 256, 128);
+                const uint64_t bd = desc(b0 + (uint32_t)(rho * 6 + 2 * q) * 512, 512, 128);
                 const uint32_t acc = (rho | q) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
@@ -194,73 +171,75 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             su32(&bar_mma)));
       }
-      if (!mbar_wait(&bar_mma, ph_mma)) {
-        atomicExch(err, 1);
-        abort_flag = 1;
-      }
-      ph_mma ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      // 3. epilogue: ZNCC = (num + B_p) * 21/|Tc| * isf, added to the partial sums
-      {
-        const float t2 = __ldg(tn2 + p);
-        const float ps = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
-        const int f = f0 + f_loc;
-        const float* isf_f = isf + (size_t)min(f, nf - 1) * sh * sw;
-        for (int by = 0; by < kDyBlk; ++by) {
-          const int dyi = 8 * by + jy;  // displacement index 0..39 (valid < w)
-          for (int bx = 0; bx < kDxBlk; ++bx) {
-            const int blk = (by * kDxBlk + bx) * kN;
-            float dv[16], cv[16];
-            tmem_ld16(tmem + lane_base + blk, dv);
-            tmem_ld16(tmem + lane_base + kCOff + blk, cv);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int dxi = 16 * bx + j;
-              if (dyi < w && dxi < w) {
-                const float num = dv[j] + __ldg(bgc + (size_t)p * w * w + dyi * w + dxi);
-                const float is = __ldg(isf_f + (size_t)(ty - R - oy + dyi) * sw + (tx - R - ox + dxi));
-                cv[j] += num * ps * is;
-              }
-            }
-            tmem_st16(tmem + lane_base + kCOff + blk, cv);
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
     }
+    ph_load ^= 1;
+    if (!mbar_wait(&bar_mma, ph_mma)) {
+      atomicExch(err, 1);
+      abort_flag = 1;
+    }
+    ph_mma ^= 1;
+    __syncthreads();
     if (abort_flag) break;
-    // 4. the range's partial sums -> the frames' fixed-point surfaces
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // 2. the shared operands are free: start the next unit's loads now
+    if (tid == 0 && wk + (int)gridDim.x < n_work) issue_loads(wk + gridDim.x);
+    // 3. epilogue (overlaps those loads): numerator = hi + lo parts + background term
     {
-      const int f = f0 + f_loc;
-      for (int by = 0; by < kDyBlk; ++by)
+      const int f = grp * kFr + f_loc;
+      float* out = num + ((size_t)min(f, nf - 1) * np + p) * nw;
+      const float* bg = bgc + (size_t)p * nw;
+      for (int by = 0; by < kDyBlk; ++by) {
+        const int dyi = 8 * by + jy;
         for (int bx = 0; bx < kDxBlk; ++bx) {
-          float cv[16];
-          tmem_ld16(tmem + lane_base + kCOff + (by * kDxBlk + bx) * kN, cv);
-          const int dyi = 8 * by + jy;
+          float hv[16], lv[16];
+          tmem_ld16(tmem + lane_base + (by * kDxBlk + bx) * kN, hv);
+          tmem_ld16(tmem + lane_base + (by * kDxBlk + bx) * kN + kJx, lv);
           if (f < nf && dyi < w) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int dxi = 16 * bx + j;
-              if (dxi < w)
-                atomicAdd(csum + ((size_t)f * w + dyi) * w + dxi,
-                          (unsigned long long)__float2ll_rn(cv[j] * (float)kFix));
+              if (dxi < w) out[dyi * w + dxi] = hv[j] + lv[j] + __ldg(bg + dyi * w + dxi);
             }
           }
         }
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
   }
+  // drain: a load issued for a unit this CTA will not run is impossible (it only
+  // issues the next unit it owns), so nothing is in flight here.
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ZNCC of every (frame, displacement) summed over the patches in patch order:
+//   C(d) = sum_p num_p(d) * 21 / |Tc_p| * isf(window_p(d)),  stored in 2^-40 fixed point.
+__global__ void k_zncc_reduce(const float* __restrict__ num, int nf, int R, PatchGrid g,
+                              const float* __restrict__ tn2, const float* __restrict__ isf,
+                              int sh, int sw, unsigned long long* __restrict__ csum) {
+  const int f = blockIdx.y, w = 2 * R + 1, nw = w * w, np = g.ny * g.nx;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nw) return;
+  const int dy = d / w, dx = d - dy * w;
+  const float* nf_ = num + (size_t)f * np * nw + d;
+  const float* is = isf + (size_t)f * sh * sw + (size_t)dy * sw + dx;
+  float acc = 0.f;
+  for (int p = 0; p < np; ++p) {
+    const int py = p / g.nx, px = p - py * g.nx;
+    const float t2 = __ldg(tn2 + p);
+    const float ps = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+    acc = fmaf(__ldg(nf_ + (size_t)p * nw) * ps, __ldg(is + (size_t)py * kPatch * sw + px * kPatch), acc);
+  }
+  csum[(size_t)f * nw + d] = (unsigned long long)__float2ll_rn(acc * (float)kFix);
+}
+
 // ---- per-template constants -----------------------------------------------------
-// Bt_p: [rho][K block 0..5][N block 0..1][jx%8][c%8] bf16 = Tc_p[rho][c - jx - o_p].
+// Bt_p: [rho][K block 0..5][N block 0..3][n%8][c%8] bf16, n = part * 16 + jx:
+// part 0 = bf16(Tc_p[rho][c - jx - o_p]), part 1 = bf16 of the remainder, so the
+// two parts carry the template to ~16 significant bits.
 __global__ void k_bt_prep(const float* __restrict__ tc, PatchGrid g, int R,
                           __nv_bfloat16* __restrict__ bt) {
   const int p = blockIdx.x;
@@ -269,9 +248,11 @@ __global__ void k_bt_prep(const float* __restrict__ tc, PatchGrid g, int R,
   __nv_bfloat16* out = bt + (size_t)p * (kBtBytes / 2);
   for (int i = threadIdx.x; i < (int)(kBtBytes / 2); i += blockDim.x) {
     const int rho = i / (kBtBytesPerRow / 2), r = i % (kBtBytesPerRow / 2);
-    const int kb = r / 128, nb = (r / 64) & 1, jx = nb * 8 + ((r >> 3) & 7), c = kb * 8 + (r & 7);
-    const int kx = c - jx - o;
-    out[i] = __float2bfloat16_rn(kx >= 0 && kx < kPatch ? t[rho * kTplStride + kx] : 0.f);
+    const int kb = r / 256, nb = (r / 64) & 3, n = nb * 8 + ((r >> 3) & 7), c = kb * 8 + (r & 7);
+    const int part = n / kJx, jx = n % kJx, kx = c - jx - o;
+    const float v = kx >= 0 && kx < kPatch ? t[rho * kTplStride + kx] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    out[i] = part == 0 ? hi : __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 
@@ -381,7 +362,7 @@ size_t bf16_tensor_map_bytes() { return sizeof(CUtensorMap); }
 
 cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
                              const __nv_bfloat16* bt, const float* bgc, const TemplateDev& td,
-                             const float* isf, unsigned long long* csum, int* err,
+                             const float* isf, float* num, unsigned long long* csum, int* err,
                              cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   static int sms = 0;
@@ -397,20 +378,15 @@ cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
       return e;
     }
   }
-  int oy, ox, sh, sw;
-  oy = g.y0 - R;
-  ox = g.x0 - R;
-  sh = kPatch * (g.ny - 1) + 2 * R + 1;
-  sw = kPatch * (g.nx - 1) + 2 * R + 1;
-  const int np = g.ny * g.nx, groups = (nf + kFr - 1) / kFr;
-  // patch ranges: enough items to fill the SMs, as few ranges as that allows
-  int ranges = std::max(1, std::min(np, (2 * sms + groups - 1) / groups));
-  const int prange = (np + ranges - 1) / ranges;
-  ranges = (np + prange - 1) / prange;
-  const int items = groups * ranges;
+  const int np = g.ny * g.nx, groups = (nf + kFr - 1) / kFr, w = 2 * R + 1;
   const CUtensorMap* map = static_cast<const CUtensorMap*>(tmap);
-  k_corr_bf16<<<std::min(items, sms), kThreads, smem, st>>>(*map, nf, R, g, bt, bgc, td.tn2, isf,
-                                                            sh, sw, oy, ox, prange, csum, err);
+  k_corr_bf16<<<std::min(groups * np, sms), kThreads, smem, st>>>(*map, nf, R, g, bt, bgc, num,
+                                                                  err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int sh = kPatch * (g.ny - 1) + 2 * R + 1, sw = kPatch * (g.nx - 1) + 2 * R + 1;
+  k_zncc_reduce<<<dim3((w * w + 127) / 128, nf), 128, 0, st>>>(num, nf, R, g, td.tn2, isf, sh, sw,
+                                                              csum);
   return cudaGetLastError();
 }
 

@@ -95,7 +95,7 @@ cudaError_t bf16_make_fc(const uint16_t* frames, int nf, int H, int W, const flo
                          __nv_bfloat16* fc, cudaStream_t st);
 cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
                              const __nv_bfloat16* bt, const float* bgc, const TemplateDev& td,
-                             const float* isf, unsigned long long* csum, int* err,
+                             const float* isf, float* num, unsigned long long* csum, int* err,
                              cudaStream_t st);
 
 // learned proposal (cnn.cu)
