@@ -352,6 +352,8 @@ def run_vimg(args):
     if not args.no_variants:
         line["variants"] = run_variants(args, frames, T, shifts, corrected, summary, stream, dev,
                                         k_max, ws)
+    if not args.no_batched:
+        line.setdefault("variants", {})["batched_6_videos"] = run_batched(args, stream, dev, ws)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         fps, nf, dt, cores = cpu_oracle_fps(frames[:512].cpu(), T.cpu(), budget_s=args.cpu_budget,
                                             max_frames=512)
@@ -453,6 +455,113 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     return out
 
 
+# Six concurrent videos of uneven size (H, W, frames): 44.6 GB of uint16 frames.
+BATCH_VIDEOS = [(256, 256, 20000), (384, 512, 15000), (512, 512, 12000), (512, 1024, 10000),
+                (768, 768, 7500), (1024, 1024, 5000)]
+
+
+def run_batched(args, stream, dev, ws):
+    """Serving-shaped load: the six videos processed together by
+    vimg_process_batch (one launch per kernel for all videos of a step, CUDA
+    graph replay, step shape picked by the autotuner on a 500-frame probe),
+    against the plain per-video path on the same videos."""
+    from paper_2403_16438_gb300 import autotune, synth, vimg
+    t0 = time.time()
+    vids = []
+    for i, (H_, W_, n_) in enumerate(BATCH_VIDEOS):
+        n_ = max(L, int(n_ * args.batch_scale))
+        cfg = synth.scaled_config(H_, W_, n_, seed=5000 + i)
+        f, _, T = synth.make_video(cfg, n_, device=dev)
+        vids.append((f, T))
+    torch.cuda.synchronize()
+    t_gen = time.time() - t0
+    frames = [f for f, _ in vids]
+    total = sum(f.shape[0] for f in frames)
+    px = sum(f.numel() for f in frames)
+    maxc = 512
+    hs = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=maxc) for f in frames]
+    for h, (_, T) in zip(hs, vids):
+        h.set_template(T)
+    shifts = [torch.empty((f.shape[0], 2), device=dev) for f in frames]
+    rings = [torch.empty((2 * maxc, f.shape[1], f.shape[2]), device=dev) for f in frames]
+    summ = [torch.empty((max(1, f.shape[0] // L), 2, f.shape[1], f.shape[2]), device=dev)
+            for f in frames]
+    probe = 500
+    choice, table = autotune.tune_batch(
+        hs, frames, probe_frames=probe,
+        outputs=dict(shifts=[x[:probe] for x in shifts], corrected=rings,
+                     summary=[m[:probe // L] for m in summ]))
+    chunk, graph = choice
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def batched():
+        for h in hs:
+            h.reset()
+        vimg.process_batch(hs, frames, shifts=shifts, corrected=rings, summary=summ, chunk=chunk,
+                           ring_chunks=2, use_graph=graph)
+
+    steps = max(1, args.batch_steps)
+    ms_b = timed(batched, steps, 1)
+    ref_shifts = [x.clone() for x in shifts]
+    for h in hs:
+        h.close()
+    # the plain per-video path: each video on its own, 500-frame calls, same rings
+    plain = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=args.chunk)
+             for f in frames]
+    for h, (_, T) in zip(plain, vids):
+        h.set_template(T)
+
+    def sequential():
+        for h, f, sh, r, m in zip(plain, frames, shifts, rings, summ):
+            h.reset()
+            k = 0
+            for i, t in enumerate(range(0, f.shape[0], 500)):
+                c = f[t:t + 500]
+                k += h.process(c, shifts=sh[t:t + 500], corrected=r[(i % 2) * 500:],
+                               summary=m[k:])
+
+    ms_p = timed(sequential, steps, 1)
+    same = all(torch.equal(a, b) for a, b in zip(ref_shifts, shifts))
+    for h in plain:
+        h.close()
+    value = total / (ms_b / 1000.0)
+    del vids, frames, rings, summ
+    torch.cuda.empty_cache()
+    return {
+        "value": value, "unit": UNIT, "ms_per_step": ms_b,
+        "x_realtime": value / RECORD_FPS,
+        "x_realtime_note": "video-seconds processed per second: sum of frames / 741 fps / time",
+        "megapixels_per_s": px / (ms_b / 1000.0) / 1e6,
+        "plain_per_video_value": total / (ms_p / 1000.0),
+        "plain_per_video_ms_per_step": ms_p,
+        "speedup_vs_plain": ms_p / ms_b,
+        "shifts_identical_to_plain": same,
+        "autotune": {"choice": {"chunk": chunk, "use_graph": graph},
+                     "probe_frames_per_video": probe,
+                     "seconds": {f"{c}/{'graph' if g else 'direct'}": t
+                                 for (c, g), t in table.items()}},
+        "config": {"videos": [{"H": H_, "W": W_, "frames": int(f_)}
+                              for (H_, W_, _), f_ in zip(BATCH_VIDEOS,
+                                                         [max(L, int(n * args.batch_scale))
+                                                          for _, _, n in BATCH_VIDEOS])],
+                   "frames_per_step": total, "gb_uint16": round(px * 2 / 1e9, 2),
+                   "outputs": "shifts, summaries, corrected frames into 2-slot rings",
+                   "generate_s": t_gen},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +575,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -72,7 +72,7 @@ typedef struct vimg_handle vimg_handle;
 typedef struct {
   int search_radius;        /* R: displacements in [-R, R]^2; 0..16; default 16  */
   int patch;                /* patch side; the paper's 21 (Sec. II); 21 only     */
-  int segment_len;          /* L; the paper's 50 (Sec. III-B); 1..64             */
+  int segment_len;          /* L; the paper's 50 (Sec. III-B); 1..50             */
   float gauss_sigma;        /* Eq. 2 smoothing sigma; the paper's 3.0; radius
                                ceil(4 sigma) must be <= 12                       */
   int hp_window;            /* boxcar high-pass length; 0 = off; <= 64           */
@@ -86,7 +86,7 @@ typedef struct {
 
 /* Fills *p with the defaults above (R = 16, patch 21, L = 50, sigma 3,
  * high-pass off, no flags, fallback 0.5, narrow radius 2, default stream,
- * max_chunk 256). */
+ * max_chunk 200). */
 void vimg_default_params(vimg_params* p);
 
 /* Creates a handle for H x W frames on the current CUDA device and allocates
@@ -207,6 +207,44 @@ int vimg_load_proposal(vimg_handle* h, const float* d_params);
 /* Frames estimated and frames that fell back to the full window since the
  * handle was created (synchronises the handle's stream). */
 int vimg_proposal_stats(vimg_handle* h, long long* frames, long long* fallbacks);
+
+/* ---- Several videos per call -------------------------------------------------
+ * A serving-shaped scheduling layer over the per-video method; the paper has
+ * no counterpart (it processes one recording at a time).  Each video v has its
+ * own handle hs[v] (own H x W, template and stream state) and processes the
+ * next ns[v] >= 0 frames of d_frames[v] (device uint16 [ns[v]][H_v][W_v]),
+ * with the same outputs and the same results, bit for bit, as vimg_process on
+ * that handle.  The call advances in steps: per step every video with frames
+ * left takes up to `chunk` of them (shortened to end on a segment boundary),
+ * and each kernel of the path (window statistics, correlation, peak, fused
+ * temporal pass) is launched once for the step's videos, up to 8 videos per
+ * launch (more are split into groups of 8).
+ *
+ * Requirements: 1 <= k <= 64 distinct handles on one device, each with its
+ * template set, created without VIMG_CORR_BF16 and VIMG_PROPOSAL_CNN (the
+ * batched form runs the full-window FP32 method).  Work is enqueued on hs[0]'s
+ * stream; the other handles' streams are ordered before and after the call
+ * with events.  Output arrays have k entries; any entry (or the whole array)
+ * may be NULL.  d_shifts_out[v] is [ns[v]][2]; d_summary_out[v] is
+ * [k_v][2][H_v][W_v] as for vimg_process.  d_corrected_out[v] is
+ * [ns[v]][H_v][W_v], or, with ring_chunks > 0, a ring of ring_chunks slots of
+ * `chunk` frames: step s writes its frames from the start of slot
+ * (s mod ring_chunks).  segments_out (k ints, may be NULL) receives k_v.
+ * Returns the sum of the k_v or a VIMG_ERR_* code (the message is on hs[0]). */
+typedef struct {
+  int chunk;        /* frames per video per step; 0 = each handle's max_chunk;
+                       must not exceed any handle's max_chunk                   */
+  int ring_chunks;  /* 0: contiguous corrected output; > 0: ring slots        */
+  int use_graph;    /* 1: record the call's launches into a CUDA graph once and
+                       replay it for identical calls (same handles in the same
+                       stream state, same pointers, sizes and options)         */
+  int reserved;     /* 0 */
+} vimg_batch_opts;
+
+int vimg_process_batch(vimg_handle* const* hs, int k, const uint16_t* const* d_frames,
+                       const int* ns, float* const* d_shifts_out, float* const* d_corrected_out,
+                       float* const* d_summary_out, int* segments_out,
+                       const vimg_batch_opts* opts);
 
 /* Per-stage timing with CUDA events recorded around each of the library's
  * launches on params.stream (off by default).  Stages:

@@ -14,6 +14,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <atomic>
+#include <vector>
 
 #include "vimg_internal.h"
 
@@ -81,7 +83,20 @@ struct vimg_handle {
   Prof prof;
   int sticky = 0;
   std::string err;
+  long long id = 0;                     // unique per handle (graph cache keys)
+  // CUDA graphs of vimg_process_batch calls led by this handle
+  struct GraphEntry {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> end_state;  // per video: frames_seen, carry_n, carry_cur
+    std::vector<int> segs;
+    int ret = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_st = nullptr;        // private stream the graphs are recorded on
 };
+
+static std::atomic<long long> g_next_id{1};
 
 // Records the start of a stage's launch; returns the slot or -1.
 static int prof_begin(vimg_handle* h, int stage) {
@@ -159,6 +174,10 @@ static void free_all(vimg_handle* h) {
     if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
   }
   if (h->copy_st) cudaStreamDestroy(h->copy_st);
+  for (auto& ge : h->graphs)
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  h->graphs.clear();
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->prof.ev) {
     for (int i = 0; i < 2 * kProfSlots; ++i)
       if (h->prof.ev[i]) cudaEventDestroy(h->prof.ev[i]);
@@ -225,6 +244,7 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     return nullptr;
   }
   vimg_handle* h = new vimg_handle();
+  h->id = g_next_id++;
   h->H = H, h->W = W, h->p = p, h->g = g;
   h->np = g.ny * g.nx;
   h->w = 2 * p.search_radius + 1;
@@ -241,6 +261,7 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
   const size_t HW = (size_t)H * W;
   h->carry_cap = std::max(p.segment_len - 1, p.hp_window > 0 ? p.hp_window - 1 : 0);
   cudaError_t e = cudaGetDevice(&h->dev);
+  if (e == cudaSuccess) e = kernels_init();
 #define ALLOC(ptr, bytes)                                                   \
   if (e == cudaSuccess && (bytes) > 0) e = cudaMalloc((void**)&(ptr), (bytes));
   ALLOC(h->td.tc, sizeof(float) * h->np * kPatch * kTplStride);
@@ -391,21 +412,12 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
   return VIMG_OK;
 }
 
-// One internal batch: n <= max_chunk frames.
-static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vimg_io& io,
-                         int k_before) {
-  const size_t HW = (size_t)h->H * h->W;
-  const int L = h->p.segment_len;
-  const float* shifts;
-  if (io.shifts_in) {
-    shifts = io.shifts_in;
-  } else {
-    float* out = io.shifts ? io.shifts : h->shift_tmp;
-    int rc = estimate(h, frames, n, out, io.peak_info, io.surface);
-    if (rc) return rc;
-    shifts = out;
-  }
+// Temporal-pass arguments of one internal batch of n frames (summary: where
+// this batch's first completed segment goes).
+static TemporalArgs temporal_args(const vimg_handle* h, const uint16_t* frames, int n,
+                                  const float* shifts, float* corrected, float* summary) {
   const long long seen = h->frames_seen;
+  const int L = h->p.segment_len;
   const int c = (int)(seen % L);
   TemporalArgs a{};
   a.src.carry = h->carry[h->carry_cur];
@@ -421,14 +433,20 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
   a.seg_base = seen - c;
   a.n_seg = (c + n + L - 1) / L;
   a.out_hp = (h->p.flags & VIMG_OUT_HIGHPASS) ? 1 : 0;
-  a.corrected = io.corrected;
-  a.summary = io.summary ? io.summary + (size_t)k_before * 2 * HW : nullptr;
-  if (io.corrected || io.summary) {
-    const int ps = prof_begin(h, 3);
-    CK(launch_temporal(a, h->st), "temporal launch");
-    prof_end(h, ps);
-  }
-  const int k = (c + n) / L;
+  a.corrected = corrected;
+  a.summary = summary;
+  return a;
+}
+
+// After a batch of n frames: keeps the frames (and shifts) that later batches
+// still need -- the open segment and the high-pass history -- in the carry
+// buffer, and advances the stream state.  Returns the segments completed.
+static int advance_state(vimg_handle* h, const uint16_t* frames, const float* shifts, int n,
+                         cudaStream_t st) {
+  const size_t HW = (size_t)h->H * h->W;
+  const int L = h->p.segment_len;
+  const long long seen = h->frames_seen;
+  const int k = (int)((seen % L + n) / L);
   // New carry: the last K' frames of (carry ++ batch).
   const long long seen2 = seen + n;
   const int c2 = (int)(seen2 % L);
@@ -437,17 +455,17 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
   if (K > seen2) K = (int)seen2;
   const int nv = h->carry_n + n, nxt = 1 - h->carry_cur;
   int dst = 0;
-  const int pcs = K > 0 ? prof_begin(h, 5) : -1;
+  const int pcs = K > 0 && st == h->st ? prof_begin(h, 5) : -1;
   for (int v = nv - K; v < nv;) {
     const bool in_carry = v < h->carry_n;
     const int run = in_carry ? std::min(h->carry_n - v, nv - v) : nv - v;
     const uint16_t* sf = in_carry ? h->carry[h->carry_cur] + HW * v : frames + HW * (v - h->carry_n);
     const float* ss = in_carry ? h->carry_shift[h->carry_cur] + 2 * v : shifts + 2 * (v - h->carry_n);
     CK(cudaMemcpyAsync(h->carry[nxt] + HW * dst, sf, sizeof(uint16_t) * HW * run,
-                       cudaMemcpyDeviceToDevice, h->st),
+                       cudaMemcpyDeviceToDevice, st),
        "carry copy");
     CK(cudaMemcpyAsync(h->carry_shift[nxt] + 2 * dst, ss, sizeof(float) * 2 * run,
-                       cudaMemcpyDeviceToDevice, h->st),
+                       cudaMemcpyDeviceToDevice, st),
        "carry shift copy");
     dst += run;
     v += run;
@@ -457,6 +475,29 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
   h->carry_n = K;
   h->frames_seen = seen2;
   return k;
+}
+
+// One internal batch: n <= max_chunk frames.
+static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vimg_io& io,
+                         int k_before) {
+  const size_t HW = (size_t)h->H * h->W;
+  const float* shifts;
+  if (io.shifts_in) {
+    shifts = io.shifts_in;
+  } else {
+    float* out = io.shifts ? io.shifts : h->shift_tmp;
+    int rc = estimate(h, frames, n, out, io.peak_info, io.surface);
+    if (rc) return rc;
+    shifts = out;
+  }
+  TemporalArgs a = temporal_args(h, frames, n, shifts, io.corrected,
+                                 io.summary ? io.summary + (size_t)k_before * 2 * HW : nullptr);
+  if (io.corrected || io.summary) {
+    const int ps = prof_begin(h, 3);
+    CK(launch_temporal(a, h->st), "temporal launch");
+    prof_end(h, ps);
+  }
+  return advance_state(h, frames, shifts, n, h->st);
 }
 
 extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io) {
@@ -497,6 +538,254 @@ extern "C" int vimg_process(vimg_handle* h, const uint16_t* d_frames, int n, flo
   io.corrected = d_corrected_out;
   io.summary = d_summary_out;
   return vimg_process_io(h, d_frames, n, &io);
+}
+
+// ---- several videos per call ---------------------------------------------------
+namespace {
+constexpr int kMaxBatchVideos = 64;
+constexpr size_t kMaxGraphs = 4;
+
+struct BatchCall {
+  vimg_handle* const* hs;
+  int k;
+  const uint16_t* const* frames;
+  const int* ns;
+  float* const* shifts;
+  float* const* corrected;
+  float* const* summary;
+  int ring;
+  std::vector<int> chunk;  // per video
+};
+
+template <class T>
+T* entry(T* const* arr, int v) {
+  return arr ? arr[v] : nullptr;
+}
+}  // namespace
+
+// Enqueues the whole call on st: per step, one launch per kernel for up to
+// kMaxVideos videos.  Returns the total segment count; segs[v] gets k_v.
+static int batch_body(const BatchCall& c, cudaStream_t st, std::vector<int>& segs) {
+  vimg_handle* h = c.hs[0];  // error messages go to the lead handle
+  const int k = c.k;
+  std::vector<int> done(k, 0);
+  segs.assign(k, 0);
+  int total = 0;
+  for (int s = 0;; ++s) {
+    std::vector<int> act, m(k, 0);
+    for (int v = 0; v < k; ++v) {
+      const int left = c.ns[v] - done[v];
+      if (left <= 0) continue;
+      const vimg_handle* hv = c.hs[v];
+      int mv = std::min(left, c.chunk[v]);
+      if (mv < left) {
+        const int cut = (int)((hv->frames_seen + mv) % hv->p.segment_len);
+        if (mv - cut > 0) mv -= cut;  // end the step on a segment boundary
+      }
+      m[v] = mv;
+      act.push_back(v);
+    }
+    if (act.empty()) break;
+    for (size_t g0 = 0; g0 < act.size(); g0 += kMaxVideos) {
+      const int gn = (int)std::min<size_t>(kMaxVideos, act.size() - g0);
+      MotionBatch mb{};
+      mb.n = gn;
+      float* sh_out[kMaxVideos];
+      const uint16_t* fr[kMaxVideos];
+      for (int i = 0; i < gn; ++i) {
+        const int v = act[g0 + i];
+        vimg_handle* hv = c.hs[v];
+        const size_t HW = (size_t)hv->H * hv->W;
+        float* so = entry(c.shifts, v);
+        sh_out[i] = so ? so + 2 * (size_t)done[v] : hv->shift_tmp;
+        fr[i] = c.frames[v] + HW * done[v];
+        MotionJob& J = mb.j[i];
+        J.frames = fr[i], J.nf = m[v], J.H = hv->H, J.W = hv->W, J.g = hv->g;
+        J.R = hv->p.search_radius;
+        J.tc = hv->td.tc, J.tn2 = hv->td.tn2, J.coff = hv->td.coff;
+        J.isf = hv->inv, J.csum = hv->csum, J.shifts = sh_out[i];
+        CK(cudaMemsetAsync(hv->csum, 0, sizeof(unsigned long long) * (size_t)m[v] * hv->nwin, st),
+           "surface reset");
+      }
+      if (!motion_batch_finalize(mb)) return fail(h, VIMG_ERR_ARG, "batch too large");
+      CK(launch_stats_multi(mb, st), "batched window statistics launch");
+      CK(launch_corr_f32_multi(mb, st), "batched correlation launch");
+      CK(launch_peak_multi(mb, st), "batched peak launch");
+      TemporalBatch tb{};
+      for (int i = 0; i < gn; ++i) {
+        const int v = act[g0 + i];
+        vimg_handle* hv = c.hs[v];
+        const size_t HW = (size_t)hv->H * hv->W;
+        float* co = entry(c.corrected, v);
+        float* su = entry(c.summary, v);
+        if (!co && !su) continue;
+        if (co)
+          co += HW * (c.ring > 0 ? (size_t)(s % c.ring) * c.chunk[v] : (size_t)done[v]);
+        if (su) su += (size_t)segs[v] * 2 * HW;
+        tb.a[tb.n++] = temporal_args(hv, fr[i], m[v], sh_out[i], co, su);
+      }
+      if (tb.n > 0) {
+        if (!temporal_batch_finalize(tb)) return fail(h, VIMG_ERR_ARG, "batch too large");
+        CK(launch_temporal_multi(tb, st), "batched temporal launch");
+      }
+      for (int i = 0; i < gn; ++i) {
+        const int v = act[g0 + i];
+        const int kk = advance_state(c.hs[v], fr[i], sh_out[i], m[v], st);
+        if (kk < 0) {
+          if (c.hs[v] != h) fail(h, kk, c.hs[v]->err);
+          return kk;
+        }
+        segs[v] += kk;
+        total += kk;
+        done[v] += m[v];
+      }
+    }
+  }
+  return total;
+}
+
+extern "C" int vimg_process_batch(vimg_handle* const* hs, int k, const uint16_t* const* d_frames,
+                                  const int* ns, float* const* d_shifts_out,
+                                  float* const* d_corrected_out, float* const* d_summary_out,
+                                  int* segments_out, const vimg_batch_opts* opts) {
+  if (!hs || k < 1 || k > kMaxBatchVideos || !d_frames || !ns)
+    return fail(hs && k >= 1 ? hs[0] : nullptr, VIMG_ERR_ARG,
+                "vimg_process_batch: need 1..64 handles, frame pointers and counts");
+  vimg_handle* h = hs[0];
+  if (!h) return fail(nullptr, VIMG_ERR_ARG, "vimg_process_batch: null handle");
+  vimg_batch_opts o{};
+  if (opts) o = *opts;
+  if (o.chunk < 0 || o.ring_chunks < 0 || o.reserved != 0)
+    return fail(h, VIMG_ERR_ARG, "vimg_process_batch: bad options");
+  BatchCall c{hs, k, d_frames, ns, d_shifts_out, d_corrected_out, d_summary_out, o.ring_chunks, {}};
+  for (int v = 0; v < k; ++v) {
+    vimg_handle* hv = hs[v];
+    if (!hv) return fail(h, VIMG_ERR_ARG, "vimg_process_batch: null handle");
+    for (int u = 0; u < v; ++u)
+      if (hs[u] == hv) return fail(h, VIMG_ERR_ARG, "vimg_process_batch: repeated handle");
+    if (hv->sticky) {
+      h->err = "vimg_process_batch: a handle is in an error state: " + hv->err;
+      return hv->sticky;
+    }
+    if (hv->dev != h->dev) return fail(h, VIMG_ERR_ARG, "vimg_process_batch: handles on different devices");
+    if (hv->p.flags & (VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN))
+      return fail(h, VIMG_ERR_ARG,
+                  "vimg_process_batch: handles must run the full-window FP32 method");
+    if (!hv->have_template)
+      return fail(h, VIMG_ERR_NO_TEMPLATE, "vimg_process_batch: a handle has no template");
+    if (ns[v] < 0 || (ns[v] > 0 && !d_frames[v]))
+      return fail(h, VIMG_ERR_ARG, "vimg_process_batch: bad frame count or pointer");
+    if (o.chunk > hv->p.max_chunk)
+      return fail(h, VIMG_ERR_ARG, "vimg_process_batch: chunk exceeds a handle's max_chunk");
+    c.chunk.push_back(o.chunk > 0 ? o.chunk : hv->p.max_chunk);
+  }
+  cudaStream_t st = h->st;
+  // Order the other handles' streams before this call.
+  struct EventGuard {
+    cudaEvent_t e = nullptr;
+    ~EventGuard() {
+      if (e) cudaEventDestroy(e);
+    }
+  } guard;
+  cudaEvent_t& ev = guard.e;
+  bool other = false;
+  for (int v = 1; v < k; ++v) other = other || hs[v]->st != st;
+  if (other) {
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    for (int v = 1; v < k; ++v)
+      if (hs[v]->st != st) {
+        CK(cudaEventRecord(ev, hs[v]->st), "event record");
+        CK(cudaStreamWaitEvent(st, ev, 0), "stream wait");
+      }
+  }
+  std::vector<int> segs;
+  int ret = 0;
+  if (!o.use_graph) {
+    ret = batch_body(c, st, segs);
+  } else {
+    // key: handles and their stream state, pointers, sizes, options
+    std::vector<long long> key = {k, o.chunk, o.ring_chunks};
+    for (int v = 0; v < k; ++v) {
+      const vimg_handle* hv = hs[v];
+      key.insert(key.end(), {hv->id, hv->frames_seen, hv->carry_n, hv->carry_cur, ns[v],
+                             (long long)(uintptr_t)d_frames[v],
+                             (long long)(uintptr_t)entry(d_shifts_out, v),
+                             (long long)(uintptr_t)entry(d_corrected_out, v),
+                             (long long)(uintptr_t)entry(d_summary_out, v)});
+    }
+    vimg_handle::GraphEntry* hit = nullptr;
+    for (auto& ge : h->graphs)
+      if (ge.key == key) hit = &ge;
+    if (hit) {
+      CK(cudaGraphLaunch(hit->exec, st), "graph launch");
+      for (int v = 0; v < k; ++v) {
+        hs[v]->frames_seen = hit->end_state[3 * v];
+        hs[v]->carry_n = (int)hit->end_state[3 * v + 1];
+        hs[v]->carry_cur = (int)hit->end_state[3 * v + 2];
+      }
+      segs = hit->segs;
+      ret = hit->ret;
+    } else {
+      std::vector<long long> saved;
+      for (int v = 0; v < k; ++v)
+        saved.insert(saved.end(), {hs[v]->frames_seen, hs[v]->carry_n, hs[v]->carry_cur});
+      auto restore = [&]() {
+        for (int v = 0; v < k; ++v) {
+          hs[v]->frames_seen = saved[3 * v];
+          hs[v]->carry_n = (int)saved[3 * v + 1];
+          hs[v]->carry_cur = (int)saved[3 * v + 2];
+        }
+      };
+      // Recorded on a private stream (the legacy default stream cannot be
+      // captured), launched on st.
+      if (!h->cap_st)
+        CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking), "capture stream");
+      CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed), "graph capture begin");
+      ret = batch_body(c, h->cap_st, segs);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap_st, &graph);
+      if (ret < 0 || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        restore();
+        if (ret < 0) return ret;
+        return cuda_fail(h, e, "graph capture end");
+      }
+      cudaGraphExec_t exec = nullptr;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        restore();
+        return cuda_fail(h, e, "graph instantiate");
+      }
+      e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        restore();
+        return cuda_fail(h, e, "graph launch");
+      }
+      vimg_handle::GraphEntry ge;
+      ge.key = std::move(key);
+      ge.exec = exec;
+      for (int v = 0; v < k; ++v)
+        ge.end_state.insert(ge.end_state.end(),
+                            {hs[v]->frames_seen, hs[v]->carry_n, hs[v]->carry_cur});
+      ge.segs = segs;
+      ge.ret = ret;
+      if (h->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+      }
+      h->graphs.push_back(std::move(ge));
+    }
+  }
+  if (ev && ret >= 0) {
+    CK(cudaEventRecord(ev, st), "event record");
+    for (int v = 1; v < k; ++v)
+      if (hs[v]->st != st) CK(cudaStreamWaitEvent(hs[v]->st, ev, 0), "stream wait");
+  }
+  if (ret >= 0 && segments_out)
+    for (int v = 0; v < k; ++v) segments_out[v] = segs[v];
+  return ret;
 }
 
 extern "C" int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n,

@@ -80,17 +80,43 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 // rows y0 - R .. y0 + 21 (ny - 1) + R, likewise for columns.  One CTA per
 // 56 x 32 block of positions per frame: row sums slide along x, window sums
 // slide along y, all in 64-bit integers.
+constexpr int kGroup = 11;  // patches per FP32 correlation work item (see k_corr_f32)
 constexpr int kBoxRows = 56, kBoxCols = 32, kBoxThreads = 256;
 constexpr int kBoxIR = kBoxRows + kPatch - 1, kBoxIC = kBoxCols + kPatch - 1;  // 76 x 52 inputs
 constexpr int kBoxInStride = kBoxIC + 1;     // 53: odd, so rows fall in distinct banks
 constexpr int kBoxRsStride = kBoxCols + 1;   // 33
 constexpr int kBoxLoads = (kBoxIR * kBoxIC + kBoxThreads - 1) / kBoxThreads;     // 16
 
+// Stats-map geometry for a patch grid.
+__host__ __device__ inline void stats_map_dims(PatchGrid g, int R, int* oy, int* ox, int* sh,
+                                               int* sw) {
+  *oy = g.y0 - R;
+  *ox = g.x0 - R;
+  *sh = kPatch * (g.ny - 1) + 2 * R + 1;
+  *sw = kPatch * (g.nx - 1) + 2 * R + 1;
+}
+
+__host__ __device__ inline int stats_tiles(PatchGrid g, int R) {
+  int oy, ox, sh, sw;
+  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+  return ((sw + kBoxCols - 1) / kBoxCols) * ((sh + kBoxRows - 1) / kBoxRows);
+}
+
+// One CTA per (job, frame, block of positions); the job comes from the prefix
+// counts of the table.
 __global__ void __launch_bounds__(kBoxThreads)
-    k_boxstats(const uint16_t* __restrict__ frames, int H, int W, int oy, int ox, int sh, int sw,
-               float* __restrict__ isf) {
-  const int f = blockIdx.z;
-  const int by = blockIdx.y * kBoxRows, bx = blockIdx.x * kBoxCols;
+    k_boxstats(const __grid_constant__ MotionBatch b) {
+  const int jb = job_of(b.stats_begin, b.n, blockIdx.x);
+  const MotionJob& J = b.j[jb];
+  const int H = J.H, W = J.W;
+  int oy, ox, sh, sw;
+  stats_map_dims(J.g, J.R, &oy, &ox, &sh, &sw);
+  const int ntx = (sw + kBoxCols - 1) / kBoxCols, per = ntx * ((sh + kBoxRows - 1) / kBoxRows);
+  const int local = blockIdx.x - b.stats_begin[jb];
+  const int f = local / per, rem = local - f * per;
+  const int by = (rem / ntx) * kBoxRows, bx = (rem % ntx) * kBoxCols;
+  const uint16_t* __restrict__ frames = J.frames;
+  float* __restrict__ isf = J.isf;
   __shared__ int in[kBoxIR * kBoxInStride];
   __shared__ int rs1[kBoxIR * kBoxRsStride];
   __shared__ long long rs2[kBoxIR * kBoxRsStride];
@@ -158,30 +184,53 @@ __global__ void __launch_bounds__(kBoxThreads)
   }
 }
 
-// Stats-map geometry for a patch grid.
-__host__ __device__ inline void stats_map_dims(PatchGrid g, int R, int* oy, int* ox, int* sh,
-                                               int* sw) {
-  *oy = g.y0 - R;
-  *ox = g.x0 - R;
-  *sh = kPatch * (g.ny - 1) + 2 * R + 1;
-  *sw = kPatch * (g.nx - 1) + 2 * R + 1;
-}
-
 size_t stats_map_floats(PatchGrid g, int R) {
   int oy, ox, sh, sw;
   stats_map_dims(g, R, &oy, &ox, &sh, &sw);
   return (size_t)sh * sw;
 }
 
+static MotionJob one_job(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                         const TemplateDev& td, float* isf, unsigned long long* csum) {
+  MotionJob j{};
+  j.frames = frames, j.nf = nf, j.H = H, j.W = W, j.g = g, j.R = R;
+  j.tc = td.tc, j.tn2 = td.tn2, j.coff = td.coff, j.isf = isf, j.csum = csum;
+  return j;
+}
+
+bool motion_batch_finalize(MotionBatch& b) {
+  if (b.n < 1 || b.n > kMaxVideos) return false;
+  long long s = 0, c = 0, p = 0;
+  b.stats_begin[0] = b.corr_begin[0] = b.peak_begin[0] = 0;
+  for (int i = 0; i < b.n; ++i) {
+    const MotionJob& J = b.j[i];
+    if (J.nf < 0 || J.R < 0 || J.R > kMaxR || J.g.ny < 1 || J.g.nx < 1) return false;
+    s += (long long)J.nf * stats_tiles(J.g, J.R);
+    c += (long long)J.nf * J.g.ny * ((J.g.nx + kGroup - 1) / kGroup);
+    p += J.nf;
+    if (s > INT_MAX || c > INT_MAX) return false;
+    b.stats_begin[i + 1] = (int)s;
+    b.corr_begin[i + 1] = (int)c;
+    b.peak_begin[i + 1] = (int)p;
+  }
+  return true;
+}
+
+cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st) {
+  const int blocks = b.stats_begin[b.n];
+  if (blocks <= 0) return cudaSuccess;
+  k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                          const TemplateDev& td, float* isf, cudaStream_t st) {
-  (void)td;
   if (nf <= 0) return cudaSuccess;
-  int oy, ox, sh, sw;
-  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
-  dim3 grid((sw + kBoxCols - 1) / kBoxCols, (sh + kBoxRows - 1) / kBoxRows, nf);
-  k_boxstats<<<grid, kBoxThreads, 0, st>>>(frames, H, W, oy, ox, sh, sw, isf);
-  return cudaGetLastError();
+  MotionBatch b{};
+  b.n = 1;
+  b.j[0] = one_job(frames, nf, H, W, g, R, td, isf, nullptr);
+  if (!motion_batch_finalize(b)) return cudaErrorInvalidValue;
+  return launch_stats_multi(b, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -203,7 +252,6 @@ cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid
 // each with its own shared buffers.  Group 1 starts once group 0 has staged its
 // first item, so from then on one group's staging (global-memory latency) runs
 // while the other group computes, and the SM's FMA pipes stay busy.
-constexpr int kGroup = 11;
 constexpr int kCsEntries = kMaxWin * kMaxWin + 1;  // keeps what follows 16-byte aligned
 constexpr int kRegionRows = kPatch + 2 * kMaxR;                     // 53
 constexpr int kRegionStride = (kGroup * kPatch + 2 * kMaxR) | 1;    // 263
@@ -250,10 +298,7 @@ __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
 
 template <int NX>
 __global__ void __launch_bounds__(kCorrThreads, 1)
-    k_corr_f32(const uint16_t* __restrict__ frames, int nf, int H, int W, PatchGrid g, int R,
-               const float* __restrict__ tc, const float* __restrict__ tn2,
-               const int* __restrict__ coff, const float* __restrict__ isf,
-               unsigned long long* __restrict__ csum, const int* __restrict__ list,
+    k_corr_f32(const __grid_constant__ MotionBatch b, const int* __restrict__ list,
                const int* __restrict__ list_n) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int grp = threadIdx.x / kGroupThreads, gtid = threadIdx.x - grp * kGroupThreads;
@@ -261,14 +306,13 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem + grp * kGroupSmem);
   float* ism = reinterpret_cast<float*>(cs + kCsEntries);  // [w][scols]
   float* reg = ism + kMaxWin * kIsfCols;                   // [rows][rs]
-  const int w = 2 * R + 1, rows = kPatch + 2 * R;
-  const int groups_per_row = (g.nx + kGroup - 1) / kGroup;
-  // With a frame list (fallback frames of the learned proposal) only the listed
-  // frames are processed; their count is read from device memory.
-  const int n_frames = list ? min(nf, *list_n) : nf;
-  const int items_per_frame = g.ny * groups_per_row, n_items = n_frames * items_per_frame;
-  int oy, ox, sh, sw;
-  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+  // With a frame list (fallback frames of the learned proposal; one job) only the
+  // listed frames are processed; their count is read from device memory.
+  int n_items = b.corr_begin[b.n];
+  if (list) {
+    const PatchGrid g0 = b.j[0].g;
+    n_items = min(b.j[0].nf, *list_n) * g0.ny * ((g0.nx + kGroup - 1) / kGroup);
+  }
   const int bar = 1 + grp;  // named barrier of this group (0 is __syncthreads)
 
   if (grp == 1) asm volatile("bar.sync 3, %0;" ::"r"(kCorrThreads) : "memory");
@@ -276,8 +320,23 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   for (int k = grp;; k += 2) {
     const int item = blockIdx.x + k * gridDim.x;
     if (item >= n_items) break;
-    const int fi = item / items_per_frame, rem = item - fi * items_per_frame;
+    const int jb = list ? 0 : job_of(b.corr_begin, b.n, item);
+    const MotionJob& J = b.j[jb];
+    const PatchGrid g = J.g;
+    const int R = J.R, H = J.H, W = J.W;
+    const int w = 2 * R + 1, rows = kPatch + 2 * R;
+    const int groups_per_row = (g.nx + kGroup - 1) / kGroup;
+    const int items_per_frame = g.ny * groups_per_row;
+    int oy, ox, sh, sw;
+    stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+    const int local = item - (list ? 0 : b.corr_begin[jb]);
+    const int fi = local / items_per_frame, rem = local - fi * items_per_frame;
     const int f = list ? list[fi] : fi;
+    const uint16_t* __restrict__ frames = J.frames;
+    const float* __restrict__ tc = J.tc;
+    const float* __restrict__ tn2 = J.tn2;
+    const float* __restrict__ isf = J.isf;
+    unsigned long long* __restrict__ csum = J.csum;
     const int py = rem / groups_per_row, gx = rem - py * groups_per_row;
     const int px0 = gx * kGroup, G = min(kGroup, g.nx - px0);
     const int cols = G * kPatch + 2 * R;
@@ -287,7 +346,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
     const int scols = (G - 1) * kPatch + w;       // isf columns this item uses
     const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
     const int p0 = py * g.nx + px0;
-    const float c = (float)coff[p0];
+    const float c = (float)J.coff[p0];
 
     // Stage: every thread first issues its global loads (one round trip per
     // batch), then converts and stores.
@@ -379,29 +438,42 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   if (grp == 0 && !released) asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
 }
 
+static int g_sms = 0;
+
+cudaError_t kernels_init() {
+  if (g_sms) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * kGroupSmem));
+  if (e == cudaSuccess) e = temporal_init();
+  if (e == cudaSuccess) g_sms = sms;
+  return e;
+}
+
+cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st, const int* list,
+                                  const int* list_n) {
+  const int items = b.corr_begin[b.n];
+  if (items <= 0) return cudaSuccess;
+  cudaError_t e = kernels_init();
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(g_sms, (items + 1) / 2);
+  k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(b, list, list_n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
                             unsigned long long* csum, cudaStream_t st, const int* list,
                             const int* list_n) {
   if (nf <= 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(2 * kGroupSmem));
-    if (e != cudaSuccess) {
-      sms = 0;
-      return e;
-    }
-  }
-  const int items = nf * g.ny * ((g.nx + kGroup - 1) / kGroup);
-  const int grid = std::min(sms, (items + 1) / 2);
-  k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(
-      frames, nf, H, W, g, R, td.tc, td.tn2, td.coff, isf, csum, list, list_n);
-  return cudaGetLastError();
+  MotionBatch b{};
+  b.n = 1;
+  b.j[0] = one_job(frames, nf, H, W, g, R, td, const_cast<float*>(isf), csum);
+  if (!motion_batch_finalize(b)) return cudaErrorInvalidValue;
+  return launch_corr_f32_multi(b, st, list, list_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,12 +544,17 @@ __device__ __forceinline__ int peak_of(const long long* C, int wy, int wx, int o
   return b.idx;
 }
 
-__global__ void k_peak(const unsigned long long* __restrict__ csum, int R, int np,
-                       float* __restrict__ shifts, float* __restrict__ info,
-                       double* __restrict__ surface, const int* __restrict__ list,
+__global__ void k_peak(const __grid_constant__ MotionBatch mb, const int* __restrict__ list,
                        const int* __restrict__ list_n) {
   if (list && (int)blockIdx.x >= *list_n) return;
-  const int f = list ? list[blockIdx.x] : blockIdx.x;
+  const int jb = list ? 0 : job_of(mb.peak_begin, mb.n, blockIdx.x);
+  const MotionJob& J = mb.j[jb];
+  const int f = list ? list[blockIdx.x] : (int)blockIdx.x - mb.peak_begin[jb];
+  const int R = J.R, np = J.g.ny * J.g.nx;
+  const unsigned long long* __restrict__ csum = J.csum;
+  float* __restrict__ shifts = J.shifts;
+  float* __restrict__ info = J.info;
+  double* __restrict__ surface = J.surface;
   const int lane = threadIdx.x, w = 2 * R + 1, nw = w * w;
   const long long* C = reinterpret_cast<const long long*>(csum) + (size_t)f * nw;
   Cand b, s2;
@@ -500,12 +577,26 @@ __global__ void k_peak(const unsigned long long* __restrict__ csum, int R, int n
   }
 }
 
+cudaError_t launch_peak_multi(const MotionBatch& b, cudaStream_t st, const int* list,
+                              const int* list_n) {
+  const int blocks = b.peak_begin[b.n];
+  if (blocks <= 0) return cudaSuccess;
+  k_peak<<<blocks, 32, 0, st>>>(b, list, list_n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, float* shifts,
                         float* peak_info, double* surface, cudaStream_t st, const int* list,
                         const int* list_n) {
   if (nf <= 0) return cudaSuccess;
-  k_peak<<<nf, 32, 0, st>>>(csum, R, np, shifts, peak_info, surface, list, list_n);
-  return cudaGetLastError();
+  MotionBatch b{};
+  b.n = 1;
+  MotionJob& j = b.j[0];
+  j.csum = const_cast<unsigned long long*>(csum);
+  j.nf = nf, j.R = R, j.g = PatchGrid{1, np, 0, 0};
+  j.shifts = shifts, j.info = peak_info, j.surface = surface;
+  b.peak_begin[0] = 0, b.peak_begin[1] = nf;
+  return launch_peak_multi(b, st, list, list_n);
 }
 
 // ---------------------------------------------------------------------------

@@ -20,6 +20,7 @@
 // exact running sum in 2^-16 fixed point (64-bit integers); values leaving the
 // window are recomputed from their frames rather than stored.
 #include <cfloat>
+#include <climits>
 
 #include "vimg_internal.h"
 
@@ -243,8 +244,11 @@ constexpr int kFst = 58;                 // staged frame row stride (uint16), >=
 constexpr int kFstRows = 57;
 constexpr int kPfRows = (kFstRows + 7) / 8;  // prefetch: 64 columns x 8 rows per pass
 
-__global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
+// One CTA per (job, segment slot, tile); the job comes from the prefix counts.
+__global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_constant__ TemporalBatch b) {
   extern __shared__ __align__(16) float sm[];
+  const int jb = job_of(b.begin, b.n, blockIdx.x);
+  const TemporalArgs& a = b.a[jb];
   const int H = a.H, W = a.W, L = a.L, HW = H * W;
   float* vext = sm;                            // [56][56] resampled tile + halo
   float* hbuf = vext + kExt * kExt;            // [56][32] row-smoothed
@@ -253,14 +257,16 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
   unsigned short* fst = reinterpret_cast<unsigned short*>(shs + 2 * kMaxL);
   unsigned short* rtab = fst + kFstRows * kFst;  // [56] row entries
   unsigned short* ctab = rtab + kExt;            // [56] column entries
-  const int ntx = (W + kTile - 1) / kTile;
-  const int ty0 = (blockIdx.x / ntx) * kTile, tx0 = (blockIdx.x % ntx) * kTile;
+  const int ntx = (W + kTile - 1) / kTile, tiles = ntx * ((H + kTile - 1) / kTile);
+  const int local = blockIdx.x - b.begin[jb];
+  const int slot = local / tiles, tile = local - slot * tiles;
+  const int ty0 = (tile / ntx) * kTile, tx0 = (tile % ntx) * kTile;
   const int tid = threadIdx.x, lx = tid & 31, ly0 = (tid >> 5) * 2;
   const int x = tx0 + lx, ya = ty0 + ly0, yb = ya + 1;
   const bool va = ya < H && x < W, vb = yb < H && x < W;
   const FrameSource& src = a.src;
   const long long t_end = src.t_first + src.n_carry + src.n_batch;
-  const long long s0 = a.seg_base + (long long)blockIdx.y * L;
+  const long long s0 = a.seg_base + (long long)slot * L;
   const long long s1 = s0 + L < t_end ? s0 + L : t_end;
   const int nfr = (int)(s1 - s0);
   const bool complete = s0 + L <= t_end;
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(TemporalArgs a) {
     hrow[kTile] = b_b;
   }
   if (!complete || !a.summary) return;
-  float* S = a.summary + (size_t)blockIdx.y * 2 * HW;
+  float* S = a.summary + (size_t)slot * 2 * HW;
   float* T = S + HW;
   const float invL = 1.0f / (float)L;
   for (int q = 0; q < 2; ++q) {
@@ -474,18 +480,47 @@ static size_t temporal_smem(int L) {
          sizeof(unsigned short) * (kFstRows * kFst + 2 * kExt);
 }
 
+cudaError_t temporal_init() {
+  static bool attr_set = false;
+  if (attr_set) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)temporal_smem(kMaxL));
+  if (e == cudaSuccess) attr_set = true;
+  return e;
+}
+
+bool temporal_batch_finalize(TemporalBatch& b) {
+  if (b.n < 1 || b.n > kMaxVideos) return false;
+  long long s = 0;
+  b.begin[0] = 0;
+  for (int i = 0; i < b.n; ++i) {
+    const TemporalArgs& a = b.a[i];
+    if (a.n_seg < 0 || a.L < 1 || a.L > kMaxL || a.H < 1 || a.W < 1) return false;
+    s += (long long)a.n_seg * (((a.H + kTile - 1) / kTile) * ((a.W + kTile - 1) / kTile));
+    if (s > INT_MAX) return false;
+    b.begin[i + 1] = (int)s;
+  }
+  return true;
+}
+
+cudaError_t launch_temporal_multi(const TemporalBatch& b, cudaStream_t st) {
+  const int blocks = b.begin[b.n];
+  if (blocks <= 0) return cudaSuccess;
+  cudaError_t e = temporal_init();
+  if (e != cudaSuccess) return e;
+  int L = 1;
+  for (int i = 0; i < b.n; ++i) L = L > b.a[i].L ? L : b.a[i].L;
+  k_temporal<<<blocks, kTempThreads, temporal_smem(L), st>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st) {
   if (a.n_seg <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)temporal_smem(kMaxL));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const int tiles = ((a.H + kTile - 1) / kTile) * ((a.W + kTile - 1) / kTile);
-  k_temporal<<<dim3(tiles, a.n_seg), kTempThreads, temporal_smem(a.L), st>>>(a);
-  return cudaGetLastError();
+  TemporalBatch b{};
+  b.n = 1;
+  b.a[0] = a;
+  if (!temporal_batch_finalize(b)) return cudaErrorInvalidValue;
+  return launch_temporal_multi(b, st);
 }
 
 }  // namespace vimg

@@ -60,6 +60,61 @@ struct TemporalArgs {
   float* summary;                     // [k][2][H][W] or null (slot j -> index j)
 };
 
+// ---- several videos per launch ----------------------------------------------
+// The motion and temporal kernels take a table of per-video jobs by value
+// (__grid_constant__); a CTA finds its job from the prefix counts of work items.
+// A single video is a table of one job.
+constexpr int kMaxVideos = 8;
+
+struct MotionJob {
+  const uint16_t* frames;     // [nf][H][W]
+  float* isf;                 // [nf][stats map] per-window 1/sqrt(SF)
+  unsigned long long* csum;   // [nf][w*w] fixed-point C sums
+  const float* tc;            // template constants (TemplateDev)
+  const float* tn2;
+  const int* coff;
+  float* shifts;              // [nf][2] or null
+  float* info;                // [nf][4] or null
+  double* surface;            // [nf][w*w] or null
+  PatchGrid g;
+  int nf, H, W, R;
+};
+
+struct MotionBatch {
+  int n;                               // jobs in use
+  int stats_begin[kMaxVideos + 1];     // prefix counts of work items per kernel
+  int corr_begin[kMaxVideos + 1];
+  int peak_begin[kMaxVideos + 1];
+  MotionJob j[kMaxVideos];
+};
+
+struct TemporalBatch {
+  int n;
+  int begin[kMaxVideos + 1];  // prefix counts of (tile, segment slot) items
+  TemporalArgs a[kMaxVideos];
+};
+
+// Job index of work item `item` (begin[] ascending, begin[0] = 0).
+__host__ __device__ __forceinline__ int job_of(const int* begin, int n, int item) {
+  int j = 0;
+  while (j + 1 < n && item >= begin[j + 1]) ++j;
+  return j;
+}
+
+// Fills the prefix counts; returns false if a job is malformed.
+bool motion_batch_finalize(MotionBatch& b);
+bool temporal_batch_finalize(TemporalBatch& b);
+// One launch per stage over every job of the table.
+cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st);
+cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st,
+                                  const int* list = nullptr, const int* list_n = nullptr);
+cudaError_t launch_peak_multi(const MotionBatch& b, cudaStream_t st, const int* list = nullptr,
+                              const int* list_n = nullptr);
+cudaError_t launch_temporal_multi(const TemporalBatch& b, cudaStream_t st);
+// Sets kernel attributes once (before any stream capture).
+cudaError_t kernels_init();
+cudaError_t temporal_init();
+
 // ---- launchers (each enqueues on `st`; returns cudaGetLastError()) ----------
 cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, TemplateDev td,
                                  cudaStream_t st);

@@ -46,6 +46,15 @@ class IO(ctypes.Structure):
     ]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [
+        ("chunk", ctypes.c_int),
+        ("ring_chunks", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+    ]
+
+
 # Every symbol include/vimg.h declares (checked by the host-only tests).
 EXPORTS = [
     "vimg_default_params", "vimg_create", "vimg_destroy", "vimg_set_template", "vimg_process",
@@ -53,7 +62,7 @@ EXPORTS = [
     "vimg_version", "vimg_profile_enable", "vimg_profile_read", "vimg_motion_noalloc",
     "vimg_cnn_param_count", "vimg_cnn_workspace_floats", "vimg_cnn_prepare", "vimg_cnn_pack_bf16",
     "vimg_cnn_forward", "vimg_cnn_loss", "vimg_cnn_backward", "vimg_cnn_adam", "vimg_load_proposal",
-    "vimg_proposal_stats", "vimg_synchronize",
+    "vimg_proposal_stats", "vimg_synchronize", "vimg_process_batch",
 ]
 NSTAGES = 6
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
@@ -113,6 +122,8 @@ def _load():
     L.vimg_proposal_stats.restype = i
     L.vimg_synchronize.argtypes = [vp]
     L.vimg_synchronize.restype = i
+    L.vimg_process_batch.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, P(BatchOpts)]
+    L.vimg_process_batch.restype = i
     L.vimg_version.argtypes = []
     L.vimg_version.restype = ctypes.c_char_p
     return L
@@ -230,6 +241,38 @@ class Handle:
         cnt = (ctypes.c_longlong * NSTAGES)()
         self._check(lib.vimg_profile_read(self._h, ms, cnt, 1 if reset else 0))
         return {STAGES[i]: (ms[i], cnt[i]) for i in range(NSTAGES)}
+
+
+def _ptr_array(ts):
+    """ctypes array of device pointers (None -> NULL), or None if ts is None."""
+    if ts is None:
+        return None
+    return (ctypes.c_void_p * len(ts))(*[None if t is None else t.data_ptr() for t in ts])
+
+
+def process_batch(handles, frames, shifts=None, corrected=None, summary=None, chunk=0,
+                  ring_chunks=0, use_graph=False):
+    """Several videos per call (vimg_process_batch).  handles: list of Handle;
+    frames: list of cuda uint16 [n_v, H_v, W_v]; shifts/corrected/summary: lists
+    of preallocated cuda tensors (entries may be None) or None.  Runs on the
+    first handle's stream.  Returns the list of segments written per video."""
+    k = len(handles)
+    if k == 0 or len(frames) != k:
+        raise ValueError("one frames tensor per handle")
+    for h, f in zip(handles, frames):
+        assert f.is_cuda and f.dtype == torch.uint16 and f.is_contiguous()
+        assert f.shape[1:] == (h.H, h.W)
+    for outs in (shifts, corrected, summary):
+        assert outs is None or len(outs) == k
+    hs = (ctypes.c_void_p * k)(*[h._h for h in handles])
+    ns = (ctypes.c_int * k)(*[f.shape[0] for f in frames])
+    segs = (ctypes.c_int * k)()
+    opts = BatchOpts(chunk, ring_chunks, 1 if use_graph else 0, 0)
+    rc = lib.vimg_process_batch(hs, k, _ptr_array(frames), ns, _ptr_array(shifts),
+                                _ptr_array(corrected), _ptr_array(summary), segs,
+                                ctypes.byref(opts))
+    handles[0]._check(rc)
+    return list(segs)
 
 
 def version() -> str:
