@@ -59,7 +59,7 @@ struct vimg_handle {
   long long prop_frames = 0;
   // BF16 tensor-core correlation
   float* tround = nullptr;              // [H][W] rounded template
-  __nv_bfloat16* bt = nullptr;          // per-patch Toeplitz template blocks
+  __nv_bfloat16* as = nullptr;          // per-patch Toeplitz template stores
   float* bgc = nullptr;                 // [np][w*w] background correlation
   __nv_bfloat16* fc = nullptr;          // [max_chunk][H][Wp] frame - rounded template
   float* num = nullptr;                 // [max_chunk][np][w*w] per-patch numerators
@@ -166,7 +166,7 @@ static void free_all(vimg_handle* h) {
                   h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
                   h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
                   h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
-                  h->fb_total, h->tround, h->bt, h->bgc, h->fc, h->dev_err, h->num};
+                  h->fb_total, h->tround, h->as, h->bgc, h->fc, h->dev_err, h->num};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
@@ -279,9 +279,9 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
   if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
   if (p.flags & VIMG_CORR_BF16) {
     ALLOC(h->tround, sizeof(float) * HW);
-    ALLOC(h->bt, bf16_bt_bytes(g));
+    ALLOC(h->as, bf16_astore_bytes(g));
     ALLOC(h->bgc, sizeof(float) * h->np * h->nwin);
-    ALLOC(h->fc, sizeof(__nv_bfloat16) * (size_t)p.max_chunk * H * bf16_row_pitch(W));
+    ALLOC(h->fc, sizeof(__nv_bfloat16) * bf16_fc_elems(p.max_chunk, H, W));
     ALLOC(h->num, sizeof(float) * (size_t)p.max_chunk * h->np * h->nwin);
     if (e == cudaSuccess && bf16_tensor_map(h->tmap, h->fc, p.max_chunk, H, W) != 0)
       e = cudaErrorNotSupported;
@@ -340,7 +340,7 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
      "template copy");
   if (h->p.flags & VIMG_CORR_BF16)
     CK(bf16_template_prep(d_template, h->H, h->W, h->g, h->p.search_radius, h->td, h->tround,
-                          h->bt, h->bgc, h->st),
+                          h->as, h->bgc, h->st),
        "tensor-core template prep");
   h->have_template = true;
   return VIMG_OK;
@@ -397,8 +397,9 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
   prof_end(h, ps);
   ps = prof_begin(h, 1);
   if (h->p.flags & VIMG_CORR_BF16) {
-    CK(bf16_make_fc(frames, nf, h->H, h->W, h->tround, h->fc, h->st), "frame offset images");
-    CK(launch_corr_bf16(h->tmap, nf, R, h->g, h->bt, h->bgc, h->td, h->inv, h->num, h->csum,
+    CK(bf16_make_fc(frames, nf, h->p.max_chunk, h->H, h->W, h->tround, h->fc, h->st),
+       "frame offset images");
+    CK(launch_corr_bf16(h->tmap, nf, R, h->g, h->as, h->bgc, h->td, h->inv, h->num, h->csum,
                         h->dev_err, h->st),
        "tensor-core correlation launch");
   } else {

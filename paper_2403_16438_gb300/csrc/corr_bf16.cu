@@ -1,32 +1,47 @@
 // BF16 tensor-core (tcgen05) correlation numerators of Sec. II, FP32 accumulate.
 //
 // num_p(d) = sum_k Tc_p[k] F[k + d] = sum_k Tc_p[k] Fc[k + d] + B_p(d), where
-//   Fc = F - round(T)                  (per pixel; small magnitude, exact in FP32)
+//   Fc = F - round(T)                  (per pixel; small magnitude)
 //   B_p(d) = sum_k Tc_p[k] round(T)[k + d]   (frame independent, set per template)
 // Only Fc and Tc go through BF16; B_p is exact up to FP32 rounding.
 //
-// Implicit GEMM per patch p and group of 16 frames (one tcgen05.mma per step):
-//   D[(f, jy)][jx] += sum_{c} A[(f, jy)][(rho, c)] * Bt[(rho, c)][jx]
-//   A[(f, jy)][(rho, c)] = Fc_f[y_p - R + 8 b_y + jy + rho][x_p - R - o_p + 16 b_x + c]
-//   Bt[(rho, c)][jx]     = Tc_p[rho][c - jx - o_p]        (Toeplitz along x)
-// so D = num_p(dy = 8 b_y + jy - R, dx = 16 b_x + jx - R).  M = 128 rows =
-// 16 frames x 8 displacement rows: the displacement row comes for free from the
-// 16-byte row stride of the canonical (no swizzle, K-major) core matrices, so the
-// frames need no im2col; they arrive by TMA straight from the Fc images (one 3-D
-// box of 8 columns x 60 rows x 16 frames per column block).  Bt is precomputed
-// per patch (o_p = 8-alignment offset of the patch's window).  5 x 3 blocks of
-// (8 dy x 16 dx) cover the 33 x 33 window; K = 21 rows x 48 columns.
+// Implicit GEMM per patch p and group of up to 128 frames (N = frames):
+//   D[(xl, i)][f] += sum_{k} A[(xl, i)][k] * B[k][f]
+//   B[k][f] = Fc_f[y_p - R + y][x_p - R - o_p + 16 b + k]       (frame row y, column k)
+//   A[(xl, i)][k] = Tc_p[y - 8a - i][k - o_p - xl]              (Toeplitz in x and y)
+// so D = num_p(dy = 8a + i - R, dx = 16b + xl - R): an M = 128 block of 8 dy x 16 dx
+// displacements; a = 0..4 and b = 0..2 cover the 33 x 33 window; the K loop runs
+// over the 53 frame rows y of the patch's search region and 3 chunks of 16
+// columns.  A depends on (a, y) only through y - 8a and not on b at all, so one
+// compact store per patch serves every MMA: S[xl][c][q][j] = Tc[27 - q][8c + j -
+// o_p - xl] with template rows reversed (q = 27 - r, zero rows above and
+// below), so that the 8 rows of a core matrix -- 8 consecutive dy -- are 8
+// consecutive 16-byte rows of S starting at q0 = 27 - (y - 8a).
+// The frames arrive by TMA from Fc images laid out [row][8-column block][frame]
+// [8], so each frame row of the region is one box of 6 column blocks x 128 frames.
 //
-// N = 32: the template is split into a BF16 high part and a BF16 remainder (16 dx
-// columns each), so it enters with ~16 significant bits; only Fc is rounded.
+// One tcgen05.mma of M = 128, K = 16 costs about the same for any N in 64..128,
+// and a tcgen05.commit stalls the issuing thread for a few hundred cycles, so
+// the kernel runs N = 128 and commits rarely.  TMEM (512 columns) holds 4
+// accumulators of 128 columns: dy block a of pass P (P counts passes over all
+// units) uses slot (a + P) mod 4.  Only 4 dy blocks are ever live at once
+// (block 0 ends at row 27, block 4 starts at row 32), and the rotation gives
+// every other hand-off between passes many rows of slack.
 //
-// Each CTA (one per SM, persistent) walks (frame group, patch) work units.  One
-// thread waits for the unit's TMA loads, issues its 945 MMAs and commits them to
-// an mbarrier; as soon as they complete the next unit's loads are issued, so the
-// epilogue (hi + lo + background term -> per-patch numerators in global memory)
-// overlaps them.  k_zncc_reduce then forms C(d) = sum_p ZNCC_p(d) per frame in
-// patch order (deterministic) as 2^-40 fixed point.  Every wait is bounded: on
-// timeout the CTA records an error and stops issuing work.
+// Warp roles (one persistent CTA per SM, 320 threads):
+//   warp 8  producer: per work unit the patch's A store (bulk copy, double
+//           buffered across units), then 3 passes x 53 frame rows of B through
+//           an 8-row ring released in groups of 4 rows;
+//   warp 9  MMA issuer: per row, 3 MMAs for each dy block the row feeds; one
+//           commit per 4 rows frees a ring group, one per finished dy block
+//           hands its accumulator to the epilogue;
+//   warps 0-7 epilogue: TMEM -> registers (warp w: lanes 32 (w mod 4) .. + 31,
+//           columns 64 (w / 4) .. + 63), + B_p(d), stores of the per-patch
+//           numerators, then release of the accumulator slot.
+// k_zncc_reduce then forms C(d) = sum_p ZNCC_p(d) per frame in patch order
+// (deterministic) as 2^-40 fixed point.  Every wait is bounded: on timeout the
+// CTA records an error, stops issuing work, waits (bounded) for its own copies
+// and MMAs, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -39,19 +54,28 @@ namespace vimg {
 
 namespace {
 
-constexpr int kFr = 16;           // frames per group (M = 128 = 16 x 8)
-constexpr int kRowsA = 60;        // staged rows: 5 dy blocks x 8 + 20
-constexpr int kColBlk = 10;       // staged column blocks of 8 (80 columns)
-constexpr int kDyBlk = 5, kDxBlk = 3, kKq = 3;  // K chunks of 16 columns per template row
-constexpr int kJx = 16;                       // displacement columns per block
-constexpr int kN = 2 * kJx;                   // N = [template hi part | lo part]
-constexpr uint32_t kAColBytes = kFr * kRowsA * 16;               // 15,360 B per column block
-constexpr uint32_t kABytes = kColBlk * kAColBytes;              // 153,600 B
-constexpr uint32_t kBtBytesPerRow = 6 * 4 * 128;                // 6 K-blocks x 4 N-blocks
-constexpr uint32_t kBtBytes = kPatch * kBtBytesPerRow;          // 64,512 B per patch
-constexpr int kThreads = 128;
+constexpr int kNF = 128;           // frames per group (N of a full group)
+constexpr int kRows = 53;          // frame rows of a search region (21 + 2 R, R = 16)
+constexpr int kDyBlk = 5;          // dy blocks of 8
+constexpr int kSlots = 4;          // TMEM accumulators of kNF columns
+constexpr int kPasses = 3;         // dx blocks of 16
+constexpr int kKq = 3;             // K chunks of 16 columns per row
+constexpr int kCb = 6;             // 8-column blocks per pass window (48 columns)
+constexpr int kQ = 35;             // reversed template rows incl. zero padding
+constexpr int kXl = 16;            // dx per block
+constexpr uint32_t kASlice = kQ * 16;                  // 560 B: one (xl, c) column strip
+constexpr uint32_t kAXl = kCb * kASlice;               // 3,360 B per xl
+constexpr uint32_t kABytes = kXl * kAXl;               // 53,760 B per patch
+constexpr uint32_t kBStage = kCb * kNF * 16;           // 12,288 B per frame row
+constexpr int kStages = 8;                             // ring of frame rows
+constexpr int kGroupRows = 4;                          // rows released by one commit
+constexpr size_t kSmem = 2 * (size_t)kABytes + (size_t)kStages * kBStage;  // 205,824 B
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (kEpiWarps + 2) * 32;         // 320
 constexpr int kTmemCols = 512;
 constexpr long long kSpin = 1LL << 22;  // bounded waits (seconds at most)
+constexpr int kWin = 33;
+constexpr int kNWin = kWin * kWin;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -62,8 +86,11 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t s
          ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(128 >> 4) << 24);
+// kind::f16, A = B = BF16, D = F32, K-major A and B, M = 128, N set per group.
+__device__ __forceinline__ uint32_t idesc_for(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done = 0;
@@ -71,8 +98,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(su32(bar)), "r"(parity));
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
   return done != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -88,29 +136,55 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Position of displacement (dyi, dxi) (0..32 each) in the numerator buffer:
+// blocks (a, b) in order b-major, within a block the accumulator row order
+// m = 8 xl + i, with only the valid rows of the edge blocks (a = 4: dyi = 32;
+// b = 2: dxi = 32) kept, so a warp's stores are contiguous.
+__host__ __device__ __forceinline__ int dperm(int dyi, int dxi) {
+  const int a = dyi >> 3, i = dyi & 7, b = dxi >> 4, xl = dxi & 15;
+  const int base = b * 528;
+  if (b < 2) return base + (a < 4 ? a * 128 + xl * 8 + i : 512 + xl);
+  return base + (a < 4 ? a * 8 + i : 32);
+}
+
+// Last frame row of dy block a (rows beyond 52 only feed displacements past 32).
+__host__ __device__ __forceinline__ int last_row(int a) { return min(8 * a + 27, kRows - 1); }
+
 __global__ void __launch_bounds__(kThreads, 1)
-    k_corr_bf16(const __grid_constant__ CUtensorMap tmap, int nf, int R, PatchGrid g,
-                const __nv_bfloat16* __restrict__ bt, const float* __restrict__ bgc,
+    k_corr_bf16(const __grid_constant__ CUtensorMap tmap, int nf, PatchGrid g,
+                const __nv_bfloat16* __restrict__ astore, const float* __restrict__ bgc,
                 float* __restrict__ num, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                 // [10 col blocks][16 frames][60 rows][16 B]
-  unsigned char* sB = smem + kABytes;       // [21][6 K blocks][4 N blocks][8][8] bf16
-  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  unsigned char* sA = smem;                     // [2][kABytes]
+  unsigned char* sB = smem + 2 * kABytes;       // [kStages][kBStage]
+  __shared__ __align__(8) uint64_t full[kStages], grp_empty[kStages / kGroupRows];
+  __shared__ __align__(8) uint64_t a_full[2], a_empty[2];
+  __shared__ __align__(8) uint64_t acc_full[kSlots], acc_free[kSlots], mma_done;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
+  __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int np = g.ny * g.nx, w = 2 * R + 1, nw = w * w;
-  const int n_groups = (nf + kFr - 1) / kFr;
-  const int n_work = n_groups * np;  // (frame group, patch) pairs, patch fastest
+  const int np = g.ny * g.nx;
+  const int n_groups = (nf + kNF - 1) / kNF;
+  const int n_work = n_groups * np;  // (frame group, patch) units, patch fastest
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_load)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_mma)));
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    for (int q = 0; q < kStages / kGroupRows; ++q) mbar_init(&grp_empty[q], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&a_full[i], 1);
+      mbar_init(&a_empty[i], 1);
+    }
+    for (int a = 0; a < kSlots; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_free[a], kEpiWarps);
+    }
+    mbar_init(&mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -118,141 +192,242 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  uint32_t ph_load = 0, ph_mma = 0;
-  const int f_loc = (warp * 32 + lane) >> 3, jy = lane & 7;
 
-  // loads of one (frame group, patch) work unit: 10 TMA boxes of Fc + the patch's Bt
-  auto issue_loads = [&](int wk) {
-    const int grp = wk / np, p = wk - grp * np;
-    const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
-    const int xa = (tx - R) & ~7;  // 16-byte aligned start column
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bar_load)),
-                 "r"(kABytes + kBtBytes));
-    for (int cb = 0; cb < kColBlk; ++cb)
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-              su32(sA + cb * kAColBytes)),
-          "l"(&tmap), "r"(xa + 8 * cb), "r"(ty - R), "r"(grp * kFr), "r"(su32(&bar_load))
-          : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(sB)),
-        "l"(bt + (size_t)p * (kBtBytes / 2)), "r"(kBtBytes), "r"(su32(&bar_load))
-        : "memory");
-  };
-
-  if (tid == 0 && (int)blockIdx.x < n_work) issue_loads(blockIdx.x);
-  for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x) {
-    const int grp = wk / np, p = wk - grp * np;
-    // 1. operands of this unit have landed -> MMAs: 5 x 3 blocks x 21 rows x 3 chunks
-    if (tid == 0) {
-      if (!mbar_wait(&bar_load, ph_load)) {
-        atomicExch(err, 1);
-        abort_flag = 1;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = su32(sA), b0 = su32(sB);
-        for (int by = 0; by < kDyBlk; ++by)
-          for (int bx = 0; bx < kDxBlk; ++bx) {
-            const uint32_t d = tmem + (uint32_t)((by * kDxBlk + bx) * kN);
-            for (int rho = 0; rho < kPatch; ++rho)
-              for (int q = 0; q < kKq; ++q) {
-                const uint32_t aaddr = a0 + (uint32_t)(2 * bx + 2 * q) * kAColBytes +
-                                       (uint32_t)(8 * by + rho) * 16;
-                const uint64_t ad = desc(aaddr, kAColBytes, kRowsA * 16);
-                const uint64_t bd = desc(b0 + (uint32_t)(rho * 6 + 2 * q) * 512, 512, 128);
-                const uint32_t acc = (rho | q) ? 1u : 0u;
+  if (warp == kEpiWarps) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int it = 0, u = 0, na = 0;  // B rows, units, A copies issued
+      for (int wk = blockIdx.x; wk < n_work && !abort_flag; wk += gridDim.x, ++u) {
+        const int grp = wk / np, p = wk - grp * np;
+        const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
+        const int cb0 = (tx - kMaxR) >> 3;  // tx - R >= 0 on the patch grid
+        const int buf = u & 1;
+        if (u >= 2 && !mbar_wait(&a_empty[buf], ((u >> 1) - 1) & 1)) {
+          atomicExch(err, 1);
+          abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&a_full[buf], kABytes);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                su32(sA + buf * kABytes)),
+            "l"(astore + (size_t)p * (kABytes / 2)), "r"(kABytes), "r"(su32(&a_full[buf]))
+            : "memory");
+        ++na;
+        for (int b = 0; b < kPasses && !abort_flag; ++b)
+          for (int y = 0; y < kRows; ++y, ++it) {
+            const int s = it % kStages, cyc = it / kStages;
+            // the first row of a ring group waits until the MMAs of its previous
+            // use have completed
+            if (cyc > 0 && s % kGroupRows == 0 &&
+                !mbar_wait(&grp_empty[s / kGroupRows], (cyc - 1) & 1)) {
+              atomicExch(err, 1);
+              abort_flag = 1;
+              break;
+            }
+            mbar_expect_tx(&full[s], kBStage);
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                    su32(sB + s * kBStage)),
+                "l"(&tmap), "r"(0), "r"(grp * (kNF / 16)), "r"(cb0 + 2 * b), "r"(ty - kMaxR + y),
+                "r"(su32(&full[s]))
+                : "memory");
+          }
+      }
+      // wait (bounded) for the copies this thread issued: the last use of every stage
+      for (int s = 0; s < kStages && s < it; ++s) {
+        const int last_use = (it - 1 - s) / kStages;
+        mbar_wait(&full[s], last_use & 1);
+      }
+      for (int i = 0; i < 2 && i < na; ++i) mbar_wait(&a_full[i], ((na - 1 - i) >> 1) & 1);
+    }
+  } else if (warp == kEpiWarps + 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int it = 0, u = 0;
+      int slot_use[kSlots] = {0, 0, 0, 0};
+      bool issued = false;
+      for (int wk = blockIdx.x; wk < n_work && !abort_flag; wk += gridDim.x, ++u) {
+        const int grp = wk / np;
+        const int rem = nf - grp * kNF;
+        const int n_cols = rem >= kNF ? kNF : ((rem + 15) & ~15);
+        const uint32_t idesc = idesc_for(n_cols);
+        const int buf = u & 1;
+        if (!mbar_wait(&a_full[buf], (u >> 1) & 1)) {
+          atomicExch(err, 1);
+          abort_flag = 1;
+          break;
+        }
+        const uint32_t a0 = su32(sA + buf * kABytes);
+        for (int b = 0; b < kPasses && !abort_flag; ++b) {
+          const int pass = u * kPasses + b;
+          for (int y = 0; y < kRows; ++y, ++it) {
+            const int s = it % kStages;
+            if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+              atomicExch(err, 1);
+              abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t b0 = su32(sB + s * kBStage);
+            for (int a = 0; a < kDyBlk; ++a) {
+              if (y < 8 * a || y > last_row(a)) continue;
+              const int slot = (a + pass) & (kSlots - 1);
+              if (y == 8 * a) {
+                const int k = slot_use[slot]++;
+                if (k > 0) {
+                  if (!mbar_wait(&acc_free[slot], (k - 1) & 1)) {
+                    atomicExch(err, 1);
+                    abort_flag = 1;
+                    break;
+                  }
+                  asm volatile("tcgen05.fence::after_thread_sync;");
+                }
+              }
+              const uint32_t q0 = (uint32_t)(27 - (y - 8 * a));
+              const uint32_t d = tmem + (uint32_t)(slot * kNF);
+#pragma unroll
+              for (int qk = 0; qk < kKq; ++qk) {
+                const uint64_t ad = desc(a0 + (uint32_t)(2 * qk) * kASlice + q0 * 16, kASlice, kAXl);
+                const uint64_t bd = desc(b0 + (uint32_t)(2 * qk) * (kNF * 16), kNF * 16, 128);
+                const uint32_t acc = (y == 8 * a && qk == 0) ? 0u : 1u;
                 asm volatile(
                     "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
-                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
               }
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            su32(&bar_mma)));
-      }
-    }
-    ph_load ^= 1;
-    if (!mbar_wait(&bar_mma, ph_mma)) {
-      atomicExch(err, 1);
-      abort_flag = 1;
-    }
-    ph_mma ^= 1;
-    __syncthreads();
-    if (abort_flag) break;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // 2. the shared operands are free: start the next unit's loads now
-    if (tid == 0 && wk + (int)gridDim.x < n_work) issue_loads(wk + gridDim.x);
-    // 3. epilogue (overlaps those loads): numerator = hi + lo parts + background term
-    {
-      const int f = grp * kFr + f_loc;
-      float* out = num + ((size_t)min(f, nf - 1) * np + p) * nw;
-      const float* bg = bgc + (size_t)p * nw;
-      for (int by = 0; by < kDyBlk; ++by) {
-        const int dyi = 8 * by + jy;
-        for (int bx = 0; bx < kDxBlk; ++bx) {
-          float hv[16], lv[16];
-          tmem_ld16(tmem + lane_base + (by * kDxBlk + bx) * kN, hv);
-          tmem_ld16(tmem + lane_base + (by * kDxBlk + bx) * kN + kJx, lv);
-          if (f < nf && dyi < w) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int dxi = 16 * bx + j;
-              if (dxi < w) out[dyi * w + dxi] = hv[j] + lv[j] + __ldg(bg + dyi * w + dxi);
+              issued = true;
+              if (y == last_row(a)) mma_commit(&acc_full[slot]);
             }
+            if (abort_flag) break;
+            if (s % kGroupRows == kGroupRows - 1) mma_commit(&grp_empty[s / kGroupRows]);
           }
         }
+        if (abort_flag) break;
+        mma_commit(&a_empty[buf]);
+      }
+      // every MMA issued by this thread has completed before the CTA frees TMEM
+      if (issued) {
+        mma_commit(&mma_done);
+        mbar_wait(&mma_done, 0);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+  } else {
+    // ------ epilogue (warp w: TMEM lanes 32 (w mod 4) .. + 31, columns 64 (w / 4) .. + 63) ------
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = quad * 32 + lane, xl = m >> 3, i = m & 7;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    int u = 0;
+    int slot_use[kSlots] = {0, 0, 0, 0};
+    for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x, ++u) {
+      const int grp = wk / np, p = wk - grp * np;
+      const int nvalid = min(kNF, nf - grp * kNF);
+      const int c_lo = half * (kNF / 2), c_hi = min(nvalid, c_lo + kNF / 2);
+      const float* bg = bgc + (size_t)p * kNWin;
+      bool stop = false;
+      for (int b = 0; b < kPasses && !stop; ++b) {
+        const int pass = u * kPasses + b;
+        const int dxi = 16 * b + xl;
+        for (int a = 0; a < kDyBlk; ++a) {
+          const int slot = (a + pass) & (kSlots - 1);
+          const int k = slot_use[slot]++;
+          const int dyi = 8 * a + i;
+          const bool valid = dyi < kWin && dxi < kWin;
+          const float bgv = valid ? __ldg(bg + dyi * kWin + dxi) : 0.f;
+          const int dp = valid ? dperm(dyi, dxi) : 0;
+          if (!mbar_wait(&acc_full[slot], k & 1)) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          float* out = num + ((size_t)(grp * kNF) * np + p) * kNWin + dp;
+          for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)(slot * kNF + c0), v);
+            if (valid) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (c0 + j < c_hi) out[(size_t)(c0 + j) * np * kNWin] = v[j] + bgv;
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_free[slot]);
+        }
+      }
+      if (stop || abort_flag) break;
+    }
   }
-  // drain: a load issued for a unit this CTA will not run is impossible (it only
-  // issues the next unit it owns), so nothing is in flight here.
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// Displacement (dyi, dxi) stored at position t of a numerator row (inverse of dperm).
+__device__ __forceinline__ void dperm_inv(int t, int& dyi, int& dxi) {
+  const int b = t / 528, r = t - 528 * b;
+  if (b < 2) {
+    if (r < 512) {
+      const int a = r >> 7, mm = r & 127;
+      dyi = 8 * a + (mm & 7);
+      dxi = 16 * b + (mm >> 3);
+    } else {
+      dyi = 32;
+      dxi = 16 * b + (r - 512);
+    }
+  } else if (r < 32) {
+    dyi = r;
+    dxi = 32;
+  } else {
+    dyi = 32;
+    dxi = 32;
+  }
+}
+
 // ZNCC of every (frame, displacement) summed over the patches in patch order:
 //   C(d) = sum_p num_p(d) * 21 / |Tc_p| * isf(window_p(d)),  stored in 2^-40 fixed point.
-__global__ void k_zncc_reduce(const float* __restrict__ num, int nf, int R, PatchGrid g,
+// Thread = storage position t (contiguous numerator reads); the patch loop is
+// unrolled so that several patches' loads are in flight.
+__global__ void k_zncc_reduce(const float* __restrict__ num, int nf, PatchGrid g,
                               const float* __restrict__ tn2, const float* __restrict__ isf,
                               int sh, int sw, unsigned long long* __restrict__ csum) {
-  const int f = blockIdx.y, w = 2 * R + 1, nw = w * w, np = g.ny * g.nx;
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= nw) return;
-  const int dy = d / w, dx = d - dy * w;
-  const float* nf_ = num + (size_t)f * np * nw + d;
+  const int f = blockIdx.y, np = g.ny * g.nx;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kNWin || f >= nf) return;
+  int dy, dx;
+  dperm_inv(t, dy, dx);
+  const float* nf_ = num + (size_t)f * np * kNWin + t;
   const float* is = isf + (size_t)f * sh * sw + (size_t)dy * sw + dx;
   float acc = 0.f;
-  for (int p = 0; p < np; ++p) {
-    const int py = p / g.nx, px = p - py * g.nx;
-    const float t2 = __ldg(tn2 + p);
-    const float ps = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
-    acc = fmaf(__ldg(nf_ + (size_t)p * nw) * ps, __ldg(is + (size_t)py * kPatch * sw + px * kPatch), acc);
+  int p = 0;
+  for (int py = 0; py < g.ny; ++py) {
+    const float* isr = is + (size_t)py * kPatch * sw;
+#pragma unroll 4
+    for (int px = 0; px < g.nx; ++px, ++p) {
+      const float t2 = __ldg(tn2 + p);
+      const float ps = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+      acc = fmaf(__ldg(nf_ + (size_t)p * kNWin) * ps, __ldg(isr + px * kPatch), acc);
+    }
   }
-  csum[(size_t)f * nw + d] = (unsigned long long)__float2ll_rn(acc * (float)kFix);
+  csum[(size_t)f * kNWin + dy * kWin + dx] = (unsigned long long)__float2ll_rn(acc * (float)kFix);
 }
 
 // ---- per-template constants -----------------------------------------------------
-// Bt_p: [rho][K block 0..5][N block 0..3][n%8][c%8] bf16, n = part * 16 + jx:
-// part 0 = bf16(Tc_p[rho][c - jx - o_p]), part 1 = bf16 of the remainder, so the
-// two parts carry the template to ~16 significant bits.
-__global__ void k_bt_prep(const float* __restrict__ tc, PatchGrid g, int R,
-                          __nv_bfloat16* __restrict__ bt) {
+// A store of patch p: [xl][c][q][j] bf16 = Tc_p[27 - q][8 c + j - o_p - xl] (0 outside).
+__global__ void k_a_prep(const float* __restrict__ tc, PatchGrid g,
+                         __nv_bfloat16* __restrict__ as) {
   const int p = blockIdx.x;
-  const int tx = g.x0 + (p % g.nx) * kPatch, o = (tx - R) & 7;
+  const int tx = g.x0 + (p % g.nx) * kPatch, o = (tx - kMaxR) & 7;
   const float* t = tc + (size_t)p * kPatch * kTplStride;
-  __nv_bfloat16* out = bt + (size_t)p * (kBtBytes / 2);
-  for (int i = threadIdx.x; i < (int)(kBtBytes / 2); i += blockDim.x) {
-    const int rho = i / (kBtBytesPerRow / 2), r = i % (kBtBytesPerRow / 2);
-    const int kb = r / 256, nb = (r / 64) & 3, n = nb * 8 + ((r >> 3) & 7), c = kb * 8 + (r & 7);
-    const int part = n / kJx, jx = n % kJx, kx = c - jx - o;
-    const float v = kx >= 0 && kx < kPatch ? t[rho * kTplStride + kx] : 0.f;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    out[i] = part == 0 ? hi : __float2bfloat16_rn(v - __bfloat162float(hi));
+  __nv_bfloat16* out = as + (size_t)p * (kABytes / 2);
+  for (int e = threadIdx.x; e < (int)(kABytes / 2); e += blockDim.x) {
+    const int j = e & 7, q = (e >> 3) % kQ, c = (e / (8 * kQ)) % kCb, x = e / (8 * kQ * kCb);
+    const int r = 27 - q, s = 8 * c + j - o - x;
+    const float v = (r >= 0 && r < kPatch && s >= 0 && s < kPatch) ? t[r * kTplStride + s] : 0.f;
+    out[e] = __float2bfloat16_rn(v);
   }
 }
 
@@ -283,19 +458,27 @@ __global__ void k_round_template(const float* __restrict__ T, int n, float* __re
   if (i < n) out[i] = fminf(65535.f, fmaxf(0.f, rintf(T[i])));
 }
 
-// Fc = F - round(T) as BF16, rows padded to Wp columns.
-__global__ void k_fc(const uint16_t* __restrict__ frames, int nf, int H, int W, int Wp,
+// Fc = F - round(T) as BF16 in the layout [row][8-column block][frame][8] with
+// fcap frame slots (columns past W are zero).  Thread = (frame, row, block), frame
+// fastest, so the 16-byte stores of a warp are contiguous.
+__global__ void k_fc(const uint16_t* __restrict__ frames, int nf, int H, int W, int ncb, int fcap,
                      const float* __restrict__ tround, __nv_bfloat16* __restrict__ fc) {
-  const size_t total = (size_t)nf * H * Wp;
+  const size_t total = (size_t)nf * H * ncb;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % Wp);
-    const size_t r = i / Wp;
-    const int y = (int)(r % H);
-    const size_t f = r / H;
-    float v = 0.f;
-    if (x < W) v = (float)frames[(f * H + y) * W + x] - tround[(size_t)y * W + x];
-    fc[i] = __float2bfloat16_rn(v);
+    const int f = (int)(i % nf);
+    const size_t r = i / nf;
+    const int cb = (int)(r % ncb), y = (int)(r / ncb);
+    const uint16_t* src = frames + ((size_t)f * H + y) * W;
+    const float* tr = tround + (size_t)y * W;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int x = 8 * cb + j;
+      v[j] = __float2bfloat16_rn(x < W ? (float)__ldg(src + x) - __ldg(tr + x) : 0.f);
+    }
+    *reinterpret_cast<uint4*>(fc + (((size_t)y * ncb + cb) * fcap + f) * 8) =
+        *reinterpret_cast<const uint4*>(v);
   }
 }
 
@@ -317,76 +500,85 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+int fc_slots(int cap_frames) { return (cap_frames + 15) & ~15; }
+
 }  // namespace
 
-size_t bf16_bt_bytes(PatchGrid g) { return (size_t)g.ny * g.nx * kBtBytes; }
+size_t bf16_astore_bytes(PatchGrid g) { return (size_t)g.ny * g.nx * kABytes; }
 int bf16_row_pitch(int W) { return (W + 7) & ~7; }
+size_t bf16_fc_elems(int cap_frames, int H, int W) {
+  return (size_t)fc_slots(cap_frames) * H * bf16_row_pitch(W);
+}
 
 cudaError_t bf16_template_prep(const float* T, int H, int W, PatchGrid g, int R,
-                               const TemplateDev& td, float* tround, __nv_bfloat16* bt,
+                               const TemplateDev& td, float* tround, __nv_bfloat16* as,
                                float* bgc, cudaStream_t st) {
   const int n = H * W;
   k_round_template<<<(n + 255) / 256, 256, 0, st>>>(T, n, tround);
-  k_bt_prep<<<g.ny * g.nx, 256, 0, st>>>(td.tc, g, R, bt);
+  k_a_prep<<<g.ny * g.nx, 256, 0, st>>>(td.tc, g, as);
   k_bg_corr<<<g.ny * g.nx, 256, 0, st>>>(td.tc, td.coff, tround, W, g, R, bgc);
   return cudaGetLastError();
 }
 
-cudaError_t bf16_make_fc(const uint16_t* frames, int nf, int H, int W, const float* tround,
-                         __nv_bfloat16* fc, cudaStream_t st) {
+cudaError_t bf16_make_fc(const uint16_t* frames, int nf, int cap_frames, int H, int W,
+                         const float* tround, __nv_bfloat16* fc, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
-  const int Wp = bf16_row_pitch(W);
-  const size_t total = (size_t)nf * H * Wp;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  k_fc<<<blocks, 256, 0, st>>>(frames, nf, H, W, Wp, tround, fc);
+  const int ncb = bf16_row_pitch(W) / 8;
+  const size_t total = (size_t)nf * H * ncb;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 8192);
+  k_fc<<<blocks, 256, 0, st>>>(frames, nf, H, W, ncb, fc_slots(cap_frames), tround, fc);
   return cudaGetLastError();
 }
 
-// Tensor map over Fc [cap_frames][H][Wp] bf16 with 8 x 60 x 16 boxes.
+// Tensor map over Fc [H][ncb][fcap][8] bf16 as 4-D {128 = 16 frames x 8, fcap/16, ncb, H}
+// with boxes {128, 8, 6, 1}: one frame row, 6 column blocks, 128 frames.
 int bf16_tensor_map(void* map_out, __nv_bfloat16* fc, int cap_frames, int H, int W) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return -1;
-  const int Wp = bf16_row_pitch(W);
-  cuuint64_t dims[3] = {(cuuint64_t)Wp, (cuuint64_t)H, (cuuint64_t)cap_frames};
-  cuuint64_t strides[2] = {(cuuint64_t)Wp * 2, (cuuint64_t)Wp * H * 2};
-  cuuint32_t box[3] = {8, kRowsA, kFr};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, fc,
+  const int ncb = bf16_row_pitch(W) / 8, fcap = fc_slots(cap_frames);
+  cuuint64_t dims[4] = {128, (cuuint64_t)fcap / 16, (cuuint64_t)ncb, (cuuint64_t)H};
+  cuuint64_t strides[3] = {256, (cuuint64_t)fcap * 16, (cuuint64_t)ncb * fcap * 16};
+  cuuint32_t box[4] = {128, kNF / 16, kCb, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, fc,
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -2;
 }
 
 size_t bf16_tensor_map_bytes() { return sizeof(CUtensorMap); }
 
+size_t bf16_num_floats(int cap_frames, PatchGrid g) {
+  return (size_t)cap_frames * g.ny * g.nx * kNWin;
+}
+
 cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
-                             const __nv_bfloat16* bt, const float* bgc, const TemplateDev& td,
+                             const __nv_bfloat16* as, const float* bgc, const TemplateDev& td,
                              const float* isf, float* num, unsigned long long* csum, int* err,
                              cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
+  if (R != kMaxR) return cudaErrorInvalidValue;
   static int sms = 0;
-  const size_t smem = kABytes + kBtBytes;
   if (!sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_corr_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(k_corr_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) {
       sms = 0;
       return e;
     }
   }
-  const int np = g.ny * g.nx, groups = (nf + kFr - 1) / kFr, w = 2 * R + 1;
+  const int np = g.ny * g.nx, groups = (nf + kNF - 1) / kNF;
   const CUtensorMap* map = static_cast<const CUtensorMap*>(tmap);
-  k_corr_bf16<<<std::min(groups * np, sms), kThreads, smem, st>>>(*map, nf, R, g, bt, bgc, num,
-                                                                  err);
+  k_corr_bf16<<<std::min(groups * np, sms), kThreads, kSmem, st>>>(*map, nf, g, as, bgc, num, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int sh = kPatch * (g.ny - 1) + 2 * R + 1, sw = kPatch * (g.nx - 1) + 2 * R + 1;
-  k_zncc_reduce<<<dim3((w * w + 127) / 128, nf), 128, 0, st>>>(num, nf, R, g, td.tn2, isf, sh, sw,
-                                                              csum);
+  k_zncc_reduce<<<dim3((kNWin + 127) / 128, nf), 128, 0, st>>>(num, nf, g, td.tn2, isf, sh, sw,
+                                                               csum);
   return cudaGetLastError();
 }
 

@@ -139,17 +139,18 @@ cudaError_t launch_peak_narrow(const unsigned long long* csum, int nf, int R, in
 cudaError_t launch_count_add(const int* n, long long* total, cudaStream_t st);
 
 // BF16 tensor-core correlation (corr_bf16.cu)
-size_t bf16_bt_bytes(PatchGrid g);
+size_t bf16_astore_bytes(PatchGrid g);              // per-patch Toeplitz template stores
 int bf16_row_pitch(int W);
+size_t bf16_fc_elems(int cap_frames, int H, int W);  // frame-offset image buffer
 size_t bf16_tensor_map_bytes();
 int bf16_tensor_map(void* map_out, __nv_bfloat16* fc, int cap_frames, int H, int W);
 cudaError_t bf16_template_prep(const float* T, int H, int W, PatchGrid g, int R,
-                               const TemplateDev& td, float* tround, __nv_bfloat16* bt,
+                               const TemplateDev& td, float* tround, __nv_bfloat16* as,
                                float* bgc, cudaStream_t st);
-cudaError_t bf16_make_fc(const uint16_t* frames, int nf, int H, int W, const float* tround,
-                         __nv_bfloat16* fc, cudaStream_t st);
+cudaError_t bf16_make_fc(const uint16_t* frames, int nf, int cap_frames, int H, int W,
+                         const float* tround, __nv_bfloat16* fc, cudaStream_t st);
 cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
-                             const __nv_bfloat16* bt, const float* bgc, const TemplateDev& td,
+                             const __nv_bfloat16* as, const float* bgc, const TemplateDev& td,
                              const float* isf, float* num, unsigned long long* csum, int* err,
                              cudaStream_t st);
 

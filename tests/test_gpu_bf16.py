@@ -50,11 +50,14 @@ def test_bf16_against_oracle_paper_scale(vimg):
     compare_images(corr, r["corrected"], "corrected", tol=1e-3)
 
 
-@pytest.mark.parametrize("H,W,n", [(300, 250, 37), (128, 128, 16)])
-def test_bf16_against_fp32_ragged(vimg, H, W, n):
+@pytest.mark.parametrize("H,W,n,chunk", [(300, 250, 37, 24), (128, 128, 16, 24),
+                                          (160, 203, 230, 200)])
+def test_bf16_against_fp32_ragged(vimg, H, W, n, chunk):
+    """Frame groups of 80 (N = 80) with ragged tails (N = 48, 32, 16), widths
+    that are not multiples of 8, and several internal batches."""
     cfg = synth.scaled_config(H, W, n, seed=H + W)
     frames, _, T = synth.make_video(cfg, n)
-    s16, i16, surf16, _ = run(vimg, frames, T, vimg.CORR_BF16, max_chunk=24)
+    s16, i16, surf16, _ = run(vimg, frames, T, vimg.CORR_BF16, max_chunk=chunk)
     s32, i32, surf32, _ = run(vimg, frames, T, 0)
     assert np.abs(surf16 - surf32).max() < 2e-3
     assert np.abs(s16 - s32).max() <= 0.05
