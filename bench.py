@@ -224,7 +224,7 @@ def run_vimg(args):
     frames, planted, T = synth.make_video(cfg, n, device=dev)
     stream = torch.cuda.current_stream(dev)
     bf16 = args.corr == "bf16"
-    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk,
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.bf16_chunk if bf16 else args.chunk,
                     flags=vimg.CORR_BF16 if bf16 else 0)
     h.set_template(T)
     shifts = torch.empty((n, 2), device=dev)
@@ -416,7 +416,7 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     out = {}
     ref = ref_shifts.clone()
     # BF16 tensor-core correlation (tcgen05), FP32 accumulation
-    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk, flags=vimg.CORR_BF16)
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.bf16_chunk, flags=vimg.CORR_BF16)
     h.set_template(T)
     sh = torch.empty_like(ref)
     ms, prof = time_variant(h, frames, (sh, corrected, summary), args.steps, args.warmup, stream)
@@ -592,6 +592,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--bf16-chunk", type=int, default=250,
+                    help="frames per internal batch of the tensor-core path (two 128-frame groups)")
     ap.add_argument("--corr", choices=["f32", "bf16"], default="f32",
                     help="correlation path of the main line (f32 = the full-window FP32 method)")
     ap.add_argument("--batch-scale", type=float, default=1.0)
