@@ -459,24 +459,37 @@ __global__ void k_round_template(const float* __restrict__ T, int n, float* __re
 }
 
 // Fc = F - round(T) as BF16 in the layout [row][8-column block][frame][8] with
-// fcap frame slots (columns past W are zero).  Thread = (frame, row, block), frame
-// fastest, so the 16-byte stores of a warp are contiguous.
+// fcap frame slots (columns past W are zero).  A warp takes one frame row, two
+// column blocks and 16 frames (lane = block * 16 + frame): each frame's two blocks
+// are one 32-byte read, and each block's 16 frames one 256-byte write.
 __global__ void k_fc(const uint16_t* __restrict__ frames, int nf, int H, int W, int ncb, int fcap,
                      const float* __restrict__ tround, __nv_bfloat16* __restrict__ fc) {
-  const size_t total = (size_t)nf * H * ncb;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int f = (int)(i % nf);
-    const size_t r = i / nf;
-    const int cb = (int)(r % ncb), y = (int)(r / ncb);
-    const uint16_t* src = frames + ((size_t)f * H + y) * W;
-    const float* tr = tround + (size_t)y * W;
+  const int lane = threadIdx.x & 31, cbl = lane >> 4, fl = lane & 15;
+  const int ncb2 = (ncb + 1) / 2, nf16 = (nf + 15) / 16;
+  const long long items = (long long)H * ncb2 * nf16;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
+       it += wstride) {
+    const int f16 = (int)(it % nf16);
+    const long long r = it / nf16;
+    const int cb2 = (int)(r % ncb2), y = (int)(r / ncb2);
+    const int f = f16 * 16 + fl, cb = 2 * cb2 + cbl;
+    if (f >= nf || cb >= ncb) continue;
+    const uint16_t* src = frames + ((size_t)f * H + y) * W + 8 * cb;
+    const float* tr = tround + (size_t)y * W + 8 * cb;
+    uint16_t px[8];
+    if (8 * cb + 8 <= W && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(src));
+      px[0] = q.x & 0xFFFF, px[1] = q.x >> 16, px[2] = q.y & 0xFFFF, px[3] = q.y >> 16;
+      px[4] = q.z & 0xFFFF, px[5] = q.z >> 16, px[6] = q.w & 0xFFFF, px[7] = q.w >> 16;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) px[j] = 8 * cb + j < W ? __ldg(src + j) : 0;
+    }
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int x = 8 * cb + j;
-      v[j] = __float2bfloat16_rn(x < W ? (float)__ldg(src + x) - __ldg(tr + x) : 0.f);
-    }
+    for (int j = 0; j < 8; ++j)
+      v[j] = __float2bfloat16_rn(8 * cb + j < W ? (float)px[j] - __ldg(tr + j) : 0.f);
     *reinterpret_cast<uint4*>(fc + (((size_t)y * ncb + cb) * fcap + f) * 8) =
         *reinterpret_cast<const uint4*>(v);
   }
@@ -524,8 +537,8 @@ cudaError_t bf16_make_fc(const uint16_t* frames, int nf, int cap_frames, int H, 
                          const float* tround, __nv_bfloat16* fc, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   const int ncb = bf16_row_pitch(W) / 8;
-  const size_t total = (size_t)nf * H * ncb;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 8192);
+  const size_t warps = (size_t)H * ((ncb + 1) / 2) * ((nf + 15) / 16);
+  const int blocks = (int)std::min<size_t>((warps + 7) / 8, 8192);
   k_fc<<<blocks, 256, 0, st>>>(frames, nf, H, W, ncb, fc_slots(cap_frames), tround, fc);
   return cudaGetLastError();
 }
