@@ -258,7 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           abort_flag = 1;
           break;
         }
-        const uint32_t a0 = su32(sA + buf * kABytes);
+        // Descriptors change only in their start-address field (bits 0-13, in
+        // 16-byte units): build the constant parts once, add offsets per MMA.
+        const uint64_t a_desc0 = desc(su32(sA + buf * kABytes), kASlice, kAXl);
+        const uint64_t b_desc0 = desc(su32(sB), kNF * 16, 128);
         for (int b = 0; b < kPasses && !abort_flag; ++b) {
           const int pass = u * kPasses + b;
           for (int y = 0; y < kRows; ++y, ++it) {
@@ -269,9 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t b0 = su32(sB + s * kBStage);
-            for (int a = 0; a < kDyBlk; ++a) {
-              if (y < 8 * a || y > last_row(a)) continue;
+            const uint64_t bd0 = b_desc0 + (uint64_t)(s * (kBStage >> 4));
+            // dy blocks fed by row y: a with 8a <= y <= last_row(a)
+            const int a_lo = y < 27 ? 0 : (y - 27 + 7) >> 3, a_hi = min(kDyBlk - 1, y >> 3);
+            for (int a = a_lo; a <= a_hi; ++a) {
               const int slot = (a + pass) & (kSlots - 1);
               if (y == 8 * a) {
                 const int k = slot_use[slot]++;
@@ -284,12 +288,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                   asm volatile("tcgen05.fence::after_thread_sync;");
                 }
               }
-              const uint32_t q0 = (uint32_t)(27 - (y - 8 * a));
+              const uint64_t ad0 = a_desc0 + (uint64_t)(27 - (y - 8 * a));  // q0 rows of 16 B
               const uint32_t d = tmem + (uint32_t)(slot * kNF);
 #pragma unroll
               for (int qk = 0; qk < kKq; ++qk) {
-                const uint64_t ad = desc(a0 + (uint32_t)(2 * qk) * kASlice + q0 * 16, kASlice, kAXl);
-                const uint64_t bd = desc(b0 + (uint32_t)(2 * qk) * (kNF * 16), kNF * 16, 128);
+                const uint64_t ad = ad0 + (uint64_t)(qk * (2 * kASlice >> 4));
+                const uint64_t bd = bd0 + (uint64_t)(qk * (2 * kNF * 16 >> 4));
                 const uint32_t acc = (y == 8 * a && qk == 0) ? 0u : 1u;
                 asm volatile(
                     "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
