@@ -224,9 +224,15 @@ def run_vimg(args):
     frames, planted, T = synth.make_video(cfg, n, device=dev)
     stream = torch.cuda.current_stream(dev)
     bf16 = args.corr == "bf16"
+    learned = args.corr == "proposal"
+    flags = vimg.CORR_BF16 if bf16 else (vimg.PROPOSAL_CNN if learned else 0)
     h = vimg.Handle(H, W, stream=stream, max_chunk=args.bf16_chunk if bf16 else args.chunk,
-                    flags=vimg.CORR_BF16 if bf16 else 0)
+                    flags=flags)
     h.set_template(T)
+    if learned:
+        from paper_2403_16438_gb300 import proposal
+        params, _ = proposal.train(total_frames=args.train_frames)
+        h.load_proposal(params)
     shifts = torch.empty((n, 2), device=dev)
     corrected = torch.empty((n, H, W), device=dev)
     k_max = n // L
@@ -289,6 +295,16 @@ def run_vimg(args):
             "peak_kind": pk_kind + " (sustained cuBLAS bf16)",
             "note": "achieved counts the useful 2 x 484 x 441 x 1089 FLOP per frame",
         }
+    elif learned:
+        t_ms, t_launches = prof["temporal"]
+        gbs = temporal_bytes_per_frame() * n * args.steps / (t_ms / 1000.0) / 1e9 if t_ms > 0 else None
+        roofline = {
+            "kernel": "k_temporal (the largest stage of this path)", "bound": "hbm",
+            "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / pk["hbm_gbs"] if gbs else None, "traffic": None,
+            "per_launch_frames": round(n * args.steps / max(1, t_launches), 3),
+            "avg_launch_ms": t_ms / max(1, t_launches), "peak_kind": pk_kind,
+        }
     else:
         tr = kernel_traffic("k_corr_f32", "motion.cu")
         roofline = {
@@ -312,7 +328,9 @@ def run_vimg(args):
         "data": "synthetic",
         "config": {
             "workload": "paper-scale synthetic video: 512x512 uint16, 10,000 frames per step, "
-                        + ("full-window BF16 tensor-core ZNCC" if bf16 else "full-window FP32 ZNCC")
+                        + ("full-window BF16 tensor-core ZNCC" if bf16 else
+                           "learned proposal + +-2 px FP32 ZNCC window, full-window fallback"
+                           if learned else "full-window FP32 ZNCC")
                         + " +-16 px (484 patches x 1089 shifts), bilinear "
                         "resampling, L=50 mean and max-median summaries",
             "frames_per_step": n, "H": H, "W": W, "search_radius": R, "segment_len": L,
@@ -594,8 +612,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--bf16-chunk", type=int, default=250,
                     help="frames per internal batch of the tensor-core path (two 128-frame groups)")
-    ap.add_argument("--corr", choices=["f32", "bf16"], default="f32",
+    ap.add_argument("--corr", choices=["f32", "bf16", "proposal"], default="f32",
                     help="correlation path of the main line (f32 = the full-window FP32 method)")
+    ap.add_argument("--train-frames", type=int, default=200000,
+                    help="training pool of the learned proposal (--corr proposal)")
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-steps", type=int, default=2)
     args = ap.parse_args()

@@ -92,23 +92,30 @@ __global__ void k_cnn_input(const uint16_t* __restrict__ frames, int H, int W,
   for (int i = threadIdx.x; i < kCrop * kCrop; i += kThreads) o[i] = (val(i) - mean) * inv;
 }
 
-// ---- conv 3x3 forward + ReLU: thread per output pixel, all 32 output channels -----
-template <int CIN, int S>
+// ---- conv 3x3 forward + ReLU: thread per (output pixel, group of kC / COG channels)
+// The deep layers have few pixels, so they split the output channels over COG
+// threads to keep enough warps in flight.  Pairs of channels accumulate with the
+// packed FP32 FMA (two independent round-to-nearest FMAs, the same results as
+// scalar fmaf).
+template <int CIN, int S, int COG>
 __global__ void __launch_bounds__(kThreads)
     k_conv_fwd(const float* __restrict__ in, const __nv_bfloat16* __restrict__ w,
                const float* __restrict__ bias, float* __restrict__ out, int n, int HI, int HO) {
+  constexpr int NC = kC / COG;  // output channels per thread (multiple of 4)
   __shared__ __align__(16) float ws[CIN * 9][kC];
   for (int i = threadIdx.x; i < CIN * 9 * kC; i += kThreads) {
     const int co = i / (CIN * 9), r = i - co * (CIN * 9);
     ws[r][co] = __bfloat162float(w[i]);
   }
   __syncthreads();
-  const int pix = blockIdx.x * kThreads + threadIdx.x;
-  if (pix >= n * HO * HO) return;
+  const int npix = n * HO * HO;
+  const int t = blockIdx.x * kThreads + threadIdx.x;
+  if (t >= npix * COG) return;
+  const int g = t / npix, pix = t - g * npix;
   const int b = pix / (HO * HO), rem = pix - b * HO * HO, oy = rem / HO, ox = rem - oy * HO;
-  float acc[kC];
+  float2 acc[NC / 2];
 #pragma unroll
-  for (int c = 0; c < kC; ++c) acc[c] = bias[c];
+  for (int c = 0; c < NC / 2; ++c) acc[c] = make_float2(bias[g * NC + 2 * c], bias[g * NC + 2 * c + 1]);
   for (int ci = 0; ci < CIN; ++ci) {
     const float* ip = in + ((size_t)b * CIN + ci) * HI * HI;
 #pragma unroll
@@ -120,21 +127,23 @@ __global__ void __launch_bounds__(kThreads)
         const int ix = ox * S + kx - 1;
         if (ix < 0 || ix >= HI) continue;
         const float v = __ldg(ip + iy * HI + ix);
-        const float4* wr = reinterpret_cast<const float4*>(ws[ci * 9 + ky * 3 + kx]);
+        const float2 vv = make_float2(v, v);
+        const float4* wr = reinterpret_cast<const float4*>(&ws[ci * 9 + ky * 3 + kx][g * NC]);
 #pragma unroll
-        for (int q = 0; q < kC / 4; ++q) {
+        for (int q = 0; q < NC / 4; ++q) {
           const float4 wv = wr[q];
-          acc[4 * q] = fmaf(wv.x, v, acc[4 * q]);
-          acc[4 * q + 1] = fmaf(wv.y, v, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(wv.z, v, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(wv.w, v, acc[4 * q + 3]);
+          acc[2 * q] = __ffma2_rn(make_float2(wv.x, wv.y), vv, acc[2 * q]);
+          acc[2 * q + 1] = __ffma2_rn(make_float2(wv.z, wv.w), vv, acc[2 * q + 1]);
         }
       }
     }
   }
-  float* op = out + (size_t)b * kC * HO * HO + oy * HO + ox;
+  float* op = out + ((size_t)b * kC + g * NC) * HO * HO + oy * HO + ox;
 #pragma unroll
-  for (int c = 0; c < kC; ++c) op[(size_t)c * HO * HO] = fmaxf(acc[c], 0.f);
+  for (int c = 0; c < NC / 2; ++c) {
+    op[(size_t)(2 * c) * HO * HO] = fmaxf(acc[c].x, 0.f);
+    op[(size_t)(2 * c + 1) * HO * HO] = fmaxf(acc[c].y, 0.f);
+  }
 }
 
 // ---- global average pool + linear ------------------------------------------------
@@ -346,10 +355,11 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
 
 inline int blocks(size_t count) { return (int)((count + kThreads - 1) / kThreads); }
 
-template <int CIN, int S>
+template <int CIN, int S, int COG>
 cudaError_t conv_fwd(const float* in, const __nv_bfloat16* w, const float* b, float* out, int n,
                      int HI, int HO, cudaStream_t st) {
-  k_conv_fwd<CIN, S><<<blocks((size_t)n * HO * HO), kThreads, 0, st>>>(in, w, b, out, n, HI, HO);
+  k_conv_fwd<CIN, S, COG><<<blocks((size_t)n * HO * HO * COG), kThreads, 0, st>>>(in, w, b, out, n,
+                                                                                 HI, HO);
   return cudaGetLastError();
 }
 
@@ -370,9 +380,13 @@ cudaError_t cnn_forward(const float* params, const __nv_bfloat16* wb, float* act
     const __nv_bfloat16* w = wb + w_off(l);
     const float* b = params + w_off(l) + w_count(l);
     const int HI = kSide[l], HO = kSide[l + 1];
-    if (l == 0) e = conv_fwd<2, 2>(in, w, b, o, n, HI, HO, st);
-    else if (kStride[l] == 2) e = conv_fwd<32, 2>(in, w, b, o, n, HI, HO, st);
-    else e = conv_fwd<32, 1>(in, w, b, o, n, HI, HO, st);
+    // output channel groups per layer: more threads where there are few pixels
+    if (l == 0) e = conv_fwd<2, 2, 1>(in, w, b, o, n, HI, HO, st);
+    else if (l == 1) e = conv_fwd<32, 2, 1>(in, w, b, o, n, HI, HO, st);
+    else if (l == 2) e = conv_fwd<32, 2, 2>(in, w, b, o, n, HI, HO, st);
+    else if (l == 3) e = conv_fwd<32, 2, 4>(in, w, b, o, n, HI, HO, st);
+    else if (l == 4) e = conv_fwd<32, 2, 8>(in, w, b, o, n, HI, HO, st);
+    else e = conv_fwd<32, 1, 8>(in, w, b, o, n, HI, HO, st);
   }
   if (e != cudaSuccess) return e;
   float* gap = acts + act_off(kLayers + 1, n);
