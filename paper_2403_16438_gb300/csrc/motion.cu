@@ -619,7 +619,7 @@ __device__ __forceinline__ void narrow_center(const float* prop, int f, int R, i
   cx = max(-lim, min(lim, cx));
 }
 
-__global__ void __launch_bounds__(kNarrowGroup * 8, 2)
+__global__ void __launch_bounds__(kNarrowGroup * 8, 4)
     k_corr_narrow(const uint16_t* __restrict__ frames, int H, int W, PatchGrid g, int R,
                   const float* __restrict__ tc, const float* __restrict__ tn2,
                   const float* __restrict__ isf, const float* __restrict__ prop,
@@ -638,10 +638,29 @@ __global__ void __launch_bounds__(kNarrowGroup * 8, 2)
   const int nrs = kNarrowStride;
   const int ty = g.y0 + py * kPatch, tx0 = g.x0 + px0 * kPatch;
   for (int i = threadIdx.x; i < kNarrow * kNarrow; i += blockDim.x) cs[i] = 0ull;
-  // stage the union of the group's narrow regions (coalesced rows)
+  // stage the union of the group's narrow regions: batches of independent loads
+  // (coalesced along rows), then the shared stores
   const uint16_t* F = frames + (size_t)f * H * W + (size_t)(ty + wy0) * W + tx0 + wx0;
-  for (int r = 0; r < rows; ++r)
-    for (int x = threadIdx.x; x < cols; x += blockDim.x) nreg[r * nrs + x] = (float)__ldg(F + (size_t)r * W + x);
+  {
+    constexpr int kBatch = 12;
+    const int total = rows * cols;
+    const unsigned m = 0xffffffffu / (unsigned)cols + 1u;  // i / cols exact for i < 2^32 / cols
+    for (int base = threadIdx.x; base < total; base += kBatch * blockDim.x) {
+      unsigned short v[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const int i = base + q * blockDim.x;
+        const int r = (int)fast_div((unsigned)i, m), x = i - r * cols;
+        v[q] = i < total ? __ldg(F + (size_t)r * W + x) : (unsigned short)0;
+      }
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const int i = base + q * blockDim.x;
+        const int r = (int)fast_div((unsigned)i, m), x = i - r * cols;
+        if (i < total) nreg[r * nrs + x] = (float)v[q];
+      }
+    }
+  }
   __syncthreads();
   if (u < G && dy < kNarrow) {
     const int p = py * g.nx + px0 + u;
