@@ -434,6 +434,8 @@ static TemporalArgs temporal_args(const vimg_handle* h, const uint16_t* frames, 
   a.seg_base = seen - c;
   a.n_seg = (c + n + L - 1) / L;
   a.out_hp = (h->p.flags & VIMG_OUT_HIGHPASS) ? 1 : 0;
+  a.pairs = (h->W % 2 == 0) && ((reinterpret_cast<uintptr_t>(frames) & 3) == 0) &&
+            ((reinterpret_cast<uintptr_t>(a.src.carry) & 3) == 0);
   a.corrected = corrected;
   a.summary = summary;
   return a;

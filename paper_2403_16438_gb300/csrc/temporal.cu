@@ -207,13 +207,14 @@ struct TileRange {
 };
 
 __device__ __forceinline__ StageGeom stage_geom(Split sy, Split sx, const TileRange& tr, int H,
-                                                int W) {
+                                                int W, bool pairs) {
   StageGeom g;
   g.sy = sy;
   g.sx = sx;
   g.r0 = max(0, min(H - 1, tr.ylo + sy.i));
   g.nr = max(0, min(H - 1, tr.yhi + sy.i + 1)) - g.r0 + 1;
   g.c0 = max(0, min(W - 1, tr.xlo + sx.i));
+  if (pairs) g.c0 &= ~1;  // 2-pixel words start on even columns (one extra column, <= 58)
   g.nc = max(0, min(W - 1, tr.xhi + sx.i + 1)) - g.c0 + 1;
   g.plain = tr.inner && tr.ylo + sy.i >= 0 && tr.yhi + sy.i + 1 <= H - 1 &&
             tr.xlo + sx.i >= 0 && tr.xhi + sx.i + 1 <= W - 1;
@@ -243,6 +244,7 @@ __device__ __forceinline__ long long hp_q(float v) { return __float2ll_rn(v * kH
 constexpr int kFst = 58;                 // staged frame row stride (uint16), >= 57 columns
 constexpr int kFstRows = 57;
 constexpr int kPfRows = (kFstRows + 7) / 8;  // prefetch: 64 columns x 8 rows per pass
+constexpr int kPf2Rows = (kFstRows + 15) / 16;  // pairs: 32 words (64 columns) x 16 rows per pass
 
 // One CTA per (job, segment slot, tile); the job comes from the prefix counts.
 __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_constant__ TemporalBatch b) {
@@ -293,11 +295,14 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
     const long long v = t - src.t_first;
     return v < src.n_carry ? src.carry + (size_t)v * HW : src.batch + (size_t)(v - src.n_carry) * HW;
   };
+  const bool pairs = a.pairs != 0;
   auto geom_of = [&](int fi) {
-    return stage_geom(split_shift(shs[2 * fi]), split_shift(shs[2 * fi + 1]), tr, H, W);
+    return stage_geom(split_shift(shs[2 * fi]), split_shift(shs[2 * fi + 1]), tr, H, W, pairs);
   };
-  // prefetch pattern: column pc of rows pr, pr + 8, ... (no division)
+  // prefetch pattern: column pc of rows pr, pr + 8, ... (no division); with
+  // pairs, 2-pixel word pc2 of rows pr2, pr2 + 16, ...
   const int pc = tid & 63, pr = tid >> 6;
+  const int pc2 = tid & 31, pr2 = tid >> 5;
 
   float sum_a = 0.f, sum_b = 0.f, mx_a = -FLT_MAX, mx_b = -FLT_MAX;
   long long hs_a = 0, hs_b = 0;
@@ -309,11 +314,21 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
   StageGeom gcur = geom_of(0);
   {
     const uint16_t* F = frame_ptr(s0);
+    if (pairs) {
 #pragma unroll
-    for (int k = 0; k < kPfRows; ++k) {
-      const int r = pr + 8 * k;
-      if (r < gcur.nr && pc < gcur.nc)
-        fst[r * kFst + pc] = __ldg(F + (size_t)(gcur.r0 + r) * W + gcur.c0 + pc);
+      for (int k = 0; k < kPf2Rows; ++k) {
+        const int r = pr2 + 16 * k;
+        if (r < gcur.nr && 2 * pc2 < gcur.nc)
+          reinterpret_cast<unsigned*>(fst + r * kFst)[pc2] =
+              __ldg(reinterpret_cast<const unsigned*>(F + (size_t)(gcur.r0 + r) * W + gcur.c0) + pc2);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kPfRows; ++k) {
+        const int r = pr + 8 * k;
+        if (r < gcur.nr && pc < gcur.nc)
+          fst[r * kFst + pc] = __ldg(F + (size_t)(gcur.r0 + r) * W + gcur.c0 + pc);
+      }
     }
     if (tid < kExt) rtab[tid] = axis_entry(ty0 - kGaussMaxRadius + tid, H, gcur.sy, gcur.r0);
     else if (tid < 2 * kExt)
@@ -327,15 +342,25 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
     const bool more = fi + 1 < nfr;
     StageGeom gnext = gcur;
     unsigned short pf[kPfRows];
+    unsigned pf2[kPf2Rows];
     if (more) {
       gnext = geom_of(fi + 1);
       const uint16_t* F = frame_ptr(t + 1);
+      if (pairs) {
+        const unsigned* F2 = reinterpret_cast<const unsigned*>(F + (size_t)gnext.r0 * W + gnext.c0);
 #pragma unroll
-      for (int k = 0; k < kPfRows; ++k) {
-        const int r = pr + 8 * k;
-        pf[k] = (r < gnext.nr && pc < gnext.nc)
-                    ? __ldg(F + (size_t)(gnext.r0 + r) * W + gnext.c0 + pc)
-                    : (unsigned short)0;
+        for (int k = 0; k < kPf2Rows; ++k) {
+          const int r = pr2 + 16 * k;
+          pf2[k] = (r < gnext.nr && 2 * pc2 < gnext.nc) ? __ldg(F2 + (size_t)r * (W >> 1) + pc2) : 0u;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kPfRows; ++k) {
+          const int r = pr + 8 * k;
+          pf[k] = (r < gnext.nr && pc < gnext.nc)
+                      ? __ldg(F + (size_t)(gnext.r0 + r) * W + gnext.c0 + pc)
+                      : (unsigned short)0;
+        }
       }
     }
     // 1. resample the tile + halo from the staged frame
@@ -429,10 +454,18 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
     }
     // 4. stage the next frame (the current one was consumed before the barrier)
     if (more) {
+      if (pairs) {
 #pragma unroll
-      for (int k = 0; k < kPfRows; ++k) {
-        const int r = pr + 8 * k;
-        if (r < gnext.nr && pc < gnext.nc) fst[r * kFst + pc] = pf[k];
+        for (int k = 0; k < kPf2Rows; ++k) {
+          const int r = pr2 + 16 * k;
+          if (r < gnext.nr && 2 * pc2 < gnext.nc) reinterpret_cast<unsigned*>(fst + r * kFst)[pc2] = pf2[k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kPfRows; ++k) {
+          const int r = pr + 8 * k;
+          if (r < gnext.nr && pc < gnext.nc) fst[r * kFst + pc] = pf[k];
+        }
       }
       if (tid < kExt) rtab[tid] = axis_entry(ty0 - kGaussMaxRadius + tid, H, gnext.sy, gnext.r0);
       else if (tid < 2 * kExt)
@@ -445,12 +478,17 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
     float col[kTaps + 1];
 #pragma unroll
     for (int k = 0; k < kTaps + 1; ++k) col[k] = hbuf[(ly0 + k) * kTile + lx];
-    float b_a = 0.f, b_b = 0.f;
+    // even and odd taps in separate chains (four independent FMA chains per thread)
+    float b_a = 0.f, b_b = 0.f, c_a = 0.f, c_b = 0.f;
 #pragma unroll
-    for (int m = 0; m < kTaps; ++m) {
+    for (int m = 0; m + 1 < kTaps; m += 2) {
       b_a = fmaf(w[m], col[m], b_a);
       b_b = fmaf(w[m], col[m + 1], b_b);
+      c_a = fmaf(w[m + 1], col[m + 1], c_a);
+      c_b = fmaf(w[m + 1], col[m + 2], c_b);
     }
+    b_a = fmaf(w[kTaps - 1], col[kTaps - 1], b_a) + c_a;
+    b_b = fmaf(w[kTaps - 1], col[kTaps], b_b) + c_b;
     sum_a += v_a;
     sum_b += v_b;
     mx_a = fmaxf(mx_a, b_a);

@@ -56,6 +56,7 @@ struct TemporalArgs {
   long long seg_base;                 // absolute start of segment slot 0
   int n_seg;                          // segment slots in this launch
   int out_hp;                         // corrected output holds the high-pass
+  int pairs;                          // stage frames as 2-pixel words (W even, 4-byte aligned)
   float* corrected;                   // [n_batch][H][W] or null
   float* summary;                     // [k][2][H][W] or null (slot j -> index j)
 };
