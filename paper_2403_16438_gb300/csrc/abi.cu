@@ -359,8 +359,8 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
     CK(cnn_forward(h->cnn_p, h->cnn_b, h->cnn_acts, nf, h->prop, h->st), "proposal forward");
     prof_end(h, ps);
     ps = prof_begin(h, 0);
-    CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st),
-       "window statistics launch");
+    CK(launch_stats_narrow(frames, nf, h->H, h->W, h->g, R, h->prop, h->inv, h->st),
+       "narrow window statistics launch");
     prof_end(h, ps);
     CK(cudaMemsetAsync(h->csum_n, 0, sizeof(unsigned long long) * kNarrowWin * kNarrowWin * nf,
                        h->st),
@@ -375,6 +375,10 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
     CK(launch_peak_narrow(h->csum_n, nf, R, h->np, h->prop, h->p.fallback_zncc, shifts, peak_info,
                           h->fb_list, h->fb_n, h->st),
        "narrow peak launch");
+    prof_end(h, ps);
+    ps = prof_begin(h, 0);
+    CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st, h->fb_list, h->fb_n),
+       "fallback window statistics launch");
     prof_end(h, ps);
     ps = prof_begin(h, 1);
     CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st, h->fb_list,

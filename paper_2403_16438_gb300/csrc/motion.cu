@@ -105,15 +105,26 @@ __host__ __device__ inline int stats_tiles(PatchGrid g, int R) {
 // One CTA per (job, frame, block of positions); the job comes from the prefix
 // counts of the table.
 __global__ void __launch_bounds__(kBoxThreads)
-    k_boxstats(const __grid_constant__ MotionBatch b) {
-  const int jb = job_of(b.stats_begin, b.n, blockIdx.x);
+    k_boxstats(const __grid_constant__ MotionBatch b, const int* __restrict__ list,
+               const int* __restrict__ list_n) {
+  // Without a list every CTA takes one work item.  With a frame list (fallback
+  // frames of the learned proposal; one job) a small grid strides over the
+  // listed frames' items, whose count is read on the device.
+  int n_items = b.stats_begin[b.n];
+  if (list) {
+    const MotionJob& J0 = b.j[0];
+    n_items = min(J0.nf, *list_n) * stats_tiles(J0.g, J0.R);
+  }
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  const int jb = list ? 0 : job_of(b.stats_begin, b.n, item);
   const MotionJob& J = b.j[jb];
   const int H = J.H, W = J.W;
   int oy, ox, sh, sw;
   stats_map_dims(J.g, J.R, &oy, &ox, &sh, &sw);
   const int ntx = (sw + kBoxCols - 1) / kBoxCols, per = ntx * ((sh + kBoxRows - 1) / kBoxRows);
-  const int local = blockIdx.x - b.stats_begin[jb];
-  const int f = local / per, rem = local - f * per;
+  const int local = item - (list ? 0 : b.stats_begin[jb]);
+  const int fi = local / per, rem = local - fi * per;
+  const int f = list ? list[fi] : fi;
   const int by = (rem / ntx) * kBoxRows, bx = (rem % ntx) * kBoxCols;
   const uint16_t* __restrict__ frames = J.frames;
   float* __restrict__ isf = J.isf;
@@ -182,6 +193,8 @@ __global__ void __launch_bounds__(kBoxThreads)
       s2 += rs2[(r + kPatch) * kBoxRsStride + c] - rs2[r * kBoxRsStride + c];
     }
   }
+  __syncthreads();  // the shared buffers are reused by the next item
+  }
 }
 
 size_t stats_map_floats(PatchGrid g, int R) {
@@ -216,21 +229,24 @@ bool motion_batch_finalize(MotionBatch& b) {
   return true;
 }
 
-cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st) {
-  const int blocks = b.stats_begin[b.n];
+cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st, const int* list,
+                               const int* list_n) {
+  int blocks = b.stats_begin[b.n];
   if (blocks <= 0) return cudaSuccess;
-  k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b);
+  if (list) blocks = std::min(blocks, 152 * 4);  // one wave; strides over the listed frames
+  k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b, list, list_n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
-                         const TemplateDev& td, float* isf, cudaStream_t st) {
+                         const TemplateDev& td, float* isf, cudaStream_t st, const int* list,
+                         const int* list_n) {
   if (nf <= 0) return cudaSuccess;
   MotionBatch b{};
   b.n = 1;
   b.j[0] = one_job(frames, nf, H, W, g, R, td, isf, nullptr);
   if (!motion_batch_finalize(b)) return cudaErrorInvalidValue;
-  return launch_stats_multi(b, st);
+  return launch_stats_multi(b, st, list, list_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -702,6 +718,76 @@ __global__ void __launch_bounds__(kNarrowGroup * 8, 4)
   __syncthreads();
   unsigned long long* out = csum + (size_t)f * kNarrow * kNarrow;
   for (int i = threadIdx.x; i < kNarrow * kNarrow; i += blockDim.x) atomicAdd(out + i, cs[i]);
+}
+
+// Window statistics of the narrow window only: for each patch the 7x7 window
+// positions around the frame's proposal (the entries of the isf map that
+// k_corr_narrow reads), with the same exact integers and the same rounding as
+// k_boxstats.  One warp per (frame, patch): lane c reads column c of the 27x27
+// region row by row (coalesced) and slides vertically (column sums at the 7 row
+// offsets); the 49 windows then sum 21 column sums each.  Frames that fall back
+// to the full window get the full map afterwards.
+constexpr int kNsPatches = 2;  // patches (warps) per CTA
+__global__ void __launch_bounds__(32 * kNsPatches)
+    k_boxstats_narrow(const uint16_t* __restrict__ frames, int nf, int H, int W, PatchGrid g,
+                      int R, const float* __restrict__ prop, float* __restrict__ isf) {
+  constexpr int kRegion = kNarrow + kPatch - 1;  // 27
+  __shared__ int cs1[kNsPatches][kNarrow][kRegion];
+  __shared__ long long cs2[kNsPatches][kNarrow][kRegion];
+  const int np = g.ny * g.nx, f = blockIdx.y, wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kNsPatches + wl;
+  if (p >= np || f >= nf) return;
+  int cy, cx;
+  narrow_center(prop, f, R, cy, cx);
+  const int wy0 = cy - kNarrow / 2, wx0 = cx - kNarrow / 2;
+  const int ty = g.y0 + (p / g.nx) * kPatch, tx = g.x0 + (p % g.nx) * kPatch;
+  if (lane < kRegion) {
+    const uint16_t* col = frames + (size_t)f * H * W + (size_t)(ty + wy0) * W + tx + wx0 + lane;
+    int v[kRegion];
+#pragma unroll
+    for (int r = 0; r < kRegion; ++r) v[r] = __ldg(col + (size_t)r * W);
+    int s1 = 0;
+    long long s2 = 0;
+#pragma unroll
+    for (int r = 0; r < kPatch; ++r) {
+      s1 += v[r];
+      s2 += (long long)v[r] * v[r];
+    }
+#pragma unroll
+    for (int j = 0; j < kNarrow; ++j) {
+      cs1[wl][j][lane] = s1;
+      cs2[wl][j][lane] = s2;
+      if (j + 1 < kNarrow) {
+        const int a = v[j + kPatch], b = v[j];
+        s1 += a - b;
+        s2 += (long long)a * a - (long long)b * b;
+      }
+    }
+  }
+  __syncwarp();
+  int oy, ox, sh, sw;
+  stats_map_dims(g, R, &oy, &ox, &sh, &sw);
+  float* out = isf + (size_t)f * sh * sw + (size_t)(ty + wy0 - oy) * sw + (tx + wx0 - ox);
+  for (int i = lane; i < kNarrow * kNarrow; i += 32) {
+    const int dy = i / kNarrow, dx = i - dy * kNarrow;
+    long long s1 = 0, s2 = 0;
+#pragma unroll
+    for (int c = 0; c < kPatch; ++c) {
+      s1 += cs1[wl][dy][dx + c];
+      s2 += cs2[wl][dy][dx + c];
+    }
+    const long long sf = (long long)kPatchArea * s2 - s1 * s1;
+    out[(size_t)dy * sw + dx] = sf > 0 ? rsqrtf((float)sf) : 0.f;
+  }
+}
+
+cudaError_t launch_stats_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                                const float* prop, float* isf, cudaStream_t st) {
+  if (nf <= 0) return cudaSuccess;
+  const int np = g.ny * g.nx;
+  k_boxstats_narrow<<<dim3((np + kNsPatches - 1) / kNsPatches, nf), 32 * kNsPatches, 0, st>>>(
+      frames, nf, H, W, g, R, prop, isf);
+  return cudaGetLastError();
 }
 
 // Peak of the narrow window.  Falls back to the full window (frame appended to

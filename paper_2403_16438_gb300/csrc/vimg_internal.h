@@ -106,7 +106,8 @@ __host__ __device__ __forceinline__ int job_of(const int* begin, int n, int item
 bool motion_batch_finalize(MotionBatch& b);
 bool temporal_batch_finalize(TemporalBatch& b);
 // One launch per stage over every job of the table.
-cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st);
+cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st, const int* list = nullptr,
+                               const int* list_n = nullptr);
 cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st,
                                   const int* list = nullptr, const int* list_n = nullptr);
 cudaError_t launch_peak_multi(const MotionBatch& b, cudaStream_t st, const int* list = nullptr,
@@ -120,8 +121,13 @@ cudaError_t temporal_init();
 cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, TemplateDev td,
                                  cudaStream_t st);
 size_t stats_map_floats(PatchGrid g, int R);  // per frame
+// list/list_n (device): only the listed frames (count read on the device).
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
-                         const TemplateDev& td, float* isf, cudaStream_t st);
+                         const TemplateDev& td, float* isf, cudaStream_t st,
+                         const int* list = nullptr, const int* list_n = nullptr);
+// Only the isf entries of the narrow windows around the proposals.
+cudaError_t launch_stats_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
+                                const float* prop, float* isf, cudaStream_t st);
 // list/list_n (device): process only the listed frames (count read on the device).
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
