@@ -27,6 +27,8 @@
 namespace vimg {
 
 constexpr int kTempThreads = 512;
+constexpr int kFst = 58;                 // staged frame row stride (uint16), >= 58 columns
+constexpr int kFstRows = 57;             // staged frame rows (56 + 1 for the bilinear taps)
 constexpr int kExt = kTile + 2 * kGaussMaxRadius;  // 56
 constexpr int kTaps = 2 * kGaussMaxRadius + 1;     // 25
 constexpr float kHpScale = 65536.0f;
@@ -119,28 +121,6 @@ __device__ __forceinline__ int mirror_idx(int i, int n) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// Range [lo, hi] of mirror_idx over the integers a..b (a <= b).
-__device__ __forceinline__ void mirror_range(int a, int b, int n, int& lo, int& hi) {
-  lo = n - 1;
-  hi = 0;
-  if (a <= -1) {  // decreasing piece: -y-1
-    const int e = b < -1 ? b : -1;
-    lo = min(lo, -e - 1);
-    hi = max(hi, -a - 1);
-  }
-  if (b >= 0 && a <= n - 1) {  // identity piece
-    lo = min(lo, a > 0 ? a : 0);
-    hi = max(hi, b < n - 1 ? b : n - 1);
-  }
-  if (b >= n) {  // decreasing piece: 2n-y-1
-    const int s = a > n ? a : n;
-    lo = min(lo, 2 * n - b - 1);
-    hi = max(hi, 2 * n - s - 1);
-  }
-  lo = max(0, min(n - 1, lo));
-  hi = max(0, min(n - 1, hi));
-}
-
 // V(y, x) = F(y + s_y, x + s_x), bilinear, coordinates clamped to the image.
 // s = i + f with 0 <= f < 1 keeps every weight exact.  Global-memory form (used
 // for the few high-pass samples outside the staged tile).
@@ -177,47 +157,28 @@ __device__ __forceinline__ float bilin(const uint16_t* __restrict__ F, int H, in
   return fmaf(wy, bot - top, top);
 }
 
-// One axis of the bilinear sample for tile coordinate i (halo-extended):
-// packed (first source index - base) | (second - first) << 8 | (weight != 0) << 9.
-__device__ __forceinline__ unsigned short axis_entry(int i0, int n, Split s, int base) {
-  const int v = mirror_idx(i0, n) + s.i;
-  int a, d, wf;
-  if (v < 0) {
-    a = 0, d = 0, wf = 0;
-  } else if (v >= n - 1) {
-    a = n - 1, d = 0, wf = 0;
-  } else {
-    a = v, d = 1, wf = s.f != 0.f;
-  }
-  return (unsigned short)((a - base) | (d << 8) | (wf << 9));
-}
-
-// Source rectangle of the staged frame tile: rows/cols whose pixels any
-// halo-extended tile coordinate can touch.  lo/hi are the tile's mirrored
-// coordinate ranges (frame independent); the shift moves them.
+// Source window of the staged frame tile: the 57x57 frame pixels under the
+// halo-extended tile moved by the shift's integer part, (r0, c0) = tile origin
+// - 12 + floor(s).  Pixels outside the image are staged with clamped
+// coordinates (replicated edges), which makes the bilinear formula on the
+// staged window equal to the clamped-coordinate resampling everywhere in the
+// image.  `plain` = the window lies inside the image (no clamping needed).
 struct StageGeom {
   Split sy, sx;
-  int r0, c0, nr, nc;
-  bool plain;  // no mirroring and no clamping: source = tile coordinate + shift
+  int r0, c0;   // window origin in the frame (may be outside the image)
+  int c0e;      // first staged column (c0, or c0 rounded down to even for 2-pixel words)
+  bool plain;
 };
 
-struct TileRange {
-  int ylo, yhi, xlo, xhi;
-  bool inner;  // the halo-extended tile lies inside the image
-};
-
-__device__ __forceinline__ StageGeom stage_geom(Split sy, Split sx, const TileRange& tr, int H,
+__device__ __forceinline__ StageGeom stage_geom(Split sy, Split sx, int ty0, int tx0, int H,
                                                 int W, bool pairs) {
   StageGeom g;
   g.sy = sy;
   g.sx = sx;
-  g.r0 = max(0, min(H - 1, tr.ylo + sy.i));
-  g.nr = max(0, min(H - 1, tr.yhi + sy.i + 1)) - g.r0 + 1;
-  g.c0 = max(0, min(W - 1, tr.xlo + sx.i));
-  if (pairs) g.c0 &= ~1;  // 2-pixel words start on even columns (one extra column, <= 58)
-  g.nc = max(0, min(W - 1, tr.xhi + sx.i + 1)) - g.c0 + 1;
-  g.plain = tr.inner && tr.ylo + sy.i >= 0 && tr.yhi + sy.i + 1 <= H - 1 &&
-            tr.xlo + sx.i >= 0 && tr.xhi + sx.i + 1 <= W - 1;
+  g.r0 = ty0 - kGaussMaxRadius + sy.i;
+  g.c0 = tx0 - kGaussMaxRadius + sx.i;
+  g.plain = g.r0 >= 0 && g.r0 + kFstRows - 1 <= H - 1 && g.c0 >= 0 && g.c0 + kFstRows - 1 <= W - 1;
+  g.c0e = (g.plain && pairs) ? (g.c0 & ~1) : g.c0;
   return g;
 }
 
@@ -241,8 +202,6 @@ __device__ __forceinline__ void frame_at(const FrameSource& s, long long t, cons
 __device__ __forceinline__ long long hp_q(float v) { return __float2ll_rn(v * kHpScale); }
 
 // ---- the fused kernel ------------------------------------------------------------
-constexpr int kFst = 58;                 // staged frame row stride (uint16), >= 57 columns
-constexpr int kFstRows = 57;
 constexpr int kPfRows = (kFstRows + 7) / 8;  // prefetch: 64 columns x 8 rows per pass
 constexpr int kPf2Rows = (kFstRows + 15) / 16;  // pairs: 32 words (64 columns) x 16 rows per pass
 
@@ -256,9 +215,7 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
   float* hbuf = vext + kExt * kExt;            // [56][32] row-smoothed
   float* hist = hbuf + kExt * kTile;           // [L][1024] smoothed history
   float* shs = hist + (size_t)L * kTile * kTile;  // [L][2] shifts of the slot's frames
-  unsigned short* fst = reinterpret_cast<unsigned short*>(shs + 2 * kMaxL);
-  unsigned short* rtab = fst + kFstRows * kFst;  // [56] row entries
-  unsigned short* ctab = rtab + kExt;            // [56] column entries
+  unsigned short* fst = reinterpret_cast<unsigned short*>(shs + 2 * kMaxL);  // [57][58]
   const int ntx = (W + kTile - 1) / kTile, tiles = ntx * ((H + kTile - 1) / kTile);
   const int local = blockIdx.x - b.begin[jb];
   const int slot = local / tiles, tile = local - slot * tiles;
@@ -273,11 +230,10 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
   const int nfr = (int)(s1 - s0);
   const bool complete = s0 + L <= t_end;
 
-  TileRange tr;
-  mirror_range(ty0 - kGaussMaxRadius, ty0 + kTile + kGaussMaxRadius - 1, H, tr.ylo, tr.yhi);
-  mirror_range(tx0 - kGaussMaxRadius, tx0 + kTile + kGaussMaxRadius - 1, W, tr.xlo, tr.xhi);
-  tr.inner = ty0 - kGaussMaxRadius >= 0 && ty0 + kTile + kGaussMaxRadius <= H &&
-             tx0 - kGaussMaxRadius >= 0 && tx0 + kTile + kGaussMaxRadius <= W;
+  // halo rows / columns of the extended tile outside the image: mirrored (Eq. 2's
+  // border rule) by copies after the resampling
+  const bool mirror_rows = ty0 - kGaussMaxRadius < 0 || ty0 + kTile + kGaussMaxRadius > H;
+  const bool mirror_cols = tx0 - kGaussMaxRadius < 0 || tx0 + kTile + kGaussMaxRadius > W;
 
   float w[kTaps];
 #pragma unroll
@@ -297,7 +253,8 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
   };
   const bool pairs = a.pairs != 0;
   auto geom_of = [&](int fi) {
-    return stage_geom(split_shift(shs[2 * fi]), split_shift(shs[2 * fi + 1]), tr, H, W, pairs);
+    return stage_geom(split_shift(shs[2 * fi]), split_shift(shs[2 * fi + 1]), ty0, tx0, H, W,
+                      pairs);
   };
   // prefetch pattern: column pc of rows pr, pr + 8, ... (no division); with
   // pairs, 2-pixel word pc2 of rows pr2, pr2 + 16, ...
@@ -310,29 +267,52 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
   const bool do_hp = a.out_hp && a.hp_w > 0 && a.corrected;
   const float hp_inv = 1.0f / ((float)a.hp_w * kHpScale);
 
-  // Stage the slot's first frame (blocking) and its tables.
-  StageGeom gcur = geom_of(0);
-  {
-    const uint16_t* F = frame_ptr(s0);
-    if (pairs) {
+  // Loads of a frame's window into registers: 2-pixel words (plain window, even
+  // width) or single pixels at clamped coordinates.
+  const int ncw = kFstRows + 1;  // staged columns incl. the even-rounding one (58)
+  auto load_window = [&](const uint16_t* F, const StageGeom& gm, unsigned short (&pf)[kPfRows],
+                         unsigned (&pf2)[kPf2Rows]) {
+    if (gm.plain && pairs) {
+      const unsigned* F2 = reinterpret_cast<const unsigned*>(F + (size_t)gm.r0 * W + gm.c0e);
 #pragma unroll
       for (int k = 0; k < kPf2Rows; ++k) {
         const int r = pr2 + 16 * k;
-        if (r < gcur.nr && 2 * pc2 < gcur.nc)
-          reinterpret_cast<unsigned*>(fst + r * kFst)[pc2] =
-              __ldg(reinterpret_cast<const unsigned*>(F + (size_t)(gcur.r0 + r) * W + gcur.c0) + pc2);
+        pf2[k] = (r < kFstRows && 2 * pc2 < ncw) ? __ldg(F2 + (size_t)r * (W >> 1) + pc2) : 0u;
+      }
+    } else {
+      const int cc = min(max(gm.c0 + pc, 0), W - 1);
+#pragma unroll
+      for (int k = 0; k < kPfRows; ++k) {
+        const int r = pr + 8 * k;
+        const int rr = min(max(gm.r0 + r, 0), H - 1);
+        pf[k] = (r < kFstRows && pc < kFstRows) ? __ldg(F + (size_t)rr * W + cc) : (unsigned short)0;
+      }
+    }
+  };
+  auto store_window = [&](const StageGeom& gm, const unsigned short (&pf)[kPfRows],
+                          const unsigned (&pf2)[kPf2Rows]) {
+    if (gm.plain && pairs) {
+#pragma unroll
+      for (int k = 0; k < kPf2Rows; ++k) {
+        const int r = pr2 + 16 * k;
+        if (r < kFstRows && 2 * pc2 < ncw) reinterpret_cast<unsigned*>(fst + r * kFst)[pc2] = pf2[k];
       }
     } else {
 #pragma unroll
       for (int k = 0; k < kPfRows; ++k) {
         const int r = pr + 8 * k;
-        if (r < gcur.nr && pc < gcur.nc)
-          fst[r * kFst + pc] = __ldg(F + (size_t)(gcur.r0 + r) * W + gcur.c0 + pc);
+        if (r < kFstRows && pc < kFstRows) fst[r * kFst + pc] = pf[k];
       }
     }
-    if (tid < kExt) rtab[tid] = axis_entry(ty0 - kGaussMaxRadius + tid, H, gcur.sy, gcur.r0);
-    else if (tid < 2 * kExt)
-      ctab[tid - kExt] = axis_entry(tx0 - kGaussMaxRadius + tid - kExt, W, gcur.sx, gcur.c0);
+  };
+
+  // Stage the slot's first frame (blocking).
+  StageGeom gcur = geom_of(0);
+  {
+    unsigned short pf0[kPfRows];
+    unsigned pf20[kPf2Rows];
+    load_window(frame_ptr(s0), gcur, pf0, pf20);
+    store_window(gcur, pf0, pf20);
   }
   __syncthreads();
 
@@ -345,61 +325,57 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
     unsigned pf2[kPf2Rows];
     if (more) {
       gnext = geom_of(fi + 1);
-      const uint16_t* F = frame_ptr(t + 1);
-      if (pairs) {
-        const unsigned* F2 = reinterpret_cast<const unsigned*>(F + (size_t)gnext.r0 * W + gnext.c0);
-#pragma unroll
-        for (int k = 0; k < kPf2Rows; ++k) {
-          const int r = pr2 + 16 * k;
-          pf2[k] = (r < gnext.nr && 2 * pc2 < gnext.nc) ? __ldg(F2 + (size_t)r * (W >> 1) + pc2) : 0u;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < kPfRows; ++k) {
-          const int r = pr + 8 * k;
-          pf[k] = (r < gnext.nr && pc < gnext.nc)
-                      ? __ldg(F + (size_t)(gnext.r0 + r) * W + gnext.c0 + pc)
-                      : (unsigned short)0;
-        }
-      }
+      load_window(frame_ptr(t + 1), gnext, pf, pf2);
     }
-    // 1. resample the tile + halo from the staged frame
+    // 1. resample the tile + halo from the staged frame: source (r, c) = tile
+    // coordinate relative to the window origin, constant weights
     {
       const float fy = gcur.sy.f, fx = gcur.sx.f;
-      if (gcur.plain) {
-        // source (r, c) = tile coordinate + shift - staging origin, constant weights
-        const int oy = tr.ylo + gcur.sy.i - gcur.r0, ox = tr.xlo + gcur.sx.i - gcur.c0;
-        if (tid < kExt * 8) {
-          const int ry = tid >> 3, c0 = (tid & 7) * 7;
-          const unsigned short* top = fst + (ry + oy) * kFst + c0 + ox;
-          const unsigned short* bot = top + kFst;
-          float tp[8], bt[8];
+      const int ox = gcur.c0 - gcur.c0e;  // 0, or 1 after the even rounding
+      if (tid < kExt * 8) {
+        const int ry = tid >> 3, c0 = (tid & 7) * 7;
+        const unsigned short* top = fst + ry * kFst + c0 + ox;
+        const unsigned short* bot = top + kFst;
+        float tp[8], bt[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            tp[k] = top[k];
-            bt[k] = bot[k];
-          }
-#pragma unroll
-          for (int k = 0; k < 7; ++k) {
-            const float u = fmaf(fx, tp[k + 1] - tp[k], tp[k]);
-            const float d = fmaf(fx, bt[k + 1] - bt[k], bt[k]);
-            vext[ry * kExt + c0 + k] = fmaf(fy, d - u, u);
-          }
+        for (int k = 0; k < 8; ++k) {
+          tp[k] = top[k];
+          bt[k] = bot[k];
         }
-      } else {
-        for (int i = tid; i < kExt * kExt; i += kTempThreads) {
-          const int ry = i / kExt, rx = i - ry * kExt;
-          const unsigned re = rtab[ry], ce = ctab[rx];
-          const int o0 = (re & 255) * kFst + (ce & 255);
-          const int od = ((re >> 8) & 1) * kFst, oc = (ce >> 8) & 1;
-          const float wy = (re >> 9) ? fy : 0.f, wx = (ce >> 9) ? fx : 0.f;
-          const float p = fst[o0], q = fst[o0 + oc], r = fst[o0 + od], u = fst[o0 + od + oc];
-          const float top = fmaf(wx, q - p, p), bot = fmaf(wx, u - r, r);
-          vext[i] = fmaf(wy, bot - top, top);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          const float u = fmaf(fx, tp[k + 1] - tp[k], tp[k]);
+          const float d = fmaf(fx, bt[k + 1] - bt[k], bt[k]);
+          vext[ry * kExt + c0 + k] = fmaf(fy, d - u, u);
         }
       }
     }
     __syncthreads();
+    // halo rows, then halo columns, outside the image: the value at the mirrored
+    // coordinate (always an in-image row or column of the extended tile for the
+    // 12 pixels that in-image outputs read; farther ones feed only outputs
+    // outside the image and are left as they are)
+    if (mirror_rows) {
+      // ext rows [0, nt) above the image and [kExt - nb, kExt) below it
+      const int nt = max(0, kGaussMaxRadius - ty0), nb = max(0, ty0 + kTile + kGaussMaxRadius - H);
+      for (int i = tid; i < (nt + nb) * kExt; i += kTempThreads) {
+        const int k = i / kExt, rx = i - k * kExt;
+        const int ry = k < nt ? k : kExt - nb + (k - nt);
+        const int rs = mirror_idx(ty0 - kGaussMaxRadius + ry, H) - (ty0 - kGaussMaxRadius);
+        if (rs >= 0 && rs < kExt) vext[ry * kExt + rx] = vext[rs * kExt + rx];
+      }
+      __syncthreads();
+    }
+    if (mirror_cols) {
+      const int nl = max(0, kGaussMaxRadius - tx0), nr = max(0, tx0 + kTile + kGaussMaxRadius - W);
+      for (int i = tid; i < (nl + nr) * kExt; i += kTempThreads) {
+        const int k = i / kExt, ry = i - k * kExt;
+        const int rx = k < nl ? k : kExt - nr + (k - nl);
+        const int cs = mirror_idx(tx0 - kGaussMaxRadius + rx, W) - (tx0 - kGaussMaxRadius);
+        if (cs >= 0 && cs < kExt) vext[ry * kExt + rx] = vext[ry * kExt + cs];
+      }
+      __syncthreads();
+    }
     const float v_a = vext[(ly0 + kGaussMaxRadius) * kExt + lx + kGaussMaxRadius];
     const float v_b = vext[(ly0 + 1 + kGaussMaxRadius) * kExt + lx + kGaussMaxRadius];
     // 2. corrected (or high-passed) output of frames new to this call
@@ -454,23 +430,7 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
     }
     // 4. stage the next frame (the current one was consumed before the barrier)
     if (more) {
-      if (pairs) {
-#pragma unroll
-        for (int k = 0; k < kPf2Rows; ++k) {
-          const int r = pr2 + 16 * k;
-          if (r < gnext.nr && 2 * pc2 < gnext.nc) reinterpret_cast<unsigned*>(fst + r * kFst)[pc2] = pf2[k];
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < kPfRows; ++k) {
-          const int r = pr + 8 * k;
-          if (r < gnext.nr && pc < gnext.nc) fst[r * kFst + pc] = pf[k];
-        }
-      }
-      if (tid < kExt) rtab[tid] = axis_entry(ty0 - kGaussMaxRadius + tid, H, gnext.sy, gnext.r0);
-      else if (tid < 2 * kExt)
-        ctab[tid - kExt] =
-            axis_entry(tx0 - kGaussMaxRadius + tid - kExt, W, gnext.sx, gnext.c0);
+      store_window(gnext, pf, pf2);
       gcur = gnext;
     }
     __syncthreads();
@@ -515,7 +475,7 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
 static size_t temporal_smem(int L) {
   return sizeof(float) * ((size_t)kExt * kExt + (size_t)kExt * kTile + (size_t)L * kTile * kTile +
                           2 * kMaxL) +
-         sizeof(unsigned short) * (kFstRows * kFst + 2 * kExt);
+         sizeof(unsigned short) * (kFstRows * kFst);
 }
 
 cudaError_t temporal_init() {
