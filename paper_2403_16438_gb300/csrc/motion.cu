@@ -80,6 +80,7 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 // rows y0 - R .. y0 + 21 (ny - 1) + R, likewise for columns.  One CTA per
 // 56 x 32 block of positions per frame: row sums slide along x, window sums
 // slide along y, all in 64-bit integers.
+static int g_sms = 0;  // SM count, set by kernels_init()
 constexpr int kGroup = 11;  // patches per FP32 correlation work item (see k_corr_f32)
 constexpr int kBoxRows = 56, kBoxCols = 32, kBoxThreads = 256;
 constexpr int kBoxIR = kBoxRows + kPatch - 1, kBoxIC = kBoxCols + kPatch - 1;  // 76 x 52 inputs
@@ -233,7 +234,11 @@ cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st, const int*
                                const int* list_n) {
   int blocks = b.stats_begin[b.n];
   if (blocks <= 0) return cudaSuccess;
-  if (list) blocks = std::min(blocks, 152 * 4);  // one wave; strides over the listed frames
+  if (list) {  // one wave of CTAs that stride over the listed frames' items
+    cudaError_t e = kernels_init();
+    if (e != cudaSuccess) return e;
+    blocks = std::min(blocks, 4 * g_sms);
+  }
   k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b, list, list_n);
   return cudaGetLastError();
 }
@@ -453,8 +458,6 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   }
   if (grp == 0 && !released) asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
 }
-
-static int g_sms = 0;
 
 cudaError_t kernels_init() {
   if (g_sms) return cudaSuccess;
