@@ -139,6 +139,18 @@ def kernel_traffic(kernel, source):
     return d
 
 
+def max_over_ranks(x, ws, device):
+    """Max of a host float over all ranks (the job's time is its slowest rank's);
+    x itself when there is one rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -181,7 +193,7 @@ def run_reference(args):
     o.process(frames[:1].numpy(), want_summary=False)
     t1 = time.perf_counter() - t0
     # each step: a bounded sample sized so warmup + steps end within ~3 minutes
-    per_step = int(max(1, min(64, 150.0 / max(1, args.steps + args.warmup) / max(t1, 1e-3))))
+    per_step = int(max(1, min(64, args.ref_budget / max(1, args.steps + args.warmup) / max(t1, 1e-3))))
     times = []
     for s in range(args.warmup + args.steps):
         o = oracle.Oracle(H, W, R=R)
@@ -270,11 +282,7 @@ def run_vimg(args):
     clk = clocks.stop()
     prof = h.profile_read(reset=True)
     h.profile(False)
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     total_frames = n * args.steps * ws
     value = total_frames / (ms / 1000.0)
 
@@ -371,11 +379,7 @@ def run_vimg(args):
             h.process_host(fh, shifts_host=sh_h, summary_host=sm_h, corrected=corrected)
         torch.cuda.synchronize()
         barrier()
-        te = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = t.item()
+        te = max_over_ranks(time.perf_counter() - t0, ws, dev)
         line["e2e"] = {"value": n * ke * ws / te, "unit": UNIT,
                        "h2d_bytes_per_step": n * H * W * 2,
                        "d2h_bytes_per_step": n * 2 * 4 + k_max * 2 * H * W * 4,
@@ -610,6 +614,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds of host work for the reference arm's warm-up and timed steps")
     ap.add_argument("--bf16-chunk", type=int, default=250,
                     help="frames per internal batch of the tensor-core path (two 128-frame groups)")
     ap.add_argument("--corr", choices=["f32", "bf16", "proposal"], default="f32",
