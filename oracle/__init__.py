@@ -74,7 +74,10 @@ def lib():
         L.orc_set_template.argtypes = [P, P]
         L.orc_frames_seen.argtypes = [P]
         L.orc_frames_seen.restype = ctypes.c_longlong
-        L.orc_process.argtypes = [P, P, i, P, P, P, P, P, P, P]
+        L.orc_process.argtypes = [P, P, i, P, P, P, P, P, P, P, P]
+        L.orc_set_rois.argtypes = [P, P, i]
+        L.orc_set_rois.restype = i
+        L.orc_roi_means.argtypes = [P, i, i, P, i, P]
         L.orc_process.restype = i
         _lib = L
     return _lib
@@ -155,6 +158,15 @@ def gauss(V, sigma=3.0):
     return out
 
 
+def roi_means(V, masks):
+    """Mean of the frame V [H][W] within each mask [n_rois][H][W] (0 if empty)."""
+    V = _f64(V)
+    m = np.ascontiguousarray(np.asarray(masks) != 0, dtype=np.uint8)
+    out = np.zeros(m.shape[0], np.float64)
+    lib().orc_roi_means(_p(V), V.shape[0], V.shape[1], _p(m), m.shape[0], _p(out))
+    return out
+
+
 def median(v) -> float:
     v = _f64(v)
     return lib().orc_median(_p(v), v.size)
@@ -184,6 +196,14 @@ class Oracle:
         assert T.shape == (self.H, self.W)
         lib().orc_set_template(self._h, _p(T))
 
+    def set_rois(self, masks):
+        """ROI masks [n_rois][H][W] (nonzero = in the ROI) for the voltage traces."""
+        m = np.ascontiguousarray(np.asarray(masks) != 0, dtype=np.uint8)
+        assert m.ndim == 3 and m.shape[1:] == (self.H, self.W)
+        self.n_rois = m.shape[0]
+        if lib().orc_set_rois(self._h, _p(m), self.n_rois) != 0:
+            raise MemoryError("oracle ROI masks")
+
     def process(self, frames, shifts_in=None, want_surface=False, want_corrected=True,
                 want_summary=True):
         frames = _u16(frames)
@@ -199,10 +219,12 @@ class Oracle:
         out["surface"] = np.zeros((n, w, w), np.float64) if want_surface else None
         out["corrected"] = np.zeros((n, H, W), np.float64) if want_corrected else None
         summ = np.zeros((max(kmax, 1), 2, H, W), np.float64) if want_summary else None
+        nr = getattr(self, "n_rois", 0)
+        out["traces"] = np.zeros((n, nr), np.float64) if nr else None
         sin = None if shifts_in is None else _f64(shifts_in).reshape(n, 2)
         k = lib().orc_process(self._h, _p(frames), n, _p(sin), _p(out["shifts"]),
                               _p(out["dstar"]), _p(out["info"]), _p(out["surface"]),
-                              _p(out["corrected"]), _p(summ))
+                              _p(out["corrected"]), _p(summ), _p(out["traces"]))
         if k < 0:
             raise RuntimeError("oracle process failed")
         assert k == kmax

@@ -15,7 +15,9 @@
  *   - time segments of L = 50 frames (Sec. III-B);
  *   - spatial summary S_i = temporal mean of the corrected video (Eq. 1);
  *   - temporal summary T_i = max - median of the Gaussian-smoothed video,
- *     sigma = 3 px (Eq. 2).
+ *     sigma = 3 px (Eq. 2);
+ *   - voltage traces: the mean pixel intensity within each neuron ROI for each
+ *     frame of the motion-corrected video (Sec. II, third pipeline stage).
  * Where the paper is silent (patch-grid placement, aggregation rule, tie
  * break, subpixel refinement, resampling, high-pass filter, Gaussian
  * truncation and border, median of an even count) the readings are stated at
@@ -250,6 +252,25 @@ int orc_gauss(const double* V, int H, int W, double sigma, double* Vbar) {
   return 0;
 }
 
+/* Voltage trace extraction (Sec. II, third stage of the pipeline): the mean
+ * pixel intensity within each ROI of one motion-corrected frame V [H][W].
+ * masks [n_rois][H][W]: nonzero = pixel in the ROI; ROIs may overlap.  An
+ * empty ROI gives 0 (reading: the paper never has one). */
+void orc_roi_means(const double* V, int H, int W, const uint8_t* masks, int n_rois, double* out) {
+  size_t hw = (size_t)H * W;
+  for (int r = 0; r < n_rois; ++r) {
+    const uint8_t* m = masks + hw * r;
+    double sum = 0.0;
+    long long cnt = 0;
+    for (size_t px = 0; px < hw; ++px)
+      if (m[px]) {
+        sum += V[px];
+        cnt++;
+      }
+    out[r] = cnt ? sum / (double)cnt : 0.0;
+  }
+}
+
 static int cmp_double(const void* a, const void* b) {
   double x = *(const double*)a, y = *(const double*)b;
   return (x > y) - (x < y);
@@ -279,6 +300,8 @@ typedef struct {
   double* ring;    /* last hp_w frames of V, frame t at slot t % hp_w */
   int seg_n;       /* frames in the open segment */
   double* seg_V;   /* [L][H*W] corrected frames of the open segment */
+  uint8_t* masks;  /* [n_rois][H*W] ROI masks for the voltage traces, or NULL */
+  int n_rois;
   double* seg_Vb;  /* [L][H*W] smoothed frames of the open segment */
 } orc_t;
 
@@ -289,6 +312,7 @@ void orc_destroy(orc_t* o) {
   free(o->ring);
   free(o->seg_V);
   free(o->seg_Vb);
+  free(o->masks);
   free(o);
 }
 
@@ -319,6 +343,21 @@ void orc_set_template(orc_t* o, const double* T) {
 
 long long orc_frames_seen(const orc_t* o) { return o->t; }
 
+/* ROI masks [n_rois][H][W] (copied) for the traces of orc_process; n_rois = 0
+ * clears them.  Returns 0 or -1. */
+int orc_set_rois(orc_t* o, const uint8_t* masks, int n_rois) {
+  free(o->masks);
+  o->masks = NULL;
+  o->n_rois = 0;
+  if (n_rois <= 0) return 0;
+  size_t bytes = (size_t)n_rois * o->H * o->W;
+  o->masks = (uint8_t*)malloc(bytes);
+  if (!o->masks) return -1;
+  memcpy(o->masks, masks, bytes);
+  o->n_rois = n_rois;
+  return 0;
+}
+
 /* Motion estimate of one frame over the full +-R window: shift, integer peak,
  * and {C(d*), second C, flags}.  C_out (optional) receives the (2R+1)^2
  * surface. */
@@ -336,7 +375,8 @@ int orc_estimate(const orc_t* o, const uint16_t* F, double* s, int* d, double* i
  * applied instead of being estimated (the temporal stage alone).
  * Outputs (each optional): shifts [n][2], dstar [n][2], info [n][3],
  * surface [n][(2R+1)^2], corrected [n][H][W] (V, or the high-passed V when
- * ORC_FLAG_OUT_HIGHPASS is set), summary [k][2][H][W] (S_i then T_i).
+ * ORC_FLAG_OUT_HIGHPASS is set), summary [k][2][H][W] (S_i then T_i), traces
+ * [n][n_rois] (orc_roi_means of each corrected frame V, never the high-pass).
  * Returns k, the number of segments completed by this call, or -1.
  *
  * Segments (Sec. III-B) are the absolute frame ranges [iL, (i+1)L); only
@@ -347,7 +387,8 @@ int orc_estimate(const orc_t* o, const uint16_t* F, double* s, int* d, double* i
  *   y[t] = v[t] - (1/W_hp) sum_{k=0}^{W_hp-1} v[t-k],  v[t<0] := v[0],
  * applied to V over the whole stream; it never feeds S_i or T_i. */
 int orc_process(orc_t* o, const uint16_t* frames, int n, const double* shifts_in, double* shifts,
-                int* dstar, double* info, double* surface, double* corrected, double* summary) {
+                int* dstar, double* info, double* surface, double* corrected, double* summary,
+                double* traces) {
   if (!o || !o->have_T || n < 0) return -1;
   int H = o->H, W = o->W, w = 2 * o->R + 1;
   size_t hw = (size_t)H * W;
@@ -381,6 +422,8 @@ int orc_process(orc_t* o, const uint16_t* frames, int n, const double* shifts_in
     if (dstar) dstar[2 * i] = d[0], dstar[2 * i + 1] = d[1];
     if (info) memcpy(info + 3 * i, inf, sizeof(inf));
     orc_resample(F, H, W, s[0], s[1], V);
+    if (traces && o->n_rois > 0)
+      orc_roi_means(V, H, W, o->masks, o->n_rois, traces + (size_t)i * o->n_rois);
     long long t = o->t;
     if (o->hp_w > 0) {
       if (t == 0) memcpy(o->first_V, V, sizeof(double) * hw);

@@ -207,6 +207,32 @@ def add_noise(expected: torch.Tensor, read_sigma: float, gen: torch.Generator) -
     return torch.clamp(torch.round(shot + read), 0, 65535).to(torch.int32).to(torch.uint16)
 
 
+def ground_truth(cfg: VideoConfig, n_frames: int | None = None):
+    """(scene, planted shifts, activity) exactly as make_video draws them."""
+    n = cfg.n_frames if n_frames is None else n_frames
+    g_cpu = torch.Generator().manual_seed(cfg.seed)
+    scene = make_scene(cfg, g_cpu)
+    shifts = planted_shifts(cfg, n, g_cpu)
+    act = activity(scene, n, g_cpu)
+    return scene, shifts, act
+
+
+def roi_masks(cfg: VideoConfig) -> torch.Tensor:
+    """Footprint interiors (rho < 1) of the scene's neurons at zero shift, bool
+    [n_neurons][H][W]: the synthetic stand-in for segmented neuron ROIs."""
+    scene = make_scene(cfg, torch.Generator().manual_seed(cfg.seed))
+    H, W = cfg.H, cfg.W
+    ys = torch.arange(H, dtype=torch.float32).view(H, 1)
+    xs = torch.arange(W, dtype=torch.float32).view(1, W)
+    masks = torch.zeros((len(scene.neurons), H, W), dtype=torch.bool)
+    for j, (cy, cx, a, b, th, _) in enumerate(scene.neurons):
+        c, s = math.cos(th), math.sin(th)
+        u = (c * (xs - cx) + s * (ys - cy)) / a
+        v = (-s * (xs - cx) + c * (ys - cy)) / b
+        masks[j] = (u * u + v * v) < 1.0
+    return masks
+
+
 def make_video(cfg: VideoConfig, n_frames: int | None = None, device="cpu", chunk: int = 256,
                out: torch.Tensor | None = None):
     """Returns (frames uint16 [n,H,W], planted shifts float64 [n,2] (CPU),
