@@ -405,12 +405,12 @@ def run_vimg(args):
         torch.distributed.destroy_process_group()
 
 
-def time_variant(h, frames, outs, steps, warmup, stream):
+def time_variant(h, frames, outs, steps, warmup, stream, traces=None):
     shifts, corrected, summary = outs
 
     def step():
         h.reset()
-        h.process(frames, shifts=shifts, corrected=corrected, summary=summary)
+        h.process(frames, shifts=shifts, corrected=corrected, summary=summary, traces=traces)
 
     for _ in range(warmup):
         step()
@@ -433,10 +433,27 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     """The task's other configurations on the same video: the learned shift
     proposal (CNN + +-2 px window + full-window fallback), judged against the
     full-window shifts."""
-    from paper_2403_16438_gb300 import proposal, vimg
+    from paper_2403_16438_gb300 import proposal, synth, vimg
     n = frames.shape[0]
     out = {}
     ref = ref_shifts.clone()
+    # voltage traces of the scene's neuron ROIs, fused into the temporal pass
+    masks = synth.roi_masks(synth.paper_scale_config(seed=1002 + dist_env()[1])).to(dev)
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk)
+    h.set_template(T)
+    h.set_rois(masks)
+    tr = torch.empty((n, masks.shape[0]), device=dev)
+    sh = torch.empty_like(ref)
+    ms, prof = time_variant(h, frames, (sh, corrected, summary), args.steps, args.warmup, stream,
+                            traces=tr)
+    h.close()
+    out["voltage_traces"] = {
+        "value": n * args.steps * ws / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / args.steps,
+        "n_rois": int(masks.shape[0]), "roi_pixels": int(masks.sum().item()),
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "config": "full-window FP32 path, corrected frames and summaries as the main line, plus "
+                  "the mean corrected intensity of every neuron footprint of the scene per frame",
+    }
     # BF16 tensor-core correlation (tcgen05), FP32 accumulation
     h = vimg.Handle(H, W, stream=stream, max_chunk=args.bf16_chunk, flags=vimg.CORR_BF16)
     h.set_template(T)

@@ -130,7 +130,21 @@ typedef struct {
                              only; for diagnostics and parity checks)           */
   const float* shifts_in; /* [n][2]: apply these shifts instead of estimating
                              them (the temporal stage alone)                    */
+  float* traces;          /* [n][n_rois] voltage traces: the mean of the corrected
+                             frame V_t (never the high-pass) within each ROI set
+                             by vimg_set_rois (Sec. II, third stage)            */
 } vimg_io;
+
+/* Voltage-trace ROIs (Sec. II: the third stage of the pipeline takes the mean
+ * pixel intensity within each detected neuron ROI for each frame of the
+ * motion-corrected video).  d_masks: device uint8 [n_rois][H][W], nonzero =
+ * pixel in the ROI; ROIs may overlap, up to 4 at any pixel (more returns
+ * VIMG_ERR_ARG with the previous ROIs kept).  0 <= n_rois <= 65535; n_rois = 0
+ * clears the ROIs.  The traces are accumulated inside the fused temporal pass
+ * in 2^-20 fixed point (exact and independent of the order of the additions);
+ * an empty ROI gives 0.  Synchronises the handle's stream (it checks the
+ * overlap limit).  Returns VIMG_OK or an error. */
+int vimg_set_rois(vimg_handle* h, const uint8_t* d_masks, int n_rois);
 
 /* Same as vimg_process with the vimg_io members.  Returns k or an error. */
 int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io);

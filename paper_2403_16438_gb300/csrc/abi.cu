@@ -6,7 +6,8 @@
 // the temporal pass reads them again):
 //   1. motion estimate of the whole batch: zero the fixed-point surfaces, window
 //      statistics, correlation numerators, integer peak + parabola;
-//   2. one fused temporal launch over every segment slot the batch touches;
+//   2. one fused temporal launch over every segment slot the batch touches (and,
+//      with ROIs set, the voltage traces of the batch's frames);
 //   3. the raw frames and shifts still needed later (the open segment and the
 //      high-pass history) are copied into the handle's carry buffer.
 #include <cmath>
@@ -84,6 +85,12 @@ struct vimg_handle {
   int sticky = 0;
   std::string err;
   long long id = 0;                     // unique per handle (graph cache keys)
+  // voltage-trace ROIs
+  int n_rois = 0;
+  unsigned long long* roi_members = nullptr;  // [H][W] ids + 1, four 16-bit fields
+  int* roi_count = nullptr;                   // [n_rois] pixels per ROI
+  unsigned long long* roi_acc = nullptr;      // [max_chunk][n_rois] 2^-20 fixed-point sums
+  int* roi_flag = nullptr;                    // [1] a pixel in more than 4 ROIs
   // CUDA graphs of vimg_process_batch calls led by this handle
   struct GraphEntry {
     std::vector<long long> key;
@@ -166,7 +173,8 @@ static void free_all(vimg_handle* h) {
                   h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
                   h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
                   h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
-                  h->fb_total, h->tround, h->as, h->bgc, h->fc, h->dev_err, h->num};
+                  h->fb_total, h->tround, h->as, h->bgc, h->fc, h->dev_err, h->num,
+                  h->roi_members, h->roi_count, h->roi_acc, h->roi_flag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
@@ -346,6 +354,49 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
   return VIMG_OK;
 }
 
+extern "C" int vimg_set_rois(vimg_handle* h, const uint8_t* d_masks, int n_rois) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  if (n_rois < 0 || n_rois > 65535 || (n_rois > 0 && !d_masks))
+    return fail(h, VIMG_ERR_ARG, "vimg_set_rois: n_rois must be in 0..65535 with a mask array");
+  if (n_rois == 0) {
+    h->n_rois = 0;
+    return VIMG_OK;
+  }
+  const size_t HW = (size_t)h->H * h->W;
+  unsigned long long *mem = nullptr, *acc = nullptr;
+  int *cnt = nullptr, *flag = nullptr;
+  auto drop = [&]() {
+    if (mem) cudaFree(mem);
+    if (acc) cudaFree(acc);
+    if (cnt) cudaFree(cnt);
+    if (flag) cudaFree(flag);
+  };
+  cudaError_t e = cudaMalloc((void**)&mem, sizeof(unsigned long long) * HW);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&cnt, sizeof(int) * (size_t)n_rois);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&acc, sizeof(unsigned long long) * (size_t)h->p.max_chunk * n_rois);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&flag, sizeof(int));
+  if (e == cudaSuccess) e = roi_build(d_masks, n_rois, h->H, h->W, mem, cnt, flag, h->st);
+  int too_many = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&too_many, flag, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    drop();
+    return cuda_fail(h, e, "vimg_set_rois");
+  }
+  if (too_many) {
+    drop();
+    return fail(h, VIMG_ERR_ARG, "vimg_set_rois: a pixel lies in more than 4 ROIs");
+  }
+  for (void* q : {(void*)h->roi_members, (void*)h->roi_count, (void*)h->roi_acc, (void*)h->roi_flag})
+    if (q) cudaFree(q);
+  h->roi_members = mem, h->roi_count = cnt, h->roi_acc = acc, h->roi_flag = flag;
+  h->n_rois = n_rois;
+  return VIMG_OK;
+}
+
 // Motion estimate of nf frames (nf <= max_chunk) into shifts[nf][2].
 static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shifts,
                     float* peak_info, double* surface) {
@@ -499,11 +550,20 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
   }
   TemporalArgs a = temporal_args(h, frames, n, shifts, io.corrected,
                                  io.summary ? io.summary + (size_t)k_before * 2 * HW : nullptr);
-  if (io.corrected || io.summary) {
+  const bool traces = io.traces && h->n_rois > 0;
+  if (traces) {
+    CK(cudaMemsetAsync(h->roi_acc, 0, sizeof(unsigned long long) * (size_t)n * h->n_rois, h->st),
+       "trace reset");
+    a.roi_members = h->roi_members;
+    a.roi_acc = h->roi_acc;
+    a.n_rois = h->n_rois;
+  }
+  if (io.corrected || io.summary || traces) {
     const int ps = prof_begin(h, 3);
     CK(launch_temporal(a, h->st), "temporal launch");
     prof_end(h, ps);
   }
+  if (traces) CK(roi_finalize(h->roi_acc, h->roi_count, n, h->n_rois, io.traces, h->st), "trace launch");
   return advance_state(h, frames, shifts, n, h->st);
 }
 
@@ -530,6 +590,7 @@ extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, 
     if (io->corrected) sub.corrected = io->corrected + HW * done;
     if (io->peak_info) sub.peak_info = io->peak_info + 4 * (size_t)done;
     if (io->surface) sub.surface = io->surface + (size_t)h->nwin * done;
+    if (io->traces) sub.traces = io->traces + (size_t)h->n_rois * done;
     int k = process_batch(h, d_frames + HW * done, m, sub, k_total);
     if (k < 0) return k;
     k_total += k;

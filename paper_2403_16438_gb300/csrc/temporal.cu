@@ -19,6 +19,12 @@
 // The high-pass y[t] = v[t] - (1/W) sum_{k<W} v[t-k] (v[t<0] := v[0]) keeps an
 // exact running sum in 2^-16 fixed point (64-bit integers); values leaving the
 // window are recomputed from their frames rather than stored.
+//
+// Voltage traces (Sec. II, third stage: the mean of the corrected frame within
+// each neuron ROI) ride on the same pass: each pixel's V_t, in 2^-20 fixed point,
+// is summed over the lanes of a warp per ROI and added to a 64-bit per-frame,
+// per-ROI accumulator -- integer sums, so the result does not depend on the
+// order of the atomics, on the tiling or on the chunking of the stream.
 #include <cfloat>
 #include <climits>
 
@@ -201,6 +207,40 @@ __device__ __forceinline__ void frame_at(const FrameSource& s, long long t, cons
 
 __device__ __forceinline__ long long hp_q(float v) { return __float2ll_rn(v * kHpScale); }
 
+// Adds V of this warp's 64 pixels to the per-ROI sums of frame row `acc`.  ma /
+// mb: the pixels' ROI ids + 1 in four 16-bit fields (0 = unused).  V in
+// [0, 65535] gives q = round(V 2^20) < 2^36 per pixel.  Each pass
+// takes one id still pending in some lane, so a warp does one 64-bit atomic per
+// distinct ROI it covers.
+__device__ __forceinline__ void roi_add(unsigned long long ma, unsigned long long mb, float v_a,
+                                        float v_b, unsigned long long* __restrict__ acc) {
+  const long long qa = __float2ll_rn(v_a * (float)kRoiFix), qb = __float2ll_rn(v_b * (float)kRoiFix);
+  for (;;) {
+    const unsigned long long m = ma ? ma : mb;
+    const unsigned my = m ? (unsigned)(m >> ((__ffsll((long long)m) - 1) & ~15)) & 0xffffu : 0u;
+    const unsigned any = __ballot_sync(0xffffffffu, my != 0);
+    if (!any) break;
+    const unsigned id = __shfl_sync(0xffffffffu, my, __ffs(any) - 1);
+    long long c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (((ma >> (16 * k)) & 0xffffu) == id) {
+        c += qa;
+        ma &= ~(0xffffull << (16 * k));
+      }
+      if (((mb >> (16 * k)) & 0xffffu) == id) {
+        c += qb;
+        mb &= ~(0xffffull << (16 * k));
+      }
+    }
+    // 0 <= c < 2^37: the warp sum of its low 20 and high 17 bits fits 32 bits each
+    const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)c & 0xfffffu);
+    const unsigned hi = __reduce_add_sync(0xffffffffu, (unsigned)(c >> 20));
+    if ((threadIdx.x & 31) == 0)
+      atomicAdd(acc + (id - 1), ((unsigned long long)hi << 20) + lo);
+  }
+}
+
 // ---- the fused kernel ------------------------------------------------------------
 constexpr int kPfRows = (kFstRows + 7) / 8;  // prefetch: 64 columns x 8 rows per pass
 constexpr int kPf2Rows = (kFstRows + 15) / 16;  // pairs: 32 words (64 columns) x 16 rows per pass
@@ -229,6 +269,12 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
   const long long s1 = s0 + L < t_end ? s0 + L : t_end;
   const int nfr = (int)(s1 - s0);
   const bool complete = s0 + L <= t_end;
+  // warps holding ROI pixels (the ids themselves are re-read per frame from L1)
+  const unsigned long long* roi_pa =
+      a.roi_acc && va ? a.roi_members + (size_t)ya * W + x : nullptr;
+  const unsigned long long* roi_pb =
+      a.roi_acc && vb ? a.roi_members + (size_t)yb * W + x : nullptr;
+  const bool roi_warp = __any_sync(0xffffffffu, (roi_pa && __ldg(roi_pa)) || (roi_pb && __ldg(roi_pb)));
 
   // halo rows / columns of the extended tile outside the image: mirrored (Eq. 2's
   // border rule) by copies after the resampling
@@ -411,6 +457,10 @@ __global__ void __launch_bounds__(kTempThreads, 1) k_temporal(const __grid_const
       if (va) out[(size_t)ya * W + x] = o_a;
       if (vb) out[(size_t)yb * W + x] = o_b;
     }
+    // 2b. voltage traces of frames new to this call (V, never the high-pass)
+    if (roi_warp && t >= src.t_new)
+      roi_add(roi_pa ? __ldg(roi_pa) : 0ull, roi_pb ? __ldg(roi_pb) : 0ull, v_a, v_b,
+              a.roi_acc + (size_t)(t - src.t_new) * a.n_rois);
     // 3. row pass of the Gaussian: 56 rows x 8 groups of 4 output columns
     if (tid < kExt * 8) {
       const int r = tid >> 3, cg = tid & 7;
@@ -485,6 +535,59 @@ cudaError_t temporal_init() {
                                        (int)temporal_smem(kMaxL));
   if (e == cudaSuccess) attr_set = true;
   return e;
+}
+
+// ---- voltage-trace ROIs ----------------------------------------------------------
+// One thread per pixel: the ids (+1) of the ROIs containing it, in increasing
+// order, packed into four 16-bit fields; per-ROI pixel counts.
+__global__ void k_roi_build(const uint8_t* __restrict__ masks, int n_rois, int HW,
+                            unsigned long long* __restrict__ members, int* __restrict__ counts,
+                            int* __restrict__ too_many) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+    unsigned long long m = 0;
+    int k = 0;
+    for (int r = 0; r < n_rois; ++r) {
+      if (!masks[(size_t)r * HW + p]) continue;
+      atomicAdd(counts + r, 1);
+      if (k < 4)
+        m |= (unsigned long long)(r + 1) << (16 * k);
+      else
+        atomicExch(too_many, 1);
+      ++k;
+    }
+    members[p] = m;
+  }
+}
+
+__global__ void k_roi_finalize(const unsigned long long* __restrict__ acc,
+                               const int* __restrict__ counts, long long total, int n_rois,
+                               float* __restrict__ traces) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = counts[i % n_rois];
+    traces[i] = c > 0 ? (float)((double)(long long)acc[i] / (kRoiFix * (double)c)) : 0.0f;
+  }
+}
+
+cudaError_t roi_build(const uint8_t* masks, int n_rois, int H, int W, unsigned long long* members,
+                      int* counts, int* too_many, cudaStream_t st) {
+  const int HW = H * W;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)(n_rois > 0 ? n_rois : 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(too_many, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int blocks = (HW + 255) / 256 < 4096 ? (HW + 255) / 256 : 4096;
+  k_roi_build<<<blocks, 256, 0, st>>>(masks, n_rois, HW, members, counts, too_many);
+  return cudaGetLastError();
+}
+
+cudaError_t roi_finalize(const unsigned long long* acc, const int* counts, int nf, int n_rois,
+                         float* traces, cudaStream_t st) {
+  const long long total = (long long)nf * n_rois;
+  if (total <= 0) return cudaSuccess;
+  const long long want = (total + 255) / 256;
+  const int blocks = want < 4096 ? (int)want : 4096;
+  k_roi_finalize<<<blocks, 256, 0, st>>>(acc, counts, total, n_rois, traces);
+  return cudaGetLastError();
 }
 
 bool temporal_batch_finalize(TemporalBatch& b) {

@@ -57,6 +57,9 @@ struct TemporalArgs {
   int n_seg;                          // segment slots in this launch
   int out_hp;                         // corrected output holds the high-pass
   int pairs;                          // stage frames as 2-pixel words (W even, 4-byte aligned)
+  const unsigned long long* roi_members;  // [H][W] up to 4 ROI ids + 1 (16 bits each), or null
+  unsigned long long* roi_acc;        // [n_batch][n_rois] fixed-point sums of V, or null
+  int n_rois;
   float* corrected;                   // [n_batch][H][W] or null
   float* summary;                     // [k][2][H][W] or null (slot j -> index j)
 };
@@ -176,5 +179,14 @@ cudaError_t cnn_adam(float* p, const float* g, float* m, float* v, float lr, flo
                      float eps, int step, cudaStream_t st);
 cudaError_t cnn_to_bf16(const float* p, __nv_bfloat16* q, cudaStream_t st);
 cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st);
+// Voltage-trace ROIs: per-pixel membership (up to 4 ids + 1 packed in 16-bit
+// fields) and per-ROI pixel counts from uint8 masks; *too_many set when a pixel
+// lies in more than 4 ROIs.
+cudaError_t roi_build(const uint8_t* masks, int n_rois, int H, int W,
+                      unsigned long long* members, int* counts, int* too_many, cudaStream_t st);
+// traces[f][r] = acc[f][r] / (2^20 * counts[r]) (0 for an empty ROI).
+cudaError_t roi_finalize(const unsigned long long* acc, const int* counts, int nf, int n_rois,
+                         float* traces, cudaStream_t st);
+constexpr double kRoiFix = 1048576.0;  // 2^20: fixed-point scale of the trace sums
 
 }  // namespace vimg

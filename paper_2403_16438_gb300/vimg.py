@@ -43,6 +43,7 @@ class IO(ctypes.Structure):
         ("peak_info", ctypes.c_void_p),
         ("surface", ctypes.c_void_p),
         ("shifts_in", ctypes.c_void_p),
+        ("traces", ctypes.c_void_p),
     ]
 
 
@@ -62,7 +63,7 @@ EXPORTS = [
     "vimg_version", "vimg_profile_enable", "vimg_profile_read", "vimg_motion_noalloc",
     "vimg_cnn_param_count", "vimg_cnn_workspace_floats", "vimg_cnn_prepare", "vimg_cnn_pack_bf16",
     "vimg_cnn_forward", "vimg_cnn_loss", "vimg_cnn_backward", "vimg_cnn_adam", "vimg_load_proposal",
-    "vimg_proposal_stats", "vimg_synchronize", "vimg_process_batch",
+    "vimg_proposal_stats", "vimg_synchronize", "vimg_process_batch", "vimg_set_rois",
 ]
 NSTAGES = 6
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
@@ -81,6 +82,8 @@ def _load():
     L.vimg_destroy.restype = None
     L.vimg_set_template.argtypes = [vp, vp]
     L.vimg_set_template.restype = i
+    L.vimg_set_rois.argtypes = [vp, vp, i]
+    L.vimg_set_rois.restype = i
     L.vimg_process.argtypes = [vp, vp, i, vp, vp, vp]
     L.vimg_process.restype = i
     L.vimg_process_io.argtypes = [vp, vp, i, P(IO)]
@@ -163,6 +166,7 @@ class Handle:
         p.stream = ctypes.c_void_p(stream.cuda_stream)
         self.params = p
         self.H, self.W = H, W
+        self.n_rois = 0
         self._h = lib.vimg_create(H, W, ctypes.byref(p))
         if not self._h:
             raise VimgError(ERR_ARG, lib.vimg_last_error(None).decode())
@@ -200,14 +204,29 @@ class Handle:
     def reset(self):
         self._check(lib.vimg_reset(self._h))
 
+    def set_rois(self, masks: torch.Tensor):
+        """masks: cuda uint8 or bool [n_rois, H, W] (nonzero = in the ROI), or
+        None to clear.  Traces of later process(traces=...) calls are the mean
+        corrected intensity per ROI and frame."""
+        if masks is None or masks.shape[0] == 0:
+            self.n_rois = 0
+            self._check(lib.vimg_set_rois(self._h, None, 0))
+            return
+        assert masks.is_cuda and masks.dtype in (torch.uint8, torch.bool)
+        assert masks.shape[1:] == (self.H, self.W)
+        m = masks.to(torch.uint8).contiguous()
+        self._check(lib.vimg_set_rois(self._h, _ptr(m), m.shape[0]))
+        self.n_rois = m.shape[0]
+
     def process(self, frames, shifts=None, corrected=None, summary=None, peak_info=None,
-                surface=None, shifts_in=None) -> int:
+                surface=None, shifts_in=None, traces=None) -> int:
         """frames: cuda uint16 [n,H,W].  Outputs are optional preallocated cuda
-        tensors (see vimg_io).  Returns k, the segments written."""
+        tensors (see vimg_io; traces: float32 [n, n_rois]).  Returns k, the
+        segments written."""
         assert frames.is_cuda and frames.dtype == torch.uint16 and frames.is_contiguous()
         n = frames.shape[0]
         io = IO(_ptr(shifts), _ptr(corrected), _ptr(summary), _ptr(peak_info), _ptr(surface),
-                _ptr(shifts_in))
+                _ptr(shifts_in), _ptr(traces))
         return self._check(lib.vimg_process_io(self._h, _ptr(frames), n, ctypes.byref(io)))
 
     def process_host(self, frames_host, shifts_host=None, summary_host=None,

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(vimg):
 def test_struct_layouts_match_header(vimg):
     # vimg_params: 8 ints/floats, a pointer, a long long, an int (+ padding)
     assert ctypes.sizeof(vimg.Params) == 56
-    assert ctypes.sizeof(vimg.IO) == 6 * 8
+    assert ctypes.sizeof(vimg.IO) == 7 * 8
 
 
 def test_defaults(vimg):
