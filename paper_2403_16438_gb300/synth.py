@@ -361,3 +361,51 @@ def augmented_batch(pool, n: int, gen: torch.Generator):
     if op & 4:  # transpose
         f, t, s = f.transpose(1, 2), t.transpose(1, 2), s[:, [1, 0]]
     return f.contiguous().view(torch.uint16), t.contiguous(), s.contiguous()
+
+
+def unet_params(layers, seed: int = 0) -> torch.Tensor:
+    """Seeded random-initialised weights for a network given as [(kind, cin,
+    cout)] with kind 'conv' (3x3), 'up' (2x2 stride-2 transposed) or 'out'
+    (1x1): weights N(0, 2 / fan_in) (He), biases U(-0.1, 0.1), flat float32 in
+    layer order, weights before biases.  A stand-in for trained weights (none
+    are available)."""
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for kind, ci, co in layers:
+        taps = {"conv": 9, "up": 4, "out": 1}[kind]
+        fan_in = ci * taps if kind != "up" else ci
+        gain = 2.0 if kind != "out" else 1.0
+        parts.append(torch.randn(ci * co * taps, generator=g, dtype=torch.float64)
+                     * math.sqrt(gain / fan_in))
+        parts.append((torch.rand(co, generator=g, dtype=torch.float64) - 0.5) * 0.2)
+    return torch.cat(parts).to(torch.float32)
+
+
+def summary_pair(cfg: VideoConfig, k: int, seed: int = 0) -> torch.Tensor:
+    """[k][2][H][W] float32 stand-ins for segment summaries: S = the scene's
+    resting image plus read noise, T = Gaussian blobs at the neurons that
+    spike in the segment plus a small noise floor (the shape of Eq. 1 / Eq. 2
+    outputs, without running the temporal pass)."""
+    g = torch.Generator().manual_seed(seed)
+    scene = make_scene(cfg, torch.Generator().manual_seed(cfg.seed))
+    H, W = cfg.H, cfg.W
+    ys = torch.arange(H, dtype=torch.float64).view(H, 1)
+    xs = torch.arange(W, dtype=torch.float64).view(1, W)
+    base = torch.full((H, W), float(cfg.bg_amp), dtype=torch.float64)
+    blobs = []
+    for (cy, cx, a, b, th, amp) in scene.neurons:
+        c, s = math.cos(th), math.sin(th)
+        u = (c * (xs - cx) + s * (ys - cy)) / a
+        v = (-s * (xs - cx) + c * (ys - cy)) / b
+        fp = torch.exp(-0.5 * (u * u + v * v) * 4.0)
+        base += amp * fp
+        blobs.append(fp)
+    out = torch.zeros((k, 2, H, W), dtype=torch.float64)
+    for i in range(k):
+        out[i, 0] = base + torch.randn((H, W), generator=g, dtype=torch.float64) * cfg.read_sigma
+        t = torch.rand((H, W), generator=g, dtype=torch.float64) * 5.0
+        for fp in blobs:
+            if torch.rand(1, generator=g).item() < 0.5:
+                t += 60.0 * fp
+        out[i, 1] = t
+    return out.to(torch.float32)
