@@ -133,6 +133,10 @@ typedef struct {
   float* traces;          /* [n][n_rois] voltage traces: the mean of the corrected
                              frame V_t (never the high-pass) within each ROI set
                              by vimg_set_rois (Sec. II, third stage)            */
+  float* prob;            /* [k][H][W] spiking-probability maps of the segments the
+                             call completes (U-Net of Sec. III-C on each summary
+                             pair); needs `summary` and a U-Net attached with
+                             vimg_attach_unet                                   */
 } vimg_io;
 
 /* Voltage-trace ROIs (Sec. II: the third stage of the pipeline takes the mean
@@ -299,6 +303,79 @@ int vimg_motion_noalloc(const float* d_template, const uint16_t* d_frames, int n
 
 /* Library version string. */
 const char* vimg_version(void);
+
+/* ---- spiking-pixel U-Net (Sec. III-C) ---------------------------------------
+ * A U-Net on 64x64 patches of a segment's summary pair (S_i, T_i) gives the
+ * probability that spiking neurons lie at each pixel during the segment; the
+ * patches (every 32 px along each axis plus one flush with the far border) are
+ * merged into one H x W map by a weighted average with the tent weight
+ * w(u) w(v), w(u) = min(u + 1, 64 - u).  Inputs are S_i and T_i standardised
+ * over the whole image, (x - mean) / (std + 1e-3).
+ *
+ * Network (layer sizes are a reading; the paper's figure is not available):
+ * levels at 64, 32, 16, 8, 4 px with 16, 32, 64, 128, 256 channels; per level
+ * two 3x3 convolutions (zero padding 1) + ReLU, 2x2 max pooling between
+ * levels; decoder: 2x2 stride-2 up-convolution (no activation), concatenation
+ * [skip, up], two 3x3 convolutions + ReLU; output 1x1 convolution 16 -> 1 and
+ * a sigmoid.  3x3 and up-convolutions run on the tensor cores with BF16
+ * weights and activations and FP32 accumulation; the output layer in FP32.
+ *
+ * Parameters: flat float32, per layer in network order (vimg_unet_layers) the
+ * weights then the bias; 3x3 weights [Cout][Cin][3][3], up-convolution weights
+ * [Cin][Cout][2][2] (out[co][2y+i][2x+j] += in[ci][y][x] w[ci][co][i][j]),
+ * output weights [16] and bias [1]. */
+typedef struct vimg_unet vimg_unet;
+
+/* Number of parameters (floats). */
+int vimg_unet_param_count(void);
+
+/* Architecture in parameter order: kind (0 = 3x3 convolution + ReLU, 1 = 2x2
+ * up-convolution, 2 = 1x1 output + sigmoid), input and output channels of
+ * the first `cap` layers (NULL arrays allowed).  Returns the layer count. */
+int vimg_unet_layers(int* kind, int* cin, int* cout, int cap);
+
+/* Workspace for H x W summary images (64 <= H, W <= 8192) and up to
+ * `max_segments` segments per internal pass; all calls enqueue on `stream`
+ * (a cudaStream_t, NULL = legacy default).  NULL on failure
+ * (vimg_unet_last_error(NULL) says why). */
+vimg_unet* vimg_unet_create(int H, int W, int max_segments, void* stream);
+void vimg_unet_destroy(vimg_unet* u);
+const char* vimg_unet_last_error(const vimg_unet* u);
+
+/* Converts the parameters (device float32, vimg_unet_param_count floats) into
+ * the tensor-core layout; the array may be freed once the stream has passed
+ * this call. */
+int vimg_unet_load(vimg_unet* u, const float* d_params);
+
+/* d_summary: device float32 [k][2][H][W] (S_i, T_i); d_prob: device float32
+ * [k][H][W].  Any k >= 0 (processed max_segments at a time). */
+int vimg_unet_run(vimg_unet* u, const float* d_summary, int k, float* d_prob);
+
+/* Synchronises the stream; VIMG_ERR_TIMEOUT (sticky) if a tensor-core kernel's
+ * bounded wait gave up. */
+int vimg_unet_synchronize(vimg_unet* u);
+
+/* CUDA-event timing of the tensor-core launches and of whole runs (ms), summed
+ * until read with reset != 0.  Profiling synchronises at the end of each run. */
+int vimg_unet_profile(vimg_unet* u, int on);
+int vimg_unet_profile_read(vimg_unet* u, double* conv_ms, double* total_ms,
+                           long long* conv_launches, int reset);
+
+/* Inspection of the last internal pass of vimg_unet_run (its n_patches =
+ * patches of up to max_segments segments, patch order segment-major, then
+ * patch rows, then patch columns): i = 0 the standardised input patches
+ * (BF16 [n][64][64][16], channels 0 and 1 = S, T), i = 1..22 the output of the
+ * i-th 3x3 or up-convolution in execution order (BF16 NHWC [n][side][side][C];
+ * execution order = parameter order), i = 23 the per-patch probabilities
+ * (float32 [n][64][64]).  Reports n_patches, side and C; copies into d_out
+ * (device, dense) on the stream unless it is NULL. */
+int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_patches, int* side,
+                         int* channels);
+
+/* Attaches a U-Net of the same H x W to a handle (NULL detaches); the handle
+ * does not own it.  vimg_process_io then fills vimg_io.prob on the handle's
+ * stream. */
+int vimg_attach_unet(vimg_handle* h, vimg_unet* u);
 
 #ifdef __cplusplus
 }

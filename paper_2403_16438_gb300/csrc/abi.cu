@@ -91,6 +91,7 @@ struct vimg_handle {
   int* roi_count = nullptr;                   // [n_rois] pixels per ROI
   unsigned long long* roi_acc = nullptr;      // [max_chunk][n_rois] 2^-20 fixed-point sums
   int* roi_flag = nullptr;                    // [1] a pixel in more than 4 ROIs
+  vimg_unet* unet = nullptr;                  // attached U-Net stage (not owned)
   // CUDA graphs of vimg_process_batch calls led by this handle
   struct GraphEntry {
     std::vector<long long> key;
@@ -354,6 +355,18 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
   return VIMG_OK;
 }
 
+extern "C" int vimg_attach_unet(vimg_handle* h, vimg_unet* u) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  if (u) {
+    int H = 0, W = 0;
+    unet_dims(u, &H, &W);
+    if (H != h->H || W != h->W) return fail(h, VIMG_ERR_ARG, "vimg_attach_unet: size mismatch");
+  }
+  h->unet = u;
+  return VIMG_OK;
+}
+
 extern "C" int vimg_set_rois(vimg_handle* h, const uint8_t* d_masks, int n_rois) {
   if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
   if (h->sticky) return h->sticky;
@@ -564,7 +577,13 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
     prof_end(h, ps);
   }
   if (traces) CK(roi_finalize(h->roi_acc, h->roi_count, n, h->n_rois, io.traces, h->st), "trace launch");
-  return advance_state(h, frames, shifts, n, h->st);
+  const int k = advance_state(h, frames, shifts, n, h->st);
+  if (k > 0 && io.prob) {
+    const int rc = vimg_unet_run_on(h->unet, io.summary + (size_t)k_before * 2 * HW, k,
+                                    io.prob + (size_t)k_before * HW, h->st);
+    if (rc < 0) return fail(h, rc, std::string("U-Net: ") + vimg_unet_last_error(h->unet));
+  }
+  return k;
 }
 
 extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io) {
@@ -575,6 +594,8 @@ extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, 
     return fail(h, VIMG_ERR_NO_TEMPLATE, "vimg_set_template must come before vimg_process");
   if (!io->shifts_in && (h->p.flags & VIMG_PROPOSAL_CNN) && !h->have_proposal)
     return fail(h, VIMG_ERR_ARG, "vimg_load_proposal must come before vimg_process");
+  if (io->prob && (!io->summary || !h->unet))
+    return fail(h, VIMG_ERR_ARG, "vimg_io.prob needs summary output and an attached U-Net");
   const size_t HW = (size_t)h->H * h->W;
   const int L = h->p.segment_len, maxc = h->p.max_chunk;
   int done = 0, k_total = 0;

@@ -1,0 +1,918 @@
+// Spiking-pixel U-Net stage for sm_103a (Sec. III-C of Bando et al., BIBM 2023):
+// a U-Net on 64x64 patches of the segment's summary pair (S_i, T_i), patches
+// every 32 px (plus one flush with the far border), outputs merged into one
+// probability map per segment by a tent-weighted average.
+//
+// Network (the layer sizes of the paper's figure are not available; this is
+// the reading): per level two 3x3 convolutions (zero padding 1) + ReLU with
+// 16, 32, 64, 128, 256 channels at 64, 32, 16, 8, 4 px, 2x2 max pooling between
+// levels; decoder: 2x2 stride-2 up-convolution (no activation) halving the
+// channels, concatenation [skip, up], two 3x3 convolutions + ReLU; output 1x1
+// convolution 16 -> 1 and a sigmoid.  Inputs: S_i and T_i standardised over the
+// whole image, (x - mean) / (std + 1e-3).
+//
+// Every 3x3 convolution and up-convolution is an implicit GEMM on the tensor
+// cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulation in TMEM):
+//   D[pixel][n] = sum_{tap, ci} A[pixel][(tap, ci)] * B[(tap, ci)][n]
+// M = 128 consecutive pixels of the NHWC activations (whole image rows, or
+// whole images below 128 px), N = output channels (x 4 quadrants for an
+// up-convolution), K = taps x input channels in chunks of up to 64 channels.
+// A chunk (one tap) arrives by TMA from the activations as 8-channel boxes of
+// 128 pixels shifted by the tap (zero fill outside the image gives the
+// padding); these boxes are exactly the K-major core-matrix layout (8 pixels x
+// 16 B per core matrix, 2 KB between 8-channel groups).  B chunks are weights
+// pre-packed in the same layout and fetched by one bulk copy.
+//
+// Warp roles (persistent CTAs, 192 threads): warp 4 producer, warp 5 MMA
+// issuer, warps 0-3 epilogue (TMEM lane = pixel): + bias, ReLU, BF16 stores
+// into NHWC at a channel offset (which forms the concatenations in place), or
+// the 2x2 scatter of an up-convolution.  Two TMEM accumulators let the
+// epilogue of one tile overlap the MMAs of the next.  Every wait is bounded:
+// on timeout the CTA records an error, stops issuing, drains its own copies and
+// MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tc_ptx.h"
+#include "vimg_internal.h"
+
+namespace vimg {
+namespace {
+using namespace tc;
+
+constexpr int kUPatch = 64;
+constexpr int kUStride = 32;
+constexpr int kULevels = 4;
+constexpr int kUC0 = 16;                 // channels at 64x64
+constexpr double kUEps = 1e-3;           // standardisation: (x - m) / (sd + eps)
+constexpr int kUMaxStages = 8;
+constexpr int kUEpiWarps = 4;
+constexpr int kUThreads = (kUEpiWarps + 2) * 32;  // 192
+constexpr size_t kUSmemMax = 200 * 1024;
+
+// Architecture in parameter order: kind (0 conv 3x3, 1 up 2x2, 2 output 1x1),
+// input and output channels.
+struct LayerDef {
+  int kind, cin, cout;
+};
+
+std::vector<LayerDef> unet_defs() {
+  std::vector<LayerDef> d;
+  int ch[kULevels + 1];
+  for (int l = 0; l <= kULevels; ++l) ch[l] = kUC0 << l;
+  d.push_back({0, 2, ch[0]});
+  d.push_back({0, ch[0], ch[0]});
+  for (int l = 1; l <= kULevels; ++l) {
+    d.push_back({0, ch[l - 1], ch[l]});
+    d.push_back({0, ch[l], ch[l]});
+  }
+  for (int l = kULevels - 1; l >= 0; --l) {
+    d.push_back({1, ch[l + 1], ch[l]});
+    d.push_back({0, 2 * ch[l], ch[l]});
+    d.push_back({0, ch[l], ch[l]});
+  }
+  d.push_back({2, ch[0], 1});
+  return d;
+}
+
+size_t weight_count(const LayerDef& L) {
+  const int taps = L.kind == 0 ? 9 : (L.kind == 1 ? 4 : 1);
+  return (size_t)L.cin * L.cout * taps;
+}
+
+struct ConvParams {
+  int total_px;            // P * Hl * Wl (input pixels)
+  int Hl, Wl, bh, bb;      // input image, TMA box rows and images (bh * bb * Wl = 128)
+  int kc, nkc, taps;       // channels per K chunk, chunks per tap, taps (9 or 1)
+  int ntile, n_ntiles, n_mtiles;
+  int stages;
+  uint32_t a_bytes, b_bytes;
+  const __nv_bfloat16* wpack;  // [n_ntiles][taps * nkc][kc / 8][ntile][8]
+  const float* bias;           // [n_ntiles * ntile]
+  __nv_bfloat16* out;
+  int out_stride, out_off;     // channels per output pixel, first channel written
+  int up, cout, relu;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(kUThreads, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kUMaxStages], empty[kUMaxStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = p.stages;
+  unsigned char* sA = smem;                                  // [S][a_bytes]
+  unsigned char* sB = smem + (size_t)S * p.a_bytes;          // [S][b_bytes]
+  const int n_tiles = p.n_mtiles * p.n_ntiles;
+  const int nq = p.taps * p.nkc;
+  const uint32_t tcols = (uint32_t)(2 * p.ntile) < 32u ? 32u : (uint32_t)(2 * p.ntile);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_base)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kUEpiWarps);
+    }
+    mbar_init(&mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int img_px = p.Hl * p.Wl;
+
+  if (warp == kUEpiWarps) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
+        const int nt = tile % p.n_ntiles, mt = tile / p.n_ntiles;
+        const int m0 = mt * 128, b0 = m0 / img_px, h0 = (m0 - b0 * img_px) / p.Wl;
+        for (int q = 0; q < nq; ++q, ++it) {
+          const int s = it % S, cyc = it / S;
+          if (cyc > 0 && !mbar_wait(&empty[s], (cyc - 1) & 1)) {
+            atomicExch(p.err, 1);
+            abort_flag = 1;
+            break;
+          }
+          const int t = q / p.nkc, c = q - t * p.nkc;
+          const int dy = p.taps == 9 ? t / 3 - 1 : 0, dx = p.taps == 9 ? t % 3 - 1 : 0;
+          mbar_expect_tx(&full[s], p.a_bytes + p.b_bytes);
+          unsigned char* a_dst = sA + (size_t)s * p.a_bytes;
+          for (int g = 0; g < p.kc / 8; ++g)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                    su32(a_dst + g * 2048)),
+                "l"(&tmap), "r"(c * p.kc + 8 * g), "r"(dx), "r"(h0 + dy), "r"(b0),
+                "r"(su32(&full[s]))
+                : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(sB + (size_t)s * p.b_bytes)),
+              "l"(p.wpack + ((size_t)nt * nq + q) * (p.b_bytes / 2)), "r"(p.b_bytes),
+              "r"(su32(&full[s]))
+              : "memory");
+        }
+      }
+      // wait (bounded) for the last use of every stage: no copy outlives the CTA
+      for (int s = 0; s < S && s < it; ++s) mbar_wait(&full[s], ((it - 1 - s) / S) & 1);
+    }
+  } else if (warp == kUEpiWarps + 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      bool issued = false;
+      const uint32_t idesc = idesc_for(p.ntile);
+      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++tl) {
+        const int buf = tl & 1, use = tl >> 1;
+        if (use > 0) {
+          if (!mbar_wait(&acc_empty[buf], (use - 1) & 1)) {
+            atomicExch(p.err, 1);
+            abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        const uint32_t d = tmem + (uint32_t)(buf * p.ntile);
+        for (int q = 0; q < nq; ++q, ++it) {
+          const int s = it % S;
+          if (!mbar_wait(&full[s], (it / S) & 1)) {
+            atomicExch(p.err, 1);
+            abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint64_t ad0 = desc(su32(sA + (size_t)s * p.a_bytes), 2048, 128);
+          const uint64_t bd0 = desc(su32(sB + (size_t)s * p.b_bytes), p.ntile * 16, 128);
+          for (int k = 0; k < p.kc / 16; ++k) {
+            const uint64_t ad = ad0 + (uint64_t)(k * (2 * 2048 >> 4));
+            const uint64_t bd = bd0 + (uint64_t)(k * (2 * p.ntile * 16 >> 4));
+            const uint32_t acc = (q > 0 || k > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+          issued = true;
+          mma_commit(&empty[s]);
+        }
+        if (abort_flag) break;
+        mma_commit(&acc_full[buf]);
+      }
+      // every MMA issued by this thread has completed before the CTA frees TMEM
+      if (issued) {
+        mma_commit(&mma_done);
+        mbar_wait(&mma_done, 0);
+      }
+    }
+  } else {
+    // ------ epilogue: warp w owns TMEM lanes (pixels) 32 w .. 32 w + 31 ------
+    int tl = 0;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
+      const int buf = tl & 1, use = tl >> 1;
+      const int nt = tile % p.n_ntiles, mt = tile / p.n_ntiles;
+      const int m = mt * 128 + warp * 32 + lane;
+      if (!mbar_wait(&acc_full[buf], use & 1)) {
+        atomicExch(p.err, 1);
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const bool valid = m < p.total_px;
+      const int b = m / img_px, r = m - b * img_px, h = r / p.Wl, w = r - h * p.Wl;
+      for (int c0 = 0; c0 < p.ntile; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + (uint32_t)(buf * p.ntile + c0), v);
+        if (!valid) continue;
+        const int ng = nt * p.ntile + c0;
+        const float* bs = p.bias + ng;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          v[j] += __ldg(bs + j);
+          if (p.relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        size_t opix;
+        int ch;
+        if (p.up) {
+          const int qd = ng / p.cout, i = qd >> 1, jj = qd & 1;
+          ch = ng - qd * p.cout;
+          opix = ((size_t)b * 2 * p.Hl + 2 * h + i) * (2 * p.Wl) + 2 * w + jj;
+        } else {
+          ch = ng;
+          opix = (size_t)m;
+        }
+        uint4 lo, hi;
+        lo.x = pack_bf16x2(v[0], v[1]), lo.y = pack_bf16x2(v[2], v[3]);
+        lo.z = pack_bf16x2(v[4], v[5]), lo.w = pack_bf16x2(v[6], v[7]);
+        hi.x = pack_bf16x2(v[8], v[9]), hi.y = pack_bf16x2(v[10], v[11]);
+        hi.z = pack_bf16x2(v[12], v[13]), hi.w = pack_bf16x2(v[14], v[15]);
+        uint4* dst = reinterpret_cast<uint4*>(p.out + opix * p.out_stride + p.out_off + ch);
+        dst[0] = lo;
+        dst[1] = hi;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
+// ---- small kernels ---------------------------------------------------------------
+// Weights of one layer into the B-operand layout [nt][tap * nkc + c][g][n][8]
+// (ci = c kc + 8 g + j, column ng = nt ntile + n), BF16; biases per column.
+__global__ void k_pack(const float* __restrict__ w, const float* __restrict__ bias, int up,
+                       int cin_real, int cout, int taps, int kc, int nkc, int ntile, int n_ntiles,
+                       __nv_bfloat16* __restrict__ out, float* __restrict__ bout) {
+  const int nq = taps * nkc;
+  const long long total = (long long)n_ntiles * nq * kc * ntile;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long r = i;
+    const int j = (int)(r % 8);
+    r /= 8;
+    const int n = (int)(r % ntile);
+    r /= ntile;
+    const int g = (int)(r % (kc / 8));
+    r /= kc / 8;
+    const int q = (int)(r % nq);
+    const int nt = (int)(r / nq);
+    const int t = q / nkc, ci = (q - t * nkc) * kc + 8 * g + j, ng = nt * ntile + n;
+    float v = 0.f;
+    if (ci < cin_real) {
+      if (up) {
+        const int qd = ng / cout, co = ng - qd * cout;
+        v = w[(((size_t)ci * cout + co) * 2 + (qd >> 1)) * 2 + (qd & 1)];
+      } else {
+        v = w[((size_t)ng * cin_real + ci) * 9 + t];
+      }
+    }
+    out[i] = __float2bfloat16_rn(v);
+    if (i < (long long)n_ntiles * ntile) bout[i] = bias[up ? (int)(i % cout) : (int)i];
+  }
+}
+
+// Mean and 1 / (population std + eps) of each summary image, FP64, two passes,
+// fixed reduction order (one block per image).
+__global__ void k_ustats(const float* __restrict__ summary, int HW, double* __restrict__ stats) {
+  __shared__ double red[256];
+  const float* img = summary + (size_t)blockIdx.x * HW;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < HW; i += blockDim.x) s += (double)img[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double mean = red[0] / HW;
+  __syncthreads();
+  double q = 0.0;
+  for (int i = threadIdx.x; i < HW; i += blockDim.x) {
+    const double d = (double)img[i] - mean;
+    q += d * d;
+  }
+  red[threadIdx.x] = q;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[2 * blockIdx.x] = mean;
+    stats[2 * blockIdx.x + 1] = sqrt(red[0] / HW) + kUEps;
+  }
+}
+
+__device__ __forceinline__ int upos(int j, int n) { return min(kUStride * j, n - kUPatch); }
+
+// Patches of the standardised pair: in0[P][64][64][16], channels 0 and 1 = S, T.
+__global__ void k_uinput(const float* __restrict__ summary, const double* __restrict__ stats,
+                         int H, int W, int npy, int npx, int n_patch_total,
+                         __nv_bfloat16* __restrict__ in0) {
+  const long long total = (long long)n_patch_total * kUPatch * kUPatch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(i % kUPatch), u = (int)((i / kUPatch) % kUPatch);
+    const int pt = (int)(i / (kUPatch * kUPatch));
+    const int seg = pt / (npy * npx), pr = pt - seg * npy * npx;
+    const int y = upos(pr / npx, H) + u, x = upos(pr % npx, W) + v;
+    const size_t HW = (size_t)H * W;
+    const float* S = summary + (size_t)seg * 2 * HW;
+    const double* st = stats + 4 * seg;
+    const double zs = ((double)S[(size_t)y * W + x] - st[0]) / st[1];
+    const double zt = ((double)S[HW + (size_t)y * W + x] - st[2]) / st[3];
+    uint4 a;
+    a.x = pack_bf16x2((float)zs, (float)zt);
+    a.y = a.z = a.w = 0u;
+    uint4* dst = reinterpret_cast<uint4*>(in0 + (size_t)i * kUC0);
+    dst[0] = a;
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// 2x2 max pooling, NHWC: input channels [0, C) of a buffer with cs channels.
+__global__ void k_upool(const __nv_bfloat16* __restrict__ in, int P, int Ho, int Wo, int C,
+                        int cs, __nv_bfloat16* __restrict__ out) {
+  const int G = C / 8;
+  const long long total = (long long)P * Ho * Wo * G;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(i % G);
+    const long long px = i / G;
+    const int xo = (int)(px % Wo), yo = (int)((px / Wo) % Ho);
+    const long long b = px / ((long long)Wo * Ho);
+    const int Wi = 2 * Wo;
+    const size_t base = (((size_t)b * 2 * Ho + 2 * yo) * Wi + 2 * xo) * cs + 8 * g;
+    const uint4 a = *reinterpret_cast<const uint4*>(in + base);
+    const uint4 bq = *reinterpret_cast<const uint4*>(in + base + cs);
+    const uint4 c = *reinterpret_cast<const uint4*>(in + base + (size_t)Wi * cs);
+    const uint4 d = *reinterpret_cast<const uint4*>(in + base + (size_t)Wi * cs + cs);
+    const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
+    const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&bq);
+    const __nv_bfloat162* pc = reinterpret_cast<const __nv_bfloat162*>(&c);
+    const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&d);
+    uint4 o;
+    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) po[k] = __hmax2(__hmax2(pa[k], pb[k]), __hmax2(pc[k], pd[k]));
+    *reinterpret_cast<uint4*>(out + (size_t)px * C + 8 * g) = o;
+  }
+}
+
+// Output layer: p = sigmoid(b + sum_c w_c d0_c), FP32 weights, per patch pixel.
+__global__ void k_uout(const __nv_bfloat16* __restrict__ d0, const float* __restrict__ wout,
+                       long long n_px, float* __restrict__ prob) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_px;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint4* src = reinterpret_cast<const uint4*>(d0 + (size_t)i * kUC0);
+    const uint4 a = src[0], b = src[1];
+    const __nv_bfloat16* ha = reinterpret_cast<const __nv_bfloat16*>(&a);
+    const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&b);
+    float s = wout[kUC0];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s = fmaf(wout[c], __bfloat162float(ha[c]), s);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s = fmaf(wout[8 + c], __bfloat162float(hb[c]), s);
+    prob[i] = 1.0f / (1.0f + expf(-s));
+  }
+}
+
+__device__ __forceinline__ float utent(int u) { return (float)min(u + 1, kUPatch - u); }
+
+// Weighted average of the patches covering each pixel (fixed order).
+__global__ void k_umerge(const float* __restrict__ pprob, int H, int W, int npy, int npx, int k,
+                         float* __restrict__ out) {
+  const long long total = (long long)k * H * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(i % W), Y = (int)((i / W) % H), seg = (int)(i / ((long long)H * W));
+    int cy[3] = {Y / kUStride - 1, Y / kUStride, npy - 1};
+    int cx[3] = {X / kUStride - 1, X / kUStride, npx - 1};
+    float acc = 0.f, ws = 0.f;
+    for (int a = 0; a < 3; ++a) {
+      const int jy = cy[a];
+      if (jy < 0 || jy >= npy || (a == 2 && (jy == cy[0] || jy == cy[1]))) continue;
+      const int u = Y - upos(jy, H);
+      if (u < 0 || u >= kUPatch) continue;
+      for (int c = 0; c < 3; ++c) {
+        const int jx = cx[c];
+        if (jx < 0 || jx >= npx || (c == 2 && (jx == cx[0] || jx == cx[1]))) continue;
+        const int v = X - upos(jx, W);
+        if (v < 0 || v >= kUPatch) continue;
+        const float wt = utent(u) * utent(v);
+        const size_t pt = (size_t)seg * npy * npx + (size_t)jy * npx + jx;
+        acc = fmaf(wt, pprob[(pt * kUPatch + u) * kUPatch + v], acc);
+        ws += wt;
+      }
+    }
+    out[i] = acc / ws;
+  }
+}
+
+int grid_for(long long n, int threads, int sms) {
+  const long long want = (n + threads - 1) / threads;
+  const long long cap = (long long)sms * 16;
+  return (int)std::max(1LL, std::min(want, cap));
+}
+
+}  // namespace
+}  // namespace vimg
+
+using namespace vimg;
+
+struct vimg_unet {
+  int H = 0, W = 0, max_seg = 0, npy = 0, npx = 0, npatch = 0, P = 0;
+  int dev = 0, sms = 0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  int sticky = 0;
+  bool loaded = false;
+  // per layer: packed weights and biases
+  std::vector<LayerDef> defs;
+  std::vector<__nv_bfloat16*> wpack;
+  std::vector<float*> bpack;
+  float* wout = nullptr;  // [17] output layer, FP32
+  // activations (NHWC BF16)
+  __nv_bfloat16* in0 = nullptr;
+  __nv_bfloat16* a[kULevels + 1] = {};    // first encoder conv of a level
+  __nv_bfloat16* da[kULevels] = {};       // first decoder conv of a level
+  __nv_bfloat16* cat[kULevels] = {};      // [skip, up] per level 0..3
+  __nv_bfloat16* pool[kULevels + 1] = {}; // pooled input of levels 1..4
+  __nv_bfloat16* d[kULevels + 1] = {};    // decoder output per level 0..3, bottleneck at 4
+  float* pprob = nullptr;                 // [P][64][64]
+  double* stats = nullptr;                // [max_seg][2][2]
+  int* dev_err = nullptr;
+  struct Conv {
+    ConvParams p;
+    CUtensorMap map;
+    int grid = 0;
+    size_t smem = 0;
+  };
+  std::vector<Conv> convs;  // execution order
+  // profiling: event pairs around the tensor-core launches and the whole run
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  double conv_ms = 0.0, total_ms = 0.0;
+  long long conv_launches = 0;
+  int last_np = 0;  // patches of the last internal pass (for vimg_unet_activation)
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int ufail(vimg_unet* u, int code, const std::string& msg) {
+  if (u) {
+    u->err = msg;
+    if (code == VIMG_ERR_CUDA || code == VIMG_ERR_TIMEOUT) u->sticky = code;
+  }
+  return code;
+}
+
+#define UCK(call, what)                                                                 \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ufail(u, VIMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+cudaError_t ualloc(vimg_unet* u, T*& p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * std::max<size_t>(n, 1));
+  if (e == cudaSuccess) u->allocs.push_back(p);
+  return e;
+}
+
+// One tensor-core convolution: input [P][Hl][Wl][cin] (whole buffer), output
+// at a channel offset of a buffer with out_stride channels.
+int setup_conv(vimg_unet* u, const __nv_bfloat16* in, int Hl, int Wl, int cin, int taps, int n_total,
+               int up, int cout, int relu, __nv_bfloat16* out, int out_stride, int out_off,
+               const __nv_bfloat16* wpack, const float* bias) {
+  vimg_unet::Conv c{};
+  ConvParams& p = c.p;
+  const int P = u->P;
+  p.total_px = P * Hl * Wl;
+  p.Hl = Hl, p.Wl = Wl;
+  p.bh = std::min(Hl, 128 / Wl);
+  p.bb = std::max(1, 128 / (Hl * Wl));
+  p.kc = std::min(cin, 64);
+  p.nkc = cin / p.kc;
+  p.taps = taps;
+  p.ntile = std::min(n_total, 256);
+  p.n_ntiles = n_total / p.ntile;
+  p.n_mtiles = (p.total_px + 127) / 128;
+  p.a_bytes = 128u * p.kc * 2u;
+  p.b_bytes = (uint32_t)p.ntile * p.kc * 2u;
+  p.stages = (int)std::min<size_t>(kUMaxStages, kUSmemMax / (p.a_bytes + p.b_bytes));
+  if (p.stages < 2 || p.bh * p.bb * Wl != 128 || cin % 16 || p.ntile % 16 || n_total % p.ntile)
+    return ufail(u, VIMG_ERR_ARG, "unet: unsupported layer shape");
+  p.wpack = wpack, p.bias = bias, p.out = out, p.out_stride = out_stride, p.out_off = out_off;
+  p.up = up, p.cout = cout, p.relu = relu, p.err = u->dev_err;
+  c.smem = (size_t)p.stages * (p.a_bytes + p.b_bytes);
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return ufail(u, VIMG_ERR_CUDA, "unet: cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)Wl, (cuuint64_t)Hl, (cuuint64_t)P};
+  cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)Wl * cin * 2,
+                           (cuuint64_t)Hl * Wl * cin * 2};
+  cuuint32_t box[4] = {8, (cuuint32_t)Wl, (cuuint32_t)p.bh, (cuuint32_t)p.bb};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(&c.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(in),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return ufail(u, VIMG_ERR_CUDA, "unet: tensor map encode failed");
+  // resident CTAs per SM: shared memory and tensor memory (512 columns)
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc, kUThreads, c.smem) !=
+      cudaSuccess)
+    occ = 1;
+  const int tcols = std::max(32, 2 * p.ntile);
+  occ = std::max(1, std::min(occ, 512 / tcols));
+  const int tiles = p.n_mtiles * p.n_ntiles;
+  c.grid = std::min(tiles, u->sms * occ);
+  u->convs.push_back(c);
+  return VIMG_OK;
+}
+
+}  // namespace
+
+extern "C" int vimg_unet_param_count(void) {
+  size_t n = 0;
+  for (const LayerDef& L : unet_defs()) n += weight_count(L) + L.cout;
+  return (int)n;
+}
+
+extern "C" int vimg_unet_layers(int* kind, int* cin, int* cout, int cap) {
+  const std::vector<LayerDef> d = unet_defs();
+  for (int i = 0; i < (int)d.size() && i < cap; ++i) {
+    if (kind) kind[i] = d[i].kind;
+    if (cin) cin[i] = d[i].cin;
+    if (cout) cout[i] = d[i].cout;
+  }
+  return (int)d.size();
+}
+
+extern "C" void vimg_unet_destroy(vimg_unet* u) {
+  if (!u) return;
+  for (void* q : u->allocs) cudaFree(q);
+  for (cudaEvent_t e : u->ev) cudaEventDestroy(e);
+  delete u;
+}
+
+static std::string g_unet_create_error;
+
+extern "C" vimg_unet* vimg_unet_create(int H, int W, int max_segments, void* stream) {
+  if (H < kUPatch || W < kUPatch || H > 8192 || W > 8192 || max_segments < 1 ||
+      max_segments > 4096) {
+    g_unet_create_error = "vimg_unet_create: need 64 <= H, W <= 8192 and 1..4096 segments";
+    return nullptr;
+  }
+  vimg_unet* u = new vimg_unet();
+  u->H = H, u->W = W, u->max_seg = max_segments;
+  u->npy = (H - kUPatch + kUStride - 1) / kUStride + 1;
+  u->npx = (W - kUPatch + kUStride - 1) / kUStride + 1;
+  u->npatch = u->npy * u->npx;
+  u->P = u->npatch * max_segments;
+  u->st = static_cast<cudaStream_t>(stream);
+  u->defs = unet_defs();
+  auto bail = [&](const std::string& m) -> vimg_unet* {
+    g_unet_create_error = m;
+    vimg_unet_destroy(u);
+    return nullptr;
+  };
+  if (cudaGetDevice(&u->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&u->sms, cudaDevAttrMultiProcessorCount, u->dev) != cudaSuccess)
+    return bail("vimg_unet_create: no CUDA device");
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kUSmemMax) != cudaSuccess)
+      return bail("vimg_unet_create: kernel attribute");
+    attr = true;
+  }
+  const size_t P = u->P;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto*& ptr, size_t n) {
+    if (e == cudaSuccess) e = ualloc(u, ptr, n);
+  };
+  A(u->dev_err, 1);
+  A(u->stats, 4 * (size_t)max_segments);
+  A(u->pprob, P * kUPatch * kUPatch);
+  A(u->in0, P * kUPatch * kUPatch * kUC0);
+  for (int l = 0; l <= kULevels; ++l) {
+    const size_t px = P * (size_t)(kUPatch >> l) * (kUPatch >> l);
+    const int C = kUC0 << l;
+    A(u->a[l], px * C);
+    A(u->d[l], px * C);
+    if (l < kULevels) A(u->cat[l], px * 2 * C);
+    if (l < kULevels) A(u->da[l], px * C);
+    if (l > 0) A(u->pool[l], px * (C / 2));
+  }
+  A(u->wout, kUC0 + 1);
+  // packed weights per tensor-core layer
+  u->wpack.assign(u->defs.size(), nullptr);
+  u->bpack.assign(u->defs.size(), nullptr);
+  for (size_t i = 0; i < u->defs.size(); ++i) {
+    const LayerDef& L = u->defs[i];
+    if (L.kind == 2) continue;
+    const int cin = std::max(L.cin, kUC0);
+    const int taps = L.kind == 0 ? 9 : 1;
+    const int n_total = L.kind == 0 ? L.cout : 4 * L.cout;
+    A(u->wpack[i], (size_t)taps * cin * n_total);
+    A(u->bpack[i], (size_t)n_total);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(u->dev_err, 0, sizeof(int), u->st);
+  if (e != cudaSuccess) return bail(std::string("vimg_unet_create: ") + cudaGetErrorString(e));
+  // layer plan (execution order)
+  int li = 0;
+  auto conv = [&](const __nv_bfloat16* in, int Hl, int cin, __nv_bfloat16* out, int ostride,
+                  int ooff) {
+    const LayerDef& L = u->defs[li];
+    const int rc = setup_conv(u, in, Hl, Hl, cin, 9, L.cout, 0, L.cout, 1, out, ostride, ooff,
+                              u->wpack[li], u->bpack[li]);
+    ++li;
+    return rc;
+  };
+  auto upc = [&](const __nv_bfloat16* in, int Hl, int cin, __nv_bfloat16* out, int ostride,
+                 int ooff) {
+    const LayerDef& L = u->defs[li];
+    const int rc = setup_conv(u, in, Hl, Hl, cin, 1, 4 * L.cout, 1, L.cout, 0, out, ostride, ooff,
+                              u->wpack[li], u->bpack[li]);
+    ++li;
+    return rc;
+  };
+  int rc = VIMG_OK;
+  // encoder: level l input = in0 (l = 0) or pool[l]; skip -> cat[l][0, C)
+  for (int l = 0; l <= kULevels && rc == VIMG_OK; ++l) {
+    const int Hl = kUPatch >> l, C = kUC0 << l;
+    const __nv_bfloat16* in = l == 0 ? u->in0 : u->pool[l];
+    const int cin = l == 0 ? kUC0 : C / 2;
+    rc = conv(in, Hl, cin, u->a[l], C, 0);
+    if (rc == VIMG_OK)
+      rc = l < kULevels ? conv(u->a[l], Hl, C, u->cat[l], 2 * C, 0) : conv(u->a[l], Hl, C, u->d[l], C, 0);
+  }
+  // decoder: up from d[l + 1] into cat[l][C, 2C), then two convolutions -> d[l]
+  for (int l = kULevels - 1; l >= 0 && rc == VIMG_OK; --l) {
+    const int Hl = kUPatch >> l, C = kUC0 << l;
+    rc = upc(u->d[l + 1], Hl / 2, 2 * C, u->cat[l], 2 * C, C);
+    if (rc == VIMG_OK) rc = conv(u->cat[l], Hl, 2 * C, u->da[l], C, 0);
+    if (rc == VIMG_OK) rc = conv(u->da[l], Hl, C, u->d[l], C, 0);
+  }
+  if (rc != VIMG_OK) return bail(u->err);
+  return u;
+}
+
+extern "C" const char* vimg_unet_last_error(const vimg_unet* u) {
+  return u ? u->err.c_str() : g_unet_create_error.c_str();
+}
+
+extern "C" int vimg_unet_load(vimg_unet* u, const float* d_params) {
+  if (!u || !d_params) return ufail(u, VIMG_ERR_ARG, "vimg_unet_load: null argument");
+  if (u->sticky) return u->sticky;
+  size_t off = 0;
+  for (size_t i = 0; i < u->defs.size(); ++i) {
+    const LayerDef& L = u->defs[i];
+    const size_t nw = weight_count(L);
+    const float* w = d_params + off;
+    const float* b = w + nw;
+    off += nw + L.cout;
+    if (L.kind == 2) {
+      UCK(cudaMemcpyAsync(u->wout, w, sizeof(float) * (kUC0 + 1), cudaMemcpyDeviceToDevice, u->st),
+          "unet output weights");
+      continue;
+    }
+    const int cin = std::max(L.cin, kUC0), taps = L.kind == 0 ? 9 : 1;
+    const int n_total = L.kind == 0 ? L.cout : 4 * L.cout;
+    const int kc = std::min(cin, 64), nkc = cin / kc;
+    const int ntile = std::min(n_total, 256), n_ntiles = n_total / ntile;
+    const long long total = (long long)n_ntiles * taps * nkc * kc * ntile;
+    k_pack<<<grid_for(total, 256, u->sms), 256, 0, u->st>>>(w, b, L.kind == 1, L.cin, L.cout, taps,
+                                                          kc, nkc, ntile, n_ntiles, u->wpack[i],
+                                                          u->bpack[i]);
+    UCK(cudaGetLastError(), "unet weight pack");
+  }
+  u->loaded = true;
+  return VIMG_OK;
+}
+
+namespace {
+
+int record(vimg_unet* u, cudaStream_t st) {
+  if (!u->prof) return -1;
+  if (u->ev_used >= (int)u->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    u->ev.push_back(e);
+  }
+  cudaEventRecord(u->ev[u->ev_used], st);
+  return u->ev_used++;
+}
+
+// Sums the recorded intervals: pairs (conv begin, end) ..., then (run begin, end).
+int prof_collect(vimg_unet* u, const std::vector<int>& conv_ev, int run0, int run1) {
+  if (!u->prof) return VIMG_OK;
+  UCK(cudaEventSynchronize(u->ev[run1]), "unet profile sync");
+  for (size_t i = 0; i + 1 < conv_ev.size(); i += 2) {
+    float ms = 0.f;
+    if (conv_ev[i] >= 0 && conv_ev[i + 1] >= 0 &&
+        cudaEventElapsedTime(&ms, u->ev[conv_ev[i]], u->ev[conv_ev[i + 1]]) == cudaSuccess)
+      u->conv_ms += ms;
+    u->conv_launches++;
+  }
+  float ms = 0.f;
+  if (run0 >= 0 && cudaEventElapsedTime(&ms, u->ev[run0], u->ev[run1]) == cudaSuccess)
+    u->total_ms += ms;
+  u->ev_used = 0;
+  return VIMG_OK;
+}
+
+}  // namespace
+
+int vimg_unet_run_on(vimg_unet* u, const float* d_summary, int k, float* d_prob, cudaStream_t st) {
+  if (!u) return ufail(u, VIMG_ERR_ARG, "null U-Net");
+  if (u->sticky) return u->sticky;
+  if (!u->loaded) return ufail(u, VIMG_ERR_ARG, "vimg_unet_load must come before vimg_unet_run");
+  if (k < 0 || (k > 0 && (!d_summary || !d_prob))) return ufail(u, VIMG_ERR_ARG, "vimg_unet_run: bad arguments");
+  const size_t HW = (size_t)u->H * u->W;
+  std::vector<int> conv_ev;
+  const int run0 = k > 0 ? record(u, st) : -1;
+  for (int s0 = 0; s0 < k; s0 += u->max_seg) {
+    const int ks = std::min(k - s0, u->max_seg);
+    const float* summ = d_summary + (size_t)s0 * 2 * HW;
+    const int np = ks * u->npatch;
+    k_ustats<<<2 * ks, 256, 0, st>>>(summ, (int)HW, u->stats);
+    UCK(cudaGetLastError(), "unet statistics");
+    const long long n_in = (long long)np * kUPatch * kUPatch;
+    k_uinput<<<grid_for(n_in, 256, u->sms), 256, 0, st>>>(summ, u->stats, u->H, u->W, u->npy,
+                                                          u->npx, np, u->in0);
+    UCK(cudaGetLastError(), "unet input");
+    // the tensor-core layers run over all P patch slots; slots past np hold
+    // stale inputs whose outputs are never read
+    size_t ci = 0;
+    auto run_conv = [&]() -> int {
+      vimg_unet::Conv& c = u->convs[ci++];
+      ConvParams p = c.p;
+      // shrink to the patches in use
+      const int px = np * p.Hl * p.Wl;
+      p.total_px = px;
+      p.n_mtiles = (px + 127) / 128;
+      const int grid = std::min(c.grid, p.n_mtiles * p.n_ntiles);
+      conv_ev.push_back(record(u, st));
+      k_conv_tc<<<grid, kUThreads, c.smem, st>>>(c.map, p);
+      conv_ev.push_back(record(u, st));
+      UCK(cudaGetLastError(), "unet convolution");
+      return VIMG_OK;
+    };
+    int rc = VIMG_OK;
+    for (int l = 0; l <= kULevels && rc == VIMG_OK; ++l) {
+      if (l > 0) {
+        const int Ho = kUPatch >> l, C = kUC0 << (l - 1);
+        const __nv_bfloat16* src = u->cat[l - 1];
+        const long long n = (long long)np * Ho * Ho * (C / 8);
+        k_upool<<<grid_for(n, 256, u->sms), 256, 0, st>>>(src, np, Ho, Ho, C, 2 * C, u->pool[l]);
+        UCK(cudaGetLastError(), "unet pooling");
+      }
+      rc = run_conv();
+      if (rc == VIMG_OK) rc = run_conv();
+    }
+    for (int l = kULevels - 1; l >= 0 && rc == VIMG_OK; --l)
+      for (int j = 0; j < 3 && rc == VIMG_OK; ++j) rc = run_conv();
+    if (rc != VIMG_OK) return rc;
+    const long long n_px = (long long)np * kUPatch * kUPatch;
+    k_uout<<<grid_for(n_px, 256, u->sms), 256, 0, st>>>(u->d[0], u->wout, n_px, u->pprob);
+    UCK(cudaGetLastError(), "unet output layer");
+    const long long n_out = (long long)ks * HW;
+    k_umerge<<<grid_for(n_out, 256, u->sms), 256, 0, st>>>(u->pprob, u->H, u->W, u->npy, u->npx, ks,
+                                                          d_prob + (size_t)s0 * HW);
+    UCK(cudaGetLastError(), "unet merge");
+    u->last_np = np;
+  }
+  if (k > 0) {
+    const int run1 = record(u, st);
+    if (run1 >= 0) return prof_collect(u, conv_ev, run0, run1);
+  }
+  return VIMG_OK;
+}
+
+extern "C" int vimg_unet_run(vimg_unet* u, const float* d_summary, int k, float* d_prob) {
+  return vimg_unet_run_on(u, d_summary, k, d_prob, u ? u->st : nullptr);
+}
+
+extern "C" int vimg_unet_synchronize(vimg_unet* u) {
+  if (!u) return ufail(u, VIMG_ERR_ARG, "null U-Net");
+  if (u->sticky) return u->sticky;
+  UCK(cudaStreamSynchronize(u->st), "unet synchronize");
+  int flag = 0;
+  UCK(cudaMemcpy(&flag, u->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "unet error read");
+  if (flag) return ufail(u, VIMG_ERR_TIMEOUT, "unet: a tensor-core kernel's bounded wait gave up");
+  return VIMG_OK;
+}
+
+extern "C" int vimg_unet_profile(vimg_unet* u, int on) {
+  if (!u) return ufail(u, VIMG_ERR_ARG, "null U-Net");
+  u->prof = on != 0;
+  u->ev_used = 0;
+  return VIMG_OK;
+}
+
+extern "C" int vimg_unet_profile_read(vimg_unet* u, double* conv_ms, double* total_ms,
+                                      long long* conv_launches, int reset) {
+  if (!u) return ufail(u, VIMG_ERR_ARG, "null U-Net");
+  if (conv_ms) *conv_ms = u->conv_ms;
+  if (total_ms) *total_ms = u->total_ms;
+  if (conv_launches) *conv_launches = u->conv_launches;
+  if (reset) {
+    u->conv_ms = u->total_ms = 0.0;
+    u->conv_launches = 0;
+  }
+  return VIMG_OK;
+}
+
+int unet_dims(const vimg_unet* u, int* H, int* W) {
+  if (!u) return -1;
+  *H = u->H, *W = u->W;
+  return 0;
+}
+
+extern "C" int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_patches, int* side,
+                                    int* channels) {
+  if (!u) return ufail(u, VIMG_ERR_ARG, "null U-Net");
+  if (u->sticky) return u->sticky;
+  const int n_tc = (int)u->convs.size();
+  if (i < 0 || i > n_tc + 1) return ufail(u, VIMG_ERR_ARG, "vimg_unet_activation: bad index");
+  const int np = u->last_np;
+  int sd, C;
+  const void* src;
+  size_t pitch, width, elem;
+  if (i == 0) {
+    sd = kUPatch, C = kUC0, src = u->in0, elem = 2, pitch = width = (size_t)C * 2;
+  } else if (i <= n_tc) {
+    const ConvParams& p = u->convs[i - 1].p;
+    sd = p.up ? 2 * p.Hl : p.Hl;
+    C = p.up ? p.cout : p.ntile * p.n_ntiles;
+    elem = 2;
+    src = p.out + p.out_off;
+    pitch = (size_t)p.out_stride * 2, width = (size_t)C * 2;
+  } else {
+    sd = kUPatch, C = 1, src = u->pprob, elem = 4, pitch = width = 4;
+  }
+  if (n_patches) *n_patches = np;
+  if (side) *side = sd;
+  if (channels) *channels = C;
+  if (!d_out || np == 0) return VIMG_OK;
+  (void)elem;
+  UCK(cudaMemcpy2DAsync(d_out, width, src, pitch, width, (size_t)np * sd * sd,
+                        cudaMemcpyDeviceToDevice, u->st),
+      "unet activation copy");
+  return VIMG_OK;
+}

@@ -190,3 +190,7 @@ cudaError_t roi_finalize(const unsigned long long* acc, const int* counts, int n
 constexpr double kRoiFix = 1048576.0;  // 2^20: fixed-point scale of the trace sums
 
 }  // namespace vimg
+
+// U-Net stage on a given stream (the handle's, when attached).
+int vimg_unet_run_on(vimg_unet* u, const float* d_summary, int k, float* d_prob, cudaStream_t st);
+int unet_dims(const vimg_unet* u, int* H, int* W);

@@ -44,6 +44,7 @@ class IO(ctypes.Structure):
         ("surface", ctypes.c_void_p),
         ("shifts_in", ctypes.c_void_p),
         ("traces", ctypes.c_void_p),
+        ("prob", ctypes.c_void_p),
     ]
 
 
@@ -64,6 +65,9 @@ EXPORTS = [
     "vimg_cnn_param_count", "vimg_cnn_workspace_floats", "vimg_cnn_prepare", "vimg_cnn_pack_bf16",
     "vimg_cnn_forward", "vimg_cnn_loss", "vimg_cnn_backward", "vimg_cnn_adam", "vimg_load_proposal",
     "vimg_proposal_stats", "vimg_synchronize", "vimg_process_batch", "vimg_set_rois",
+    "vimg_unet_param_count", "vimg_unet_layers", "vimg_unet_create", "vimg_unet_destroy",
+    "vimg_unet_last_error", "vimg_unet_load", "vimg_unet_run", "vimg_unet_synchronize",
+    "vimg_unet_profile", "vimg_unet_profile_read", "vimg_attach_unet", "vimg_unet_activation",
 ]
 NSTAGES = 6
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
@@ -84,6 +88,30 @@ def _load():
     L.vimg_set_template.restype = i
     L.vimg_set_rois.argtypes = [vp, vp, i]
     L.vimg_set_rois.restype = i
+    L.vimg_unet_param_count.argtypes = []
+    L.vimg_unet_param_count.restype = i
+    L.vimg_unet_layers.argtypes = [vp, vp, vp, i]
+    L.vimg_unet_layers.restype = i
+    L.vimg_unet_create.argtypes = [i, i, i, vp]
+    L.vimg_unet_create.restype = vp
+    L.vimg_unet_destroy.argtypes = [vp]
+    L.vimg_unet_destroy.restype = None
+    L.vimg_unet_last_error.argtypes = [vp]
+    L.vimg_unet_last_error.restype = ctypes.c_char_p
+    L.vimg_unet_load.argtypes = [vp, vp]
+    L.vimg_unet_load.restype = i
+    L.vimg_unet_run.argtypes = [vp, vp, i, vp]
+    L.vimg_unet_run.restype = i
+    L.vimg_unet_synchronize.argtypes = [vp]
+    L.vimg_unet_synchronize.restype = i
+    L.vimg_unet_profile.argtypes = [vp, i]
+    L.vimg_unet_profile.restype = i
+    L.vimg_unet_profile_read.argtypes = [vp, vp, vp, vp, i]
+    L.vimg_unet_profile_read.restype = i
+    L.vimg_unet_activation.argtypes = [vp, i, vp, vp, vp, vp]
+    L.vimg_unet_activation.restype = i
+    L.vimg_attach_unet.argtypes = [vp, vp]
+    L.vimg_attach_unet.restype = i
     L.vimg_process.argtypes = [vp, vp, i, vp, vp, vp]
     L.vimg_process.restype = i
     L.vimg_process_io.argtypes = [vp, vp, i, P(IO)]
@@ -218,15 +246,21 @@ class Handle:
         self._check(lib.vimg_set_rois(self._h, _ptr(m), m.shape[0]))
         self.n_rois = m.shape[0]
 
+    def attach_unet(self, unet):
+        """Attach a Unet of the same size (None detaches): process(prob=...)
+        then gives each completed segment's spiking-probability map."""
+        self._unet = unet
+        self._check(lib.vimg_attach_unet(self._h, None if unet is None else unet._u))
+
     def process(self, frames, shifts=None, corrected=None, summary=None, peak_info=None,
-                surface=None, shifts_in=None, traces=None) -> int:
+                surface=None, shifts_in=None, traces=None, prob=None) -> int:
         """frames: cuda uint16 [n,H,W].  Outputs are optional preallocated cuda
-        tensors (see vimg_io; traces: float32 [n, n_rois]).  Returns k, the
-        segments written."""
+        tensors (see vimg_io; traces: float32 [n, n_rois]; prob: float32
+        [k, H, W], needs summary).  Returns k, the segments written."""
         assert frames.is_cuda and frames.dtype == torch.uint16 and frames.is_contiguous()
         n = frames.shape[0]
         io = IO(_ptr(shifts), _ptr(corrected), _ptr(summary), _ptr(peak_info), _ptr(surface),
-                _ptr(shifts_in), _ptr(traces))
+                _ptr(shifts_in), _ptr(traces), _ptr(prob))
         return self._check(lib.vimg_process_io(self._h, _ptr(frames), n, ctypes.byref(io)))
 
     def process_host(self, frames_host, shifts_host=None, summary_host=None,
@@ -296,3 +330,86 @@ def process_batch(handles, frames, shifts=None, corrected=None, summary=None, ch
 
 def version() -> str:
     return lib.vimg_version().decode()
+
+
+def unet_param_count() -> int:
+    return lib.vimg_unet_param_count()
+
+
+def unet_layers():
+    """[(kind, cin, cout)] in parameter order, kind 'conv', 'up' or 'out'."""
+    n = lib.vimg_unet_layers(None, None, None, 0)
+    k, ci, co = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)()
+    lib.vimg_unet_layers(k, ci, co, n)
+    names = {0: "conv", 1: "up", 2: "out"}
+    return [(names[k[i]], ci[i], co[i]) for i in range(n)]
+
+
+class Unet:
+    """Spiking-pixel U-Net on summary pairs (see vimg_unet_create)."""
+
+    def __init__(self, H, W, max_segments=4, stream=None):
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.H, self.W = H, W
+        self._u = lib.vimg_unet_create(H, W, max_segments, ctypes.c_void_p(stream.cuda_stream))
+        if not self._u:
+            raise VimgError(ERR_ARG, lib.vimg_unet_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "_u", None):
+            lib.vimg_unet_destroy(self._u)
+            self._u = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc < 0:
+            raise VimgError(rc, lib.vimg_unet_last_error(self._u).decode())
+        return rc
+
+    def load(self, params: torch.Tensor):
+        assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
+        assert params.numel() == unet_param_count()
+        self._params = params
+        self._check(lib.vimg_unet_load(self._u, _ptr(params)))
+
+    def run(self, summary: torch.Tensor, prob: torch.Tensor):
+        """summary: cuda float32 [k, 2, H, W]; prob: cuda float32 [k, H, W]."""
+        assert summary.is_cuda and summary.dtype == torch.float32 and summary.is_contiguous()
+        k = summary.shape[0]
+        assert summary.shape == (k, 2, self.H, self.W) and prob.shape == (k, self.H, self.W)
+        self._check(lib.vimg_unet_run(self._u, _ptr(summary), k, _ptr(prob)))
+
+    def synchronize(self):
+        self._check(lib.vimg_unet_synchronize(self._u))
+
+    def activation(self, i: int) -> torch.Tensor:
+        """Activation i of the last internal pass (see vimg_unet_activation):
+        bfloat16 [n, side, side, C] for i <= 22, float32 [n, 64, 64] for 23."""
+        n, sd, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib.vimg_unet_activation(self._u, i, None, ctypes.byref(n), ctypes.byref(sd),
+                                             ctypes.byref(c)))
+        if c.value == 1 and i > 0:
+            out = torch.empty((n.value, sd.value, sd.value), device="cuda", dtype=torch.float32)
+        else:
+            out = torch.empty((n.value, sd.value, sd.value, c.value), device="cuda",
+                              dtype=torch.bfloat16)
+        self._check(lib.vimg_unet_activation(self._u, i, _ptr(out), None, None, None))
+        self.synchronize()
+        return out
+
+    def profile(self, on: bool = True):
+        self._check(lib.vimg_unet_profile(self._u, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True):
+        """(tensor-core ms, whole-run ms, tensor-core launches) since the last reset."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        self._check(lib.vimg_unet_profile_read(self._u, ctypes.byref(a), ctypes.byref(b),
+                                               ctypes.byref(c), 1 if reset else 0))
+        return a.value, b.value, c.value

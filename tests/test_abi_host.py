@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(vimg):
 def test_struct_layouts_match_header(vimg):
     # vimg_params: 8 ints/floats, a pointer, a long long, an int (+ padding)
     assert ctypes.sizeof(vimg.Params) == 56
-    assert ctypes.sizeof(vimg.IO) == 7 * 8
+    assert ctypes.sizeof(vimg.IO) == 8 * 8
 
 
 def test_defaults(vimg):
@@ -67,3 +67,16 @@ def test_null_handle_calls(vimg):
     assert L.vimg_reset(None) == vimg.ERR_ARG
     assert L.vimg_frames_seen(None) == -1
     assert b"sm_103a" in L.vimg_version()
+
+
+def test_unet_architecture_matches_the_oracle(vimg):
+    """The library's U-Net (parameter layout and layer list) is the oracle's reading."""
+    import oracle.unet as U
+    assert vimg.unet_layers() == U.architecture()
+    assert vimg.unet_param_count() == U.param_count()
+
+
+def test_unet_create_rejects_small_images(vimg):
+    assert not vimg.lib.vimg_unet_create(63, 128, 4, None)
+    assert b"64" in vimg.lib.vimg_unet_last_error(None)
+    assert vimg.lib.vimg_unet_load(None, None) == vimg.ERR_ARG
