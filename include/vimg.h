@@ -343,8 +343,7 @@ void vimg_unet_destroy(vimg_unet* u);
 const char* vimg_unet_last_error(const vimg_unet* u);
 
 /* Converts the parameters (device float32, vimg_unet_param_count floats) into
- * the tensor-core layout; the array may be freed once the stream has passed
- * this call. */
+ * the tensor-core layout.  Synchronous: the array may be freed on return. */
 int vimg_unet_load(vimg_unet* u, const float* d_params);
 
 /* d_summary: device float32 [k][2][H][W] (S_i, T_i); d_prob: device float32

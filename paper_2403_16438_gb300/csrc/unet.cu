@@ -86,17 +86,39 @@ size_t weight_count(const LayerDef& L) {
   return (size_t)L.cin * L.cout * taps;
 }
 
+// Activations are BF16 in 8-channel planes: [C / 8][guard + pixels + guard][8],
+// pixels patch-major, so that 8 channels of consecutive pixels -- one K-major
+// core matrix per 8 pixels -- are contiguous.  Levels 0..kUPadLevels-1 (64, 32,
+// 16 px) are stored with a one-pixel zero border (side s + 2) and zero guard
+// zones around each plane, none of which any kernel writes: a 3x3 convolution
+// reads pixel i + dy (s + 2) + dx of the same plane, so one contiguous halo of
+// 128 + 2 (s + 2) + 2 pixels per plane, fetched by one bulk copy, serves all
+// nine taps ("halo" tiles, shifted descriptors).  The 8 and 4 px levels are
+// stored dense; their tiles take one TMA box per tap and plane (im2col boxes
+// with zero fill at the image border), which costs less there than a border.
+constexpr int kUPadLevels = 3;
+constexpr int kUGuard = 272;  // guard pixels before and after each padded plane
+
 struct ConvParams {
-  int total_px;            // P * Hl * Wl (input pixels)
-  int Hl, Wl, bh, bb;      // input image, TMA box rows and images (bh * bb * Wl = 128)
-  int kc, nkc, taps;       // channels per K chunk, chunks per tap, taps (9 or 1)
+  int lin;                 // 1: padded input, halo tiles (bulk copies); 0: im2col boxes (TMA)
+  const __nv_bfloat16* in; // input planes (halo tiles)
+  size_t in_plane;         // elements per input plane (incl. guards)
+  int in_guard;            // guard pixels before the data of an input plane
+  int m_px;                // M rows in use: pixels of the input layout (incl. border)
+  int s_in, sp_in;         // input side, and its stored side (s_in + 2 when padded)
+  int bh, bb;              // boxes: rows and images per box (bh * bb * s_in = 128)
+  int hoff;                // halo: first pixel = m0 - hoff
+  uint32_t plane_bytes;    // halo: one 8-channel plane in shared memory (rows x 16 B)
+  int kc, nkc, taps;       // channels per K chunk, chunks per tile (x taps in box mode)
   int ntile, n_ntiles, n_mtiles;
   int stages;
-  uint32_t a_bytes, b_bytes;
-  const __nv_bfloat16* wpack;  // [n_ntiles][taps * nkc][kc / 8][ntile][8]
+  uint32_t a_bytes, b_bytes;   // per stage
+  const __nv_bfloat16* wpack;  // [n_ntiles][chunk][tap in chunk][kc / 8][ntile][8]
   const float* bias;           // [n_ntiles * ntile]
   __nv_bfloat16* out;
-  int out_stride, out_off;     // channels per output pixel, first channel written
+  size_t out_plane;            // elements per output plane (incl. guards)
+  int out_guard, out_goff;     // guard pixels; first output plane written
+  int so, spo;                 // output side, stored output side
   int up, cout, relu;
   int* err;
 };
@@ -118,7 +140,8 @@ __global__ void __launch_bounds__(kUThreads, 1)
   unsigned char* sA = smem;                                  // [S][a_bytes]
   unsigned char* sB = smem + (size_t)S * p.a_bytes;          // [S][b_bytes]
   const int n_tiles = p.n_mtiles * p.n_ntiles;
-  const int nq = p.taps * p.nkc;
+  const int nq = p.lin ? p.nkc : p.taps * p.nkc;             // stages per tile
+  const int tq = p.lin ? p.taps : 1;                         // taps per stage
   const uint32_t tcols = (uint32_t)(2 * p.ntile) < 32u ? 32u : (uint32_t)(2 * p.ntile);
 
   if (warp == 0) {
@@ -144,7 +167,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int img_px = p.Hl * p.Wl;
+  const int img_px = p.sp_in * p.sp_in;
 
   if (warp == kUEpiWarps) {
     // ---------------- producer ----------------
@@ -152,7 +175,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
       int it = 0;
       for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
         const int nt = tile % p.n_ntiles, mt = tile / p.n_ntiles;
-        const int m0 = mt * 128, b0 = m0 / img_px, h0 = (m0 - b0 * img_px) / p.Wl;
+        const int m0 = mt * 128, b0 = m0 / img_px, h0 = (m0 - b0 * img_px) / p.sp_in;
         for (int q = 0; q < nq; ++q, ++it) {
           const int s = it % S, cyc = it / S;
           if (cyc > 0 && !mbar_wait(&empty[s], (cyc - 1) & 1)) {
@@ -160,17 +183,30 @@ __global__ void __launch_bounds__(kUThreads, 1)
             abort_flag = 1;
             break;
           }
-          const int t = q / p.nkc, c = q - t * p.nkc;
-          const int dy = p.taps == 9 ? t / 3 - 1 : 0, dx = p.taps == 9 ? t % 3 - 1 : 0;
           mbar_expect_tx(&full[s], p.a_bytes + p.b_bytes);
           unsigned char* a_dst = sA + (size_t)s * p.a_bytes;
-          for (int g = 0; g < p.kc / 8; ++g)
-            asm volatile(
-                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
-                    su32(a_dst + g * 2048)),
-                "l"(&tmap), "r"(c * p.kc + 8 * g), "r"(dx), "r"(h0 + dy), "r"(b0),
-                "r"(su32(&full[s]))
-                : "memory");
+          if (p.lin) {
+            // one contiguous halo per plane (the guards keep it inside the buffer)
+            const __nv_bfloat16* src0 =
+                p.in + (size_t)(p.in_guard + m0 - p.hoff) * 8 + (size_t)q * (p.kc / 8) * p.in_plane;
+            for (int g = 0; g < p.kc / 8; ++g)
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                      su32(a_dst + g * p.plane_bytes)),
+                  "l"(src0 + (size_t)g * p.in_plane), "r"(p.plane_bytes), "r"(su32(&full[s]))
+                  : "memory");
+          } else {
+            const int t = q / p.nkc, c = q - t * p.nkc;
+            const int dy = p.taps == 9 ? t / 3 - 1 : 0, dx = p.taps == 9 ? t % 3 - 1 : 0;
+            // map dims {8 s (x, channel), s (y), P, planes}: x = dx * 8 elements
+            for (int g = 0; g < p.kc / 8; ++g)
+              asm volatile(
+                  "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                      su32(a_dst + g * 2048)),
+                  "l"(&tmap), "r"(dx * 8), "r"(h0 + dy), "r"(b0), "r"(c * (p.kc / 8) + g),
+                  "r"(su32(&full[s]))
+                  : "memory");
+          }
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   su32(sB + (size_t)s * p.b_bytes)),
@@ -188,6 +224,8 @@ __global__ void __launch_bounds__(kUThreads, 1)
       int it = 0, tl = 0;
       bool issued = false;
       const uint32_t idesc = idesc_for(p.ntile);
+      const uint32_t a_lbo = p.lin ? p.plane_bytes : 2048u;
+      const uint32_t b_tap = (uint32_t)p.ntile * p.kc * 2;  // bytes of one tap's weights
       for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++tl) {
         const int buf = tl & 1, use = tl >> 1;
         if (use > 0) {
@@ -207,16 +245,21 @@ __global__ void __launch_bounds__(kUThreads, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint64_t ad0 = desc(su32(sA + (size_t)s * p.a_bytes), 2048, 128);
+          const uint64_t ad0 = desc(su32(sA + (size_t)s * p.a_bytes), a_lbo, 128);
           const uint64_t bd0 = desc(su32(sB + (size_t)s * p.b_bytes), p.ntile * 16, 128);
-          for (int k = 0; k < p.kc / 16; ++k) {
-            const uint64_t ad = ad0 + (uint64_t)(k * (2 * 2048 >> 4));
-            const uint64_t bd = bd0 + (uint64_t)(k * (2 * p.ntile * 16 >> 4));
-            const uint32_t acc = (q > 0 || k > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          for (int t = 0; t < tq; ++t) {
+            // halo tiles: tap (dy, dx) starts hoff + dy (s + 2) + dx pixels into the plane
+            const int off_px =
+                p.lin && p.taps == 9 ? p.hoff + (t / 3 - 1) * p.sp_in + (t % 3 - 1) : 0;
+            for (int k = 0; k < p.kc / 16; ++k) {
+              const uint64_t ad = ad0 + (uint64_t)((2 * k * a_lbo + off_px * 16) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((t * b_tap + k * 2 * p.ntile * 16) >> 4);
+              const uint32_t acc = (q > 0 || t > 0 || k > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
           }
           issued = true;
           mma_commit(&empty[s]);
@@ -234,6 +277,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
     // ------ epilogue: warp w owns TMEM lanes (pixels) 32 w .. 32 w + 31 ------
     int tl = 0;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int pad_in = p.sp_in != p.s_in, pad_out = p.spo != p.so;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
       const int buf = tl & 1, use = tl >> 1;
       const int nt = tile % p.n_ntiles, mt = tile / p.n_ntiles;
@@ -244,8 +288,10 @@ __global__ void __launch_bounds__(kUThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const bool valid = m < p.total_px;
-      const int b = m / img_px, r = m - b * img_px, h = r / p.Wl, w = r - h * p.Wl;
+      // input pixel of this row; rows on the zero border (or past the end) store nothing
+      const int b = m / img_px, r = m - b * img_px;
+      const int y = r / p.sp_in - pad_in, x = r % p.sp_in - pad_in;
+      const bool valid = m < p.m_px && y >= 0 && y < p.s_in && x >= 0 && x < p.s_in;
       for (int c0 = 0; c0 < p.ntile; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + lane_base + (uint32_t)(buf * p.ntile + c0), v);
@@ -257,24 +303,25 @@ __global__ void __launch_bounds__(kUThreads, 1)
           v[j] += __ldg(bs + j);
           if (p.relu) v[j] = fmaxf(v[j], 0.f);
         }
-        size_t opix;
-        int ch;
+        int ch, oy = y, ox = x;
         if (p.up) {
-          const int qd = ng / p.cout, i = qd >> 1, jj = qd & 1;
+          const int qd = ng / p.cout;
           ch = ng - qd * p.cout;
-          opix = ((size_t)b * 2 * p.Hl + 2 * h + i) * (2 * p.Wl) + 2 * w + jj;
+          oy = 2 * y + (qd >> 1), ox = 2 * x + (qd & 1);
         } else {
           ch = ng;
-          opix = (size_t)m;
         }
+        const size_t opix = ((size_t)b * p.spo + oy + pad_out) * p.spo + ox + pad_out;
         uint4 lo, hi;
         lo.x = pack_bf16x2(v[0], v[1]), lo.y = pack_bf16x2(v[2], v[3]);
         lo.z = pack_bf16x2(v[4], v[5]), lo.w = pack_bf16x2(v[6], v[7]);
         hi.x = pack_bf16x2(v[8], v[9]), hi.y = pack_bf16x2(v[10], v[11]);
         hi.z = pack_bf16x2(v[12], v[13]), hi.w = pack_bf16x2(v[14], v[15]);
-        uint4* dst = reinterpret_cast<uint4*>(p.out + opix * p.out_stride + p.out_off + ch);
-        dst[0] = lo;
-        dst[1] = hi;
+        // two planes of 8 channels; consecutive lanes = consecutive pixels
+        __nv_bfloat16* dst =
+            p.out + (size_t)(p.out_goff + ch / 8) * p.out_plane + (size_t)(p.out_guard + opix) * 8;
+        *reinterpret_cast<uint4*>(dst) = lo;
+        *reinterpret_cast<uint4*>(dst + p.out_plane) = hi;
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -288,13 +335,14 @@ __global__ void __launch_bounds__(kUThreads, 1)
 }
 
 // ---- small kernels ---------------------------------------------------------------
-// Weights of one layer into the B-operand layout [nt][tap * nkc + c][g][n][8]
-// (ci = c kc + 8 g + j, column ng = nt ntile + n), BF16; biases per column.
+// Weights of one layer into the B-operand layout [nt][chunk][tap in chunk][g][n][8]
+// (box tiles: chunk = tap x channel chunk, one tap each; halo tiles: chunk =
+// channel chunk, all taps), BF16; ci = c kc + 8 g + j, column ng = nt ntile + n.
 __global__ void k_pack(const float* __restrict__ w, const float* __restrict__ bias, int up,
-                       int cin_real, int cout, int taps, int kc, int nkc, int ntile, int n_ntiles,
-                       __nv_bfloat16* __restrict__ out, float* __restrict__ bout) {
-  const int nq = taps * nkc;
-  const long long total = (long long)n_ntiles * nq * kc * ntile;
+                       int lin, int cin_real, int cout, int taps, int kc, int nkc, int ntile,
+                       int n_ntiles, __nv_bfloat16* __restrict__ out, float* __restrict__ bout) {
+  const int nq = lin ? nkc : taps * nkc, tq = lin ? taps : 1;
+  const long long total = (long long)n_ntiles * nq * tq * kc * ntile;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long r = i;
@@ -304,9 +352,12 @@ __global__ void k_pack(const float* __restrict__ w, const float* __restrict__ bi
     r /= ntile;
     const int g = (int)(r % (kc / 8));
     r /= kc / 8;
+    const int tt = (int)(r % tq);
+    r /= tq;
     const int q = (int)(r % nq);
     const int nt = (int)(r / nq);
-    const int t = q / nkc, ci = (q - t * nkc) * kc + 8 * g + j, ng = nt * ntile + n;
+    const int t = lin ? tt : q / nkc, c = lin ? q : q - (q / nkc) * nkc;
+    const int ci = c * kc + 8 * g + j, ng = nt * ntile + n;
     float v = 0.f;
     if (ci < cin_real) {
       if (up) {
@@ -321,45 +372,58 @@ __global__ void k_pack(const float* __restrict__ w, const float* __restrict__ bi
   }
 }
 
-// Mean and 1 / (population std + eps) of each summary image, FP64, two passes,
-// fixed reduction order (one block per image).
-__global__ void k_ustats(const float* __restrict__ summary, int HW, double* __restrict__ stats) {
-  __shared__ double red[256];
-  const float* img = summary + (size_t)blockIdx.x * HW;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < HW; i += blockDim.x) s += (double)img[i];
-  red[threadIdx.x] = s;
+constexpr int kUStatBlocks = 64;  // partial-sum blocks per image
+
+// Partial FP64 sums of x and x^2 per image (fixed order per block).
+__global__ void k_ustats_part(const float* __restrict__ summary, int HW, double* __restrict__ part) {
+  __shared__ double r1[256], r2[256];
+  const float* img = summary + (size_t)blockIdx.y * HW;
+  double s = 0.0, q = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += gridDim.x * blockDim.x) {
+    const double v = (double)img[i];
+    s += v;
+    q = fma(v, v, q);
+  }
+  r1[threadIdx.x] = s;
+  r2[threadIdx.x] = q;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double mean = red[0] / HW;
-  __syncthreads();
-  double q = 0.0;
-  for (int i = threadIdx.x; i < HW; i += blockDim.x) {
-    const double d = (double)img[i] - mean;
-    q += d * d;
-  }
-  red[threadIdx.x] = q;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] += r2[threadIdx.x + o];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    stats[2 * blockIdx.x] = mean;
-    stats[2 * blockIdx.x + 1] = sqrt(red[0] / HW) + kUEps;
+    part[2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x)] = r1[0];
+    part[2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x) + 1] = r2[0];
   }
+}
+
+// Mean and 1 / (population std + eps) per image from the partial sums.
+__global__ void k_ustats_fin(const double* __restrict__ part, int n_img, int HW,
+                             double* __restrict__ stats) {
+  const int im = blockIdx.x * blockDim.x + threadIdx.x;
+  if (im >= n_img) return;
+  double s = 0.0, q = 0.0;
+  for (int b = 0; b < kUStatBlocks; ++b) {
+    s += part[2 * ((size_t)im * kUStatBlocks + b)];
+    q += part[2 * ((size_t)im * kUStatBlocks + b) + 1];
+  }
+  const double mean = s / HW, var = fmax(q / HW - mean * mean, 0.0);
+  stats[2 * im] = mean;
+  stats[2 * im + 1] = 1.0 / (sqrt(var) + kUEps);
 }
 
 __device__ __forceinline__ int upos(int j, int n) { return min(kUStride * j, n - kUPatch); }
 
-// Patches of the standardised pair: in0[P][64][64][16], channels 0 and 1 = S, T.
+// Patches of the standardised pair into plane 0 of the padded level-0 input
+// (66 x 66 per patch, border and plane 1 left zero): channels 0, 1 = S, T.
 __global__ void k_uinput(const float* __restrict__ summary, const double* __restrict__ stats,
-                         int H, int W, int npy, int npx, int n_patch_total,
+                         int H, int W, int npy, int npx, int n_patch_total, int guard,
                          __nv_bfloat16* __restrict__ in0) {
   const long long total = (long long)n_patch_total * kUPatch * kUPatch;
+  constexpr int sp = kUPatch + 2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int v = (int)(i % kUPatch), u = (int)((i / kUPatch) % kUPatch);
@@ -369,53 +433,60 @@ __global__ void k_uinput(const float* __restrict__ summary, const double* __rest
     const size_t HW = (size_t)H * W;
     const float* S = summary + (size_t)seg * 2 * HW;
     const double* st = stats + 4 * seg;
-    const double zs = ((double)S[(size_t)y * W + x] - st[0]) / st[1];
-    const double zt = ((double)S[HW + (size_t)y * W + x] - st[2]) / st[3];
+    const double zs = ((double)S[(size_t)y * W + x] - st[0]) * st[1];
+    const double zt = ((double)S[HW + (size_t)y * W + x] - st[2]) * st[3];
     uint4 a;
     a.x = pack_bf16x2((float)zs, (float)zt);
     a.y = a.z = a.w = 0u;
-    uint4* dst = reinterpret_cast<uint4*>(in0 + (size_t)i * kUC0);
-    dst[0] = a;
-    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+    const size_t o = ((size_t)pt * sp + u + 1) * sp + v + 1;
+    *reinterpret_cast<uint4*>(in0 + (guard + o) * 8) = a;
   }
 }
 
-// 2x2 max pooling, NHWC: input channels [0, C) of a buffer with cs channels.
-__global__ void k_upool(const __nv_bfloat16* __restrict__ in, int P, int Ho, int Wo, int C,
-                        int cs, __nv_bfloat16* __restrict__ out) {
-  const int G = C / 8;
-  const long long total = (long long)P * Ho * Wo * G;
+// 2x2 max pooling between planar buffers: planes [0, G) of the input (stored
+// side spi = 2 so or 2 so + 2) into planes [0, G) of the output (side spo).
+__global__ void k_upool(const __nv_bfloat16* __restrict__ in, size_t in_plane, int in_guard,
+                        int spi, __nv_bfloat16* __restrict__ out, size_t out_plane, int out_guard,
+                        int spo, int P, int so, int G) {
+  const int pi = spi != 2 * so, po = spo != so;
+  const long long npx = (long long)P * so * so, total = npx * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int g = (int)(i % G);
-    const long long px = i / G;
-    const int xo = (int)(px % Wo), yo = (int)((px / Wo) % Ho);
-    const long long b = px / ((long long)Wo * Ho);
-    const int Wi = 2 * Wo;
-    const size_t base = (((size_t)b * 2 * Ho + 2 * yo) * Wi + 2 * xo) * cs + 8 * g;
-    const uint4 a = *reinterpret_cast<const uint4*>(in + base);
-    const uint4 bq = *reinterpret_cast<const uint4*>(in + base + cs);
-    const uint4 c = *reinterpret_cast<const uint4*>(in + base + (size_t)Wi * cs);
-    const uint4 d = *reinterpret_cast<const uint4*>(in + base + (size_t)Wi * cs + cs);
+    const long long px = i % npx;
+    const int g = (int)(i / npx);
+    const int xo = (int)(px % so), yo = (int)((px / so) % so);
+    const long long b = px / ((long long)so * so);
+    const size_t ip = ((size_t)b * spi + 2 * yo + pi) * spi + 2 * xo + pi;
+    const __nv_bfloat16* src = in + (size_t)g * in_plane + (in_guard + ip) * 8;
+    const uint4 a = *reinterpret_cast<const uint4*>(src);
+    const uint4 bq = *reinterpret_cast<const uint4*>(src + 8);
+    const uint4 c = *reinterpret_cast<const uint4*>(src + (size_t)spi * 8);
+    const uint4 d = *reinterpret_cast<const uint4*>(src + (size_t)spi * 8 + 8);
     const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
     const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&bq);
     const __nv_bfloat162* pc = reinterpret_cast<const __nv_bfloat162*>(&c);
     const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&d);
     uint4 o;
-    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+    __nv_bfloat162* pw = reinterpret_cast<__nv_bfloat162*>(&o);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) po[k] = __hmax2(__hmax2(pa[k], pb[k]), __hmax2(pc[k], pd[k]));
-    *reinterpret_cast<uint4*>(out + (size_t)px * C + 8 * g) = o;
+    for (int k = 0; k < 4; ++k) pw[k] = __hmax2(__hmax2(pa[k], pb[k]), __hmax2(pc[k], pd[k]));
+    const size_t op = ((size_t)b * spo + yo + po) * spo + xo + po;
+    *reinterpret_cast<uint4*>(out + (size_t)g * out_plane + (out_guard + op) * 8) = o;
   }
 }
 
-// Output layer: p = sigmoid(b + sum_c w_c d0_c), FP32 weights, per patch pixel.
-__global__ void k_uout(const __nv_bfloat16* __restrict__ d0, const float* __restrict__ wout,
-                       long long n_px, float* __restrict__ prob) {
+// Output layer: p = sigmoid(b + sum_c w_c d0_c), FP32 weights, per patch pixel
+// (d0: two planes, padded 66 x 66 per patch).
+__global__ void k_uout(const __nv_bfloat16* __restrict__ d0, size_t plane, int guard,
+                       const float* __restrict__ wout, long long n_px, float* __restrict__ prob) {
+  constexpr int sp = kUPatch + 2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_px;
        i += (long long)gridDim.x * blockDim.x) {
-    const uint4* src = reinterpret_cast<const uint4*>(d0 + (size_t)i * kUC0);
-    const uint4 a = src[0], b = src[1];
+    const int v = (int)(i % kUPatch), u = (int)((i / kUPatch) % kUPatch);
+    const long long pt = i / (kUPatch * kUPatch);
+    const size_t o = ((size_t)pt * sp + u + 1) * sp + v + 1;
+    const uint4 a = *reinterpret_cast<const uint4*>(d0 + (guard + o) * 8);
+    const uint4 b = *reinterpret_cast<const uint4*>(d0 + plane + (guard + o) * 8);
     const __nv_bfloat16* ha = reinterpret_cast<const __nv_bfloat16*>(&a);
     const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&b);
     float s = wout[kUC0];
@@ -424,6 +495,23 @@ __global__ void k_uout(const __nv_bfloat16* __restrict__ d0, const float* __rest
 #pragma unroll
     for (int c = 0; c < 8; ++c) s = fmaf(wout[8 + c], __bfloat162float(hb[c]), s);
     prob[i] = 1.0f / (1.0f + expf(-s));
+  }
+}
+
+// Interior of planes [goff, goff + C / 8) of a planar buffer (stored side sp)
+// into a dense NHWC array [P][s][s][C].
+__global__ void k_ucompact(const __nv_bfloat16* __restrict__ in, size_t plane, int guard, int goff,
+                           int P, int s, int sp, int C, __nv_bfloat16* __restrict__ out) {
+  const int pad = sp != s;
+  const long long total = (long long)P * s * s * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long px = i / C;
+    const int x = (int)(px % s), y = (int)((px / s) % s);
+    const long long b = px / ((long long)s * s);
+    const size_t ip = ((size_t)b * sp + y + pad) * sp + x + pad;
+    out[i] = in[(size_t)(goff + c / 8) * plane + (guard + ip) * 8 + (c % 8)];
   }
 }
 
@@ -477,28 +565,32 @@ struct vimg_unet {
   std::string err;
   int sticky = 0;
   bool loaded = false;
-  // per layer: packed weights and biases
   std::vector<LayerDef> defs;
-  std::vector<__nv_bfloat16*> wpack;
-  std::vector<float*> bpack;
   float* wout = nullptr;  // [17] output layer, FP32
-  // activations (NHWC BF16)
-  __nv_bfloat16* in0 = nullptr;
-  __nv_bfloat16* a[kULevels + 1] = {};    // first encoder conv of a level
-  __nv_bfloat16* da[kULevels] = {};       // first decoder conv of a level
-  __nv_bfloat16* cat[kULevels] = {};      // [skip, up] per level 0..3
-  __nv_bfloat16* pool[kULevels + 1] = {}; // pooled input of levels 1..4
-  __nv_bfloat16* d[kULevels + 1] = {};    // decoder output per level 0..3, bottleneck at 4
+  // activations: planar BF16 (levels < kUPadLevels with zero border and guards)
+  struct Act {
+    __nv_bfloat16* p = nullptr;
+    int level = 0, C = 0, guard = 0;
+    size_t plane = 0;  // elements per 8-channel plane
+  };
+  Act in0;
+  Act a[kULevels + 1];     // first encoder conv of a level
+  Act da[kULevels];        // first decoder conv of a level
+  Act cat[kULevels];       // [skip, up] per level 0..3
+  Act pool[kULevels + 1];  // pooled input of levels 1..4
+  Act d[kULevels + 1];     // decoder output per level 0..3, bottleneck at 4
   float* pprob = nullptr;                 // [P][64][64]
   double* stats = nullptr;                // [max_seg][2][2]
+  double* part = nullptr;                 // [max_seg][2][kUStatBlocks][2]
   int* dev_err = nullptr;
   struct Conv {
     ConvParams p;
     CUtensorMap map;
     int grid = 0;
     size_t smem = 0;
+    int cin_real = 0;                     // weights' input channels (2 for the first layer)
   };
-  std::vector<Conv> convs;  // execution order
+  std::vector<Conv> convs;  // execution order = parameter order
   // profiling: event pairs around the tensor-core launches and the whole run
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -533,55 +625,84 @@ cudaError_t ualloc(vimg_unet* u, T*& p, size_t n) {
   return e;
 }
 
-// One tensor-core convolution: input [P][Hl][Wl][cin] (whole buffer), output
-// at a channel offset of a buffer with out_stride channels.
-int setup_conv(vimg_unet* u, const __nv_bfloat16* in, int Hl, int Wl, int cin, int taps, int n_total,
-               int up, int cout, int relu, __nv_bfloat16* out, int out_stride, int out_off,
-               const __nv_bfloat16* wpack, const float* bias) {
+inline int side(int l) { return kUPatch >> l; }
+inline int stored(int l) { return l < kUPadLevels ? side(l) + 2 : side(l); }
+
+// One tensor-core layer: input = all planes of `in`; output into planes
+// [out_goff, out_goff + cout / 8) of `out`.
+int setup_conv(vimg_unet* u, const vimg_unet::Act& in, int cin_real, int taps, int n_total, int up,
+               int cout, int relu, const vimg_unet::Act& out, int out_goff) {
   vimg_unet::Conv c{};
   ConvParams& p = c.p;
-  const int P = u->P;
-  p.total_px = P * Hl * Wl;
-  p.Hl = Hl, p.Wl = Wl;
-  p.bh = std::min(Hl, 128 / Wl);
-  p.bb = std::max(1, 128 / (Hl * Wl));
-  p.kc = std::min(cin, 64);
-  p.nkc = cin / p.kc;
+  const int P = u->P, li = in.level, cin = in.C;
+  p.s_in = side(li), p.sp_in = stored(li);
+  p.lin = p.sp_in != p.s_in;
+  p.m_px = P * p.sp_in * p.sp_in;
   p.taps = taps;
   p.ntile = std::min(n_total, 256);
   p.n_ntiles = n_total / p.ntile;
-  p.n_mtiles = (p.total_px + 127) / 128;
-  p.a_bytes = 128u * p.kc * 2u;
-  p.b_bytes = (uint32_t)p.ntile * p.kc * 2u;
-  p.stages = (int)std::min<size_t>(kUMaxStages, kUSmemMax / (p.a_bytes + p.b_bytes));
-  if (p.stages < 2 || p.bh * p.bb * Wl != 128 || cin % 16 || p.ntile % 16 || n_total % p.ntile)
+  p.n_mtiles = (p.m_px + 127) / 128;
+  p.kc = std::min(cin, 64);
+  if (p.lin)  // all taps' weights of a chunk in one stage: keep them within 48 KB
+    while (p.kc > 16 && (size_t)taps * p.ntile * p.kc * 2 > 48 * 1024) p.kc /= 2;
+  p.nkc = cin / p.kc;
+  if (p.lin) {
+    p.in = in.p, p.in_plane = in.plane, p.in_guard = in.guard;
+    p.hoff = taps == 9 ? p.sp_in + 1 : 0;
+    const int rows = (128 + 2 * p.hoff + 7) & ~7;  // 128-byte multiple
+    p.plane_bytes = (uint32_t)rows * 16;
+    p.a_bytes = (uint32_t)(p.kc / 8) * p.plane_bytes;
+    p.b_bytes = (uint32_t)taps * p.ntile * p.kc * 2;
+    if (p.hoff > in.guard || rows - p.hoff > in.guard)
+      return ufail(u, VIMG_ERR_ARG, "unet: halo exceeds the guard zone");
+  } else {
+    p.bh = std::min(p.s_in, 128 / p.s_in);
+    p.bb = std::max(1, 128 / (p.s_in * p.s_in));
+    p.a_bytes = 128u * p.kc * 2u;
+    p.b_bytes = (uint32_t)p.ntile * p.kc * 2u;
+  }
+  const size_t stage = (size_t)p.a_bytes + p.b_bytes;
+  const int max_st = p.lin ? 4 : kUMaxStages;  // halo stages are few and large
+  p.stages = (int)std::min<size_t>(max_st, kUSmemMax / stage);
+  if (p.stages < 2 || cin % 16 || p.ntile % 16 || n_total % p.ntile ||
+      (!p.lin && (p.bh * p.bb * p.s_in != 128 || 8 * p.s_in > 256)))
     return ufail(u, VIMG_ERR_ARG, "unet: unsupported layer shape");
-  p.wpack = wpack, p.bias = bias, p.out = out, p.out_stride = out_stride, p.out_off = out_off;
+  p.bias = nullptr, p.wpack = nullptr;  // set after allocation
+  p.out = out.p, p.out_plane = out.plane, p.out_guard = out.guard, p.out_goff = out_goff;
+  p.so = up ? 2 * p.s_in : p.s_in;
+  p.spo = stored(out.level);
   p.up = up, p.cout = cout, p.relu = relu, p.err = u->dev_err;
-  c.smem = (size_t)p.stages * (p.a_bytes + p.b_bytes);
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return ufail(u, VIMG_ERR_CUDA, "unet: cuTensorMapEncodeTiled unavailable");
-  cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)Wl, (cuuint64_t)Hl, (cuuint64_t)P};
-  cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)Wl * cin * 2,
-                           (cuuint64_t)Hl * Wl * cin * 2};
-  cuuint32_t box[4] = {8, (cuuint32_t)Wl, (cuuint32_t)p.bh, (cuuint32_t)p.bb};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = fn(&c.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(in),
-                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return ufail(u, VIMG_ERR_CUDA, "unet: tensor map encode failed");
-  // resident CTAs per SM: shared memory and tensor memory (512 columns)
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc, kUThreads, c.smem) !=
-      cudaSuccess)
-    occ = 1;
+  c.cin_real = cin_real;
+  c.smem = (size_t)p.stages * stage;
+  if (!p.lin) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return ufail(u, VIMG_ERR_CUDA, "unet: cuTensorMapEncodeTiled unavailable");
+    const int sd = p.s_in;
+    cuuint64_t dims[4] = {(cuuint64_t)8 * sd, (cuuint64_t)sd, (cuuint64_t)P, (cuuint64_t)cin / 8};
+    cuuint64_t strides[3] = {(cuuint64_t)sd * 16, (cuuint64_t)sd * sd * 16,
+                             (cuuint64_t)in.plane * 2};
+    cuuint32_t box[4] = {(cuuint32_t)(8 * sd), (cuuint32_t)p.bh, (cuuint32_t)p.bb, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(&c.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                    const_cast<__nv_bfloat16*>(in.p + (size_t)in.guard * 8), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return ufail(u, VIMG_ERR_CUDA, "unet: tensor map encode failed");
+  } else {
+    std::memset(&c.map, 0, sizeof(c.map));  // unused by halo tiles
+  }
+  // resident CTAs per SM: shared memory (228 KB per SM, ~1 KB reserved per CTA)
+  // and tensor memory (512 columns)
   const int tcols = std::max(32, 2 * p.ntile);
-  occ = std::max(1, std::min(occ, 512 / tcols));
-  const int tiles = p.n_mtiles * p.n_ntiles;
-  c.grid = std::min(tiles, u->sms * occ);
+  const int by_smem = (int)((228 * 1024) / (c.smem + 2048));
+  const int occ = std::max(1, std::min({by_smem, 512 / tcols, 4}));
+  c.grid = u->sms * occ;
   u->convs.push_back(c);
   return VIMG_OK;
+}
+
+size_t pack_elems(const ConvParams& p) {
+  return (size_t)p.n_ntiles * p.taps * p.nkc * p.kc * p.ntile;
 }
 
 }  // namespace
@@ -645,70 +766,67 @@ extern "C" vimg_unet* vimg_unet_create(int H, int W, int max_segments, void* str
   auto A = [&](auto*& ptr, size_t n) {
     if (e == cudaSuccess) e = ualloc(u, ptr, n);
   };
+  // planar activations, zeroed once: borders and guards are never written
+  auto Z = [&](vimg_unet::Act& act, int level, int C) {
+    act.level = level, act.C = C;
+    act.guard = level < kUPadLevels ? kUGuard : 0;
+    act.plane = (P * (size_t)stored(level) * stored(level) + 2 * (size_t)act.guard) * 8;
+    const size_t n = act.plane * (C / 8);
+    A(act.p, n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(act.p, 0, n * sizeof(__nv_bfloat16), u->st);
+  };
   A(u->dev_err, 1);
   A(u->stats, 4 * (size_t)max_segments);
+  A(u->part, 4 * (size_t)max_segments * kUStatBlocks);
   A(u->pprob, P * kUPatch * kUPatch);
-  A(u->in0, P * kUPatch * kUPatch * kUC0);
+  Z(u->in0, 0, kUC0);
   for (int l = 0; l <= kULevels; ++l) {
-    const size_t px = P * (size_t)(kUPatch >> l) * (kUPatch >> l);
     const int C = kUC0 << l;
-    A(u->a[l], px * C);
-    A(u->d[l], px * C);
-    if (l < kULevels) A(u->cat[l], px * 2 * C);
-    if (l < kULevels) A(u->da[l], px * C);
-    if (l > 0) A(u->pool[l], px * (C / 2));
+    Z(u->a[l], l, C);
+    Z(u->d[l], l, C);
+    if (l < kULevels) Z(u->cat[l], l, 2 * C);
+    if (l < kULevels) Z(u->da[l], l, C);
+    if (l > 0) Z(u->pool[l], l, C / 2);
   }
   A(u->wout, kUC0 + 1);
-  // packed weights per tensor-core layer
-  u->wpack.assign(u->defs.size(), nullptr);
-  u->bpack.assign(u->defs.size(), nullptr);
-  for (size_t i = 0; i < u->defs.size(); ++i) {
-    const LayerDef& L = u->defs[i];
-    if (L.kind == 2) continue;
-    const int cin = std::max(L.cin, kUC0);
-    const int taps = L.kind == 0 ? 9 : 1;
-    const int n_total = L.kind == 0 ? L.cout : 4 * L.cout;
-    A(u->wpack[i], (size_t)taps * cin * n_total);
-    A(u->bpack[i], (size_t)n_total);
-  }
   if (e == cudaSuccess) e = cudaMemsetAsync(u->dev_err, 0, sizeof(int), u->st);
   if (e != cudaSuccess) return bail(std::string("vimg_unet_create: ") + cudaGetErrorString(e));
-  // layer plan (execution order)
+  // layer plan (execution order = parameter order)
   int li = 0;
-  auto conv = [&](const __nv_bfloat16* in, int Hl, int cin, __nv_bfloat16* out, int ostride,
-                  int ooff) {
-    const LayerDef& L = u->defs[li];
-    const int rc = setup_conv(u, in, Hl, Hl, cin, 9, L.cout, 0, L.cout, 1, out, ostride, ooff,
-                              u->wpack[li], u->bpack[li]);
-    ++li;
-    return rc;
+  auto conv = [&](const vimg_unet::Act& in, const vimg_unet::Act& out, int goff) {
+    const LayerDef& L = u->defs[li++];
+    return setup_conv(u, in, L.cin, 9, L.cout, 0, L.cout, 1, out, goff);
   };
-  auto upc = [&](const __nv_bfloat16* in, int Hl, int cin, __nv_bfloat16* out, int ostride,
-                 int ooff) {
-    const LayerDef& L = u->defs[li];
-    const int rc = setup_conv(u, in, Hl, Hl, cin, 1, 4 * L.cout, 1, L.cout, 0, out, ostride, ooff,
-                              u->wpack[li], u->bpack[li]);
-    ++li;
-    return rc;
+  auto upc = [&](const vimg_unet::Act& in, const vimg_unet::Act& out, int goff) {
+    const LayerDef& L = u->defs[li++];
+    return setup_conv(u, in, L.cin, 1, 4 * L.cout, 1, L.cout, 0, out, goff);
   };
   int rc = VIMG_OK;
-  // encoder: level l input = in0 (l = 0) or pool[l]; skip -> cat[l][0, C)
+  // encoder: level l input = in0 (l = 0) or pool[l]; skip -> cat[l] planes [0, C / 8)
   for (int l = 0; l <= kULevels && rc == VIMG_OK; ++l) {
-    const int Hl = kUPatch >> l, C = kUC0 << l;
-    const __nv_bfloat16* in = l == 0 ? u->in0 : u->pool[l];
-    const int cin = l == 0 ? kUC0 : C / 2;
-    rc = conv(in, Hl, cin, u->a[l], C, 0);
-    if (rc == VIMG_OK)
-      rc = l < kULevels ? conv(u->a[l], Hl, C, u->cat[l], 2 * C, 0) : conv(u->a[l], Hl, C, u->d[l], C, 0);
+    const vimg_unet::Act& in = l == 0 ? u->in0 : u->pool[l];
+    rc = conv(in, u->a[l], 0);
+    if (rc == VIMG_OK) rc = l < kULevels ? conv(u->a[l], u->cat[l], 0) : conv(u->a[l], u->d[l], 0);
   }
-  // decoder: up from d[l + 1] into cat[l][C, 2C), then two convolutions -> d[l]
+  // decoder: up from d[l + 1] into cat[l] planes [C / 8, C / 4), then two convolutions -> d[l]
   for (int l = kULevels - 1; l >= 0 && rc == VIMG_OK; --l) {
-    const int Hl = kUPatch >> l, C = kUC0 << l;
-    rc = upc(u->d[l + 1], Hl / 2, 2 * C, u->cat[l], 2 * C, C);
-    if (rc == VIMG_OK) rc = conv(u->cat[l], Hl, 2 * C, u->da[l], C, 0);
-    if (rc == VIMG_OK) rc = conv(u->da[l], Hl, C, u->d[l], C, 0);
+    const int C = kUC0 << l;
+    rc = upc(u->d[l + 1], u->cat[l], C / 8);
+    if (rc == VIMG_OK) rc = conv(u->cat[l], u->da[l], 0);
+    if (rc == VIMG_OK) rc = conv(u->da[l], u->d[l], 0);
   }
   if (rc != VIMG_OK) return bail(u->err);
+  // packed weights and biases per tensor-core layer
+  for (auto& c : u->convs) {
+    __nv_bfloat16* w = nullptr;
+    float* b = nullptr;
+    A(w, pack_elems(c.p));
+    A(b, (size_t)c.p.n_ntiles * c.p.ntile);
+    c.p.wpack = w, c.p.bias = b;
+  }
+  // the zeroed buffers must be in place before any stream uses them
+  if (e == cudaSuccess) e = cudaStreamSynchronize(u->st);
+  if (e != cudaSuccess) return bail(std::string("vimg_unet_create: ") + cudaGetErrorString(e));
   return u;
 }
 
@@ -731,16 +849,16 @@ extern "C" int vimg_unet_load(vimg_unet* u, const float* d_params) {
           "unet output weights");
       continue;
     }
-    const int cin = std::max(L.cin, kUC0), taps = L.kind == 0 ? 9 : 1;
-    const int n_total = L.kind == 0 ? L.cout : 4 * L.cout;
-    const int kc = std::min(cin, 64), nkc = cin / kc;
-    const int ntile = std::min(n_total, 256), n_ntiles = n_total / ntile;
-    const long long total = (long long)n_ntiles * taps * nkc * kc * ntile;
-    k_pack<<<grid_for(total, 256, u->sms), 256, 0, u->st>>>(w, b, L.kind == 1, L.cin, L.cout, taps,
-                                                          kc, nkc, ntile, n_ntiles, u->wpack[i],
-                                                          u->bpack[i]);
+    vimg_unet::Conv& c = u->convs[i];
+    const ConvParams& p = c.p;
+    const long long total = (long long)pack_elems(p);
+    k_pack<<<grid_for(total, 256, u->sms), 256, 0, u->st>>>(
+        w, b, p.up, p.lin, c.cin_real, L.cout, p.taps, p.kc, p.nkc, p.ntile, p.n_ntiles,
+        const_cast<__nv_bfloat16*>(p.wpack), const_cast<float*>(p.bias));
     UCK(cudaGetLastError(), "unet weight pack");
   }
+  // synchronous, so that a handle on another stream may run the U-Net next
+  UCK(cudaStreamSynchronize(u->st), "unet weight pack");
   u->loaded = true;
   return VIMG_OK;
 }
@@ -790,22 +908,21 @@ int vimg_unet_run_on(vimg_unet* u, const float* d_summary, int k, float* d_prob,
     const int ks = std::min(k - s0, u->max_seg);
     const float* summ = d_summary + (size_t)s0 * 2 * HW;
     const int np = ks * u->npatch;
-    k_ustats<<<2 * ks, 256, 0, st>>>(summ, (int)HW, u->stats);
+    k_ustats_part<<<dim3(kUStatBlocks, 2 * ks), 256, 0, st>>>(summ, (int)HW, u->part);
+    UCK(cudaGetLastError(), "unet statistics");
+    k_ustats_fin<<<(2 * ks + 63) / 64, 64, 0, st>>>(u->part, 2 * ks, (int)HW, u->stats);
     UCK(cudaGetLastError(), "unet statistics");
     const long long n_in = (long long)np * kUPatch * kUPatch;
     k_uinput<<<grid_for(n_in, 256, u->sms), 256, 0, st>>>(summ, u->stats, u->H, u->W, u->npy,
-                                                          u->npx, np, u->in0);
+                                                          u->npx, np, u->in0.guard, u->in0.p);
     UCK(cudaGetLastError(), "unet input");
-    // the tensor-core layers run over all P patch slots; slots past np hold
-    // stale inputs whose outputs are never read
+    // the tensor-core layers run over the np patch slots in use
     size_t ci = 0;
     auto run_conv = [&]() -> int {
       vimg_unet::Conv& c = u->convs[ci++];
       ConvParams p = c.p;
-      // shrink to the patches in use
-      const int px = np * p.Hl * p.Wl;
-      p.total_px = px;
-      p.n_mtiles = (px + 127) / 128;
+      p.m_px = np * p.sp_in * p.sp_in;
+      p.n_mtiles = (p.m_px + 127) / 128;
       const int grid = std::min(c.grid, p.n_mtiles * p.n_ntiles);
       conv_ev.push_back(record(u, st));
       k_conv_tc<<<grid, kUThreads, c.smem, st>>>(c.map, p);
@@ -816,10 +933,12 @@ int vimg_unet_run_on(vimg_unet* u, const float* d_summary, int k, float* d_prob,
     int rc = VIMG_OK;
     for (int l = 0; l <= kULevels && rc == VIMG_OK; ++l) {
       if (l > 0) {
-        const int Ho = kUPatch >> l, C = kUC0 << (l - 1);
-        const __nv_bfloat16* src = u->cat[l - 1];
-        const long long n = (long long)np * Ho * Ho * (C / 8);
-        k_upool<<<grid_for(n, 256, u->sms), 256, 0, st>>>(src, np, Ho, Ho, C, 2 * C, u->pool[l]);
+        const int so = side(l), G = (kUC0 << (l - 1)) / 8;
+        const vimg_unet::Act &src = u->cat[l - 1], &dst = u->pool[l];
+        const long long n = (long long)np * so * so * G;
+        k_upool<<<grid_for(n, 256, u->sms), 256, 0, st>>>(src.p, src.plane, src.guard,
+                                                          stored(l - 1), dst.p, dst.plane,
+                                                          dst.guard, stored(l), np, so, G);
         UCK(cudaGetLastError(), "unet pooling");
       }
       rc = run_conv();
@@ -829,7 +948,8 @@ int vimg_unet_run_on(vimg_unet* u, const float* d_summary, int k, float* d_prob,
       for (int j = 0; j < 3 && rc == VIMG_OK; ++j) rc = run_conv();
     if (rc != VIMG_OK) return rc;
     const long long n_px = (long long)np * kUPatch * kUPatch;
-    k_uout<<<grid_for(n_px, 256, u->sms), 256, 0, st>>>(u->d[0], u->wout, n_px, u->pprob);
+    k_uout<<<grid_for(n_px, 256, u->sms), 256, 0, st>>>(u->d[0].p, u->d[0].plane, u->d[0].guard,
+                                                        u->wout, n_px, u->pprob);
     UCK(cudaGetLastError(), "unet output layer");
     const long long n_out = (long long)ks * HW;
     k_umerge<<<grid_for(n_out, 256, u->sms), 256, 0, st>>>(u->pprob, u->H, u->W, u->npy, u->npx, ks,
@@ -884,7 +1004,7 @@ int unet_dims(const vimg_unet* u, int* H, int* W) {
   return 0;
 }
 
-extern "C" int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_patches, int* side,
+extern "C" int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_patches, int* side_out,
                                     int* channels) {
   if (!u) return ufail(u, VIMG_ERR_ARG, "null U-Net");
   if (u->sticky) return u->sticky;
@@ -892,27 +1012,36 @@ extern "C" int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_pat
   if (i < 0 || i > n_tc + 1) return ufail(u, VIMG_ERR_ARG, "vimg_unet_activation: bad index");
   const int np = u->last_np;
   int sd, C;
-  const void* src;
-  size_t pitch, width, elem;
   if (i == 0) {
-    sd = kUPatch, C = kUC0, src = u->in0, elem = 2, pitch = width = (size_t)C * 2;
+    sd = kUPatch, C = kUC0;
   } else if (i <= n_tc) {
     const ConvParams& p = u->convs[i - 1].p;
-    sd = p.up ? 2 * p.Hl : p.Hl;
-    C = p.up ? p.cout : p.ntile * p.n_ntiles;
-    elem = 2;
-    src = p.out + p.out_off;
-    pitch = (size_t)p.out_stride * 2, width = (size_t)C * 2;
+    sd = p.so, C = p.up ? p.cout : p.ntile * p.n_ntiles;
   } else {
-    sd = kUPatch, C = 1, src = u->pprob, elem = 4, pitch = width = 4;
+    sd = kUPatch, C = 1;
   }
   if (n_patches) *n_patches = np;
-  if (side) *side = sd;
+  if (side_out) *side_out = sd;
   if (channels) *channels = C;
   if (!d_out || np == 0) return VIMG_OK;
-  (void)elem;
-  UCK(cudaMemcpy2DAsync(d_out, width, src, pitch, width, (size_t)np * sd * sd,
+  if (i == n_tc + 1) {
+    UCK(cudaMemcpyAsync(d_out, u->pprob, sizeof(float) * (size_t)np * kUPatch * kUPatch,
                         cudaMemcpyDeviceToDevice, u->st),
-      "unet activation copy");
+        "unet activation copy");
+    return VIMG_OK;
+  }
+  const __nv_bfloat16* src;
+  size_t plane;
+  int sp, guard, goff;
+  if (i == 0) {
+    src = u->in0.p, plane = u->in0.plane, guard = u->in0.guard, sp = stored(0), goff = 0;
+  } else {
+    const ConvParams& p = u->convs[i - 1].p;
+    src = p.out, plane = p.out_plane, guard = p.out_guard, sp = p.spo, goff = p.out_goff;
+  }
+  const long long n = (long long)np * sd * sd * C;
+  k_ucompact<<<grid_for(n, 256, u->sms), 256, 0, u->st>>>(src, plane, guard, goff, np, sd, sp, C,
+                                                         static_cast<__nv_bfloat16*>(d_out));
+  UCK(cudaGetLastError(), "unet activation copy");
   return VIMG_OK;
 }
