@@ -58,6 +58,21 @@ def fp32_alu_peak_tflops(sm_max_mhz):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
 
 
+def unet_flops_per_patch(layers):
+    """Useful FLOPs of one 64x64 patch through the U-Net (3x3 and up-convolutions
+    and the output layer; the first layer's 2 input channels, not its padding)."""
+    side = {0: 64, 1: 32, 2: 16, 3: 8, 4: 4}
+    sides = []
+    for l in range(5):
+        sides += [side[l]] * 2
+    for l in range(3, -1, -1):
+        sides += [side[l + 1], side[l], side[l]]
+    fl = 0
+    for (kind, ci, co), s in zip(layers[:-1], sides):
+        fl += 2 * s * s * ci * co * (9 if kind == "conv" else 4)
+    return fl + 2 * 64 * 64 * layers[-1][1]
+
+
 def corr_flops_per_frame():
     ny = nx = (H - 2 * R) // P
     return 2.0 * ny * nx * P * P * (2 * R + 1) ** 2
@@ -430,9 +445,10 @@ def time_variant(h, frames, outs, steps, warmup, stream, traces=None):
 
 
 def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k_max, ws):
-    """The task's other configurations on the same video: the learned shift
-    proposal (CNN + +-2 px window + full-window fallback), judged against the
-    full-window shifts."""
+    """Other configurations on the same video: voltage traces of the neuron
+    ROIs, the spiking-pixel U-Net on the summary pairs, the BF16 tensor-core
+    correlation and the learned shift proposal (CNN + +-2 px window +
+    full-window fallback), the last two judged against the full-window shifts."""
     from paper_2403_16438_gb300 import proposal, synth, vimg
     n = frames.shape[0]
     out = {}
@@ -453,6 +469,69 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "config": "full-window FP32 path, corrected frames and summaries as the main line, plus "
                   "the mean corrected intensity of every neuron footprint of the scene per frame",
+    }
+    # spiking-pixel U-Net on every segment's summary pair (Sec. III-C), random
+    # weights of the architecture: alone on the 200 summary pairs, and attached
+    # to the pipeline (corrected frames, summaries and probability maps)
+    layers = vimg.unet_layers()
+    up = synth.unet_params(layers, seed=7).to(dev)
+    un = vimg.Unet(H, W, max_segments=8, stream=stream)
+    un.load(up)
+    prob = torch.empty((k_max, H, W), device=dev)
+    for _ in range(args.warmup):
+        un.run(summary, prob)
+    un.synchronize()
+    un.profile(True)
+    un.profile_read(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        un.run(summary, prob)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    conv_ms, run_ms, conv_launches = un.profile_read(reset=True)
+    un.profile(False)
+    ms_alone = e0.elapsed_time(e1)
+    n_patch = k_max * ((H - 64 + 31) // 32 + 1) * ((W - 64 + 31) // 32 + 1)
+    fl = unet_flops_per_patch(layers) * n_patch * args.steps
+    pk, _ = peaks()
+    tflops = fl / (conv_ms / 1e3) / 1e12 if conv_ms > 0 else None
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk)
+    h.set_template(T)
+    h.attach_unet(un)
+
+    def pipe_step():
+        h.reset()
+        h.process(frames, shifts=torch.empty_like(ref), corrected=corrected, summary=summary,
+                  prob=prob)
+    for _ in range(args.warmup):
+        pipe_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        pipe_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pipe = e0.elapsed_time(e1)
+    h.close()
+    un.close()
+    out["unet_segmentation"] = {
+        "value": n * args.steps * ws / (ms_pipe / 1000.0), "unit": UNIT,
+        "x_realtime": n * args.steps / (ms_pipe / 1000.0) / RECORD_FPS,
+        "ms_per_step": ms_pipe / args.steps,
+        "unet_alone_ms_per_step": ms_alone / args.steps,
+        "unet_segments_per_s": k_max * args.steps / (ms_alone / 1000.0),
+        "unet_patches_per_step": n_patch,
+        "conv_roofline": {"kernel": "k_conv_tc (22 tensor-core layers)", "bound": "tensor",
+                          "achieved": tflops, "peak": pk["bf16_tflops_sustained"],
+                          "unit": "TFLOP/s",
+                          "frac": tflops / pk["bf16_tflops_sustained"] if tflops else None,
+                          "useful_gflop_per_patch": unet_flops_per_patch(layers) / 1e9,
+                          "conv_ms_per_step": conv_ms / args.steps,
+                          "conv_launches_per_step": conv_launches / args.steps},
+        "config": "summary pairs of the same 10,000-frame video (200 segments), 64x64 patches "
+                  "every 32 px (225 per segment), 8 segments per internal pass; random weights "
+                  "of the U-Net reading (16..256 channels, 4 pooling steps)",
     }
     # BF16 tensor-core correlation (tcgen05), FP32 accumulation
     h = vimg.Handle(H, W, stream=stream, max_chunk=args.bf16_chunk, flags=vimg.CORR_BF16)

@@ -97,7 +97,7 @@ size_t weight_count(const LayerDef& L) {
 // stored dense; their tiles take one TMA box per tap and plane (im2col boxes
 // with zero fill at the image border), which costs less there than a border.
 constexpr int kUPadLevels = 3;
-constexpr int kUGuard = 272;  // guard pixels before and after each padded plane
+constexpr int kUGuard = 640;  // guard pixels before and after each padded plane
 
 struct ConvParams {
   int lin;                 // 1: padded input, halo tiles (bulk copies); 0: im2col boxes (TMA)
@@ -110,6 +110,9 @@ struct ConvParams {
   int hoff;                // halo: first pixel = m0 - hoff
   uint32_t plane_bytes;    // halo: one 8-channel plane in shared memory (rows x 16 B)
   int kc, nkc, taps;       // channels per K chunk, chunks per tile (x taps in box mode)
+  int R;                   // 128-row subtiles per tile (halo tiles share one halo)
+  int bres;                // 1: the layer's weights stay in shared memory for the whole CTA
+  uint32_t bres_bytes;
   int ntile, n_ntiles, n_mtiles;
   int stages;
   uint32_t a_bytes, b_bytes;   // per stage
@@ -120,29 +123,54 @@ struct ConvParams {
   int out_guard, out_goff;     // guard pixels; first output plane written
   int so, spo;                 // output side, stored output side
   int up, cout, relu;
+  unsigned long long div_img, div_sp;  // ceil(2^40 / (sp_in^2)), ceil(2^40 / sp_in)
   int* err;
 };
+
+// n / d for 0 <= n < 2^31 and d < 2^16 from M = ceil(2^40 / d): the estimate is
+// exact or one too large.
+__device__ __forceinline__ int fdiv(int n, int d, unsigned long long M) {
+  int q = (int)(((unsigned long long)n * M) >> 40);
+  if (q * d > n) --q;
+  return q;
+}
+
+// Bounded wait with a short sleep between polls, for the epilogue warps (they
+// wait long) so that they leave issue slots to the MMA thread.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kTcSpin; ++i) {
+    if (mbar_wait(bar, parity, 1)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// TQ: taps per stage (9 for 3x3 halo tiles, 1 for up-convolutions and im2col boxes).
+template <int TQ>
 __global__ void __launch_bounds__(kUThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kUMaxStages], empty[kUMaxStages];
-  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done, bres_full;
+  __shared__ float sbias[4 * 256];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = p.stages;
-  unsigned char* sA = smem;                                  // [S][a_bytes]
-  unsigned char* sB = smem + (size_t)S * p.a_bytes;          // [S][b_bytes]
+  unsigned char* sBres = smem;                                   // resident weights
+  unsigned char* sA = smem + p.bres_bytes;                       // [S][a_bytes]
+  unsigned char* sB = sA + (size_t)S * p.a_bytes;                // [S][b_bytes] (not resident)
   const int n_tiles = p.n_mtiles * p.n_ntiles;
-  const int nq = p.lin ? p.nkc : p.taps * p.nkc;             // stages per tile
-  const int tq = p.lin ? p.taps : 1;                         // taps per stage
-  const uint32_t tcols = (uint32_t)(2 * p.ntile) < 32u ? 32u : (uint32_t)(2 * p.ntile);
+  const int nq = TQ == 9 ? p.nkc : p.taps * p.nkc;           // stages per tile
+  const int acc_cols = p.R * p.ntile;                        // columns of one accumulator
+  uint32_t tcols = 32;
+  while (tcols < (uint32_t)(2 * acc_cols)) tcols <<= 1;
+  const uint32_t stage_tx = p.a_bytes + (p.bres ? 0u : p.b_bytes);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -150,6 +178,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  for (int i = tid; i < p.n_ntiles * p.ntile; i += blockDim.x) sbias[i] = p.bias[i];
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -160,6 +189,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
       mbar_init(&acc_empty[b], kUEpiWarps);
     }
     mbar_init(&mma_done, 1);
+    mbar_init(&bres_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -168,14 +198,27 @@ __global__ void __launch_bounds__(kUThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int img_px = p.sp_in * p.sp_in;
+  const int m_tile = 128 * p.R;
 
   if (warp == kUEpiWarps) {
     // ---------------- producer ----------------
     if (lane == 0) {
+      if (p.bres) {  // the whole layer's weights, once
+        mbar_expect_tx(&bres_full, p.bres_bytes);
+        for (uint32_t o = 0; o < p.bres_bytes; o += 32768u) {
+          const uint32_t n = p.bres_bytes - o < 32768u ? p.bres_bytes - o : 32768u;
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(sBres + o)),
+              "l"(reinterpret_cast<const unsigned char*>(p.wpack) + o), "r"(n),
+              "r"(su32(&bres_full))
+              : "memory");
+        }
+      }
       int it = 0;
       for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
         const int nt = tile % p.n_ntiles, mt = tile / p.n_ntiles;
-        const int m0 = mt * 128, b0 = m0 / img_px, h0 = (m0 - b0 * img_px) / p.sp_in;
+        const int m0 = mt * m_tile, b0 = m0 / img_px, h0 = (m0 - b0 * img_px) / p.sp_in;
         for (int q = 0; q < nq; ++q, ++it) {
           const int s = it % S, cyc = it / S;
           if (cyc > 0 && !mbar_wait(&empty[s], (cyc - 1) & 1)) {
@@ -183,7 +226,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
             abort_flag = 1;
             break;
           }
-          mbar_expect_tx(&full[s], p.a_bytes + p.b_bytes);
+          mbar_expect_tx(&full[s], stage_tx);
           unsigned char* a_dst = sA + (size_t)s * p.a_bytes;
           if (p.lin) {
             // one contiguous halo per plane (the guards keep it inside the buffer)
@@ -207,16 +250,18 @@ __global__ void __launch_bounds__(kUThreads, 1)
                   "r"(su32(&full[s]))
                   : "memory");
           }
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  su32(sB + (size_t)s * p.b_bytes)),
-              "l"(p.wpack + ((size_t)nt * nq + q) * (p.b_bytes / 2)), "r"(p.b_bytes),
-              "r"(su32(&full[s]))
-              : "memory");
+          if (!p.bres)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    su32(sB + (size_t)s * p.b_bytes)),
+                "l"(p.wpack + ((size_t)nt * nq + q) * (p.b_bytes / 2)), "r"(p.b_bytes),
+                "r"(su32(&full[s]))
+                : "memory");
         }
       }
       // wait (bounded) for the last use of every stage: no copy outlives the CTA
       for (int s = 0; s < S && s < it; ++s) mbar_wait(&full[s], ((it - 1 - s) / S) & 1);
+      if (p.bres) mbar_wait(&bres_full, 0);
     }
   } else if (warp == kUEpiWarps + 1) {
     // ---------------- MMA issuer ----------------
@@ -225,7 +270,18 @@ __global__ void __launch_bounds__(kUThreads, 1)
       bool issued = false;
       const uint32_t idesc = idesc_for(p.ntile);
       const uint32_t a_lbo = p.lin ? p.plane_bytes : 2048u;
-      const uint32_t b_tap = (uint32_t)p.ntile * p.kc * 2;  // bytes of one tap's weights
+      // descriptor steps in 16-byte units
+      const uint64_t a_k = (2 * a_lbo) >> 4, b_k = (2 * p.ntile * 16) >> 4;
+      const uint64_t b_t = ((uint32_t)p.ntile * p.kc * 2) >> 4;
+      uint64_t a_t[TQ];  // halo tiles: tap (dy, dx) starts hoff + dy (s + 2) + dx pixels in
+#pragma unroll
+      for (int t = 0; t < TQ; ++t)
+        a_t[t] = TQ == 9 ? (uint64_t)(p.hoff + (t / 3 - 1) * p.sp_in + (t % 3 - 1)) : 0;
+      const int kk = p.kc / 16, R = p.R;
+      if (p.bres && !mbar_wait(&bres_full, 0)) {
+        atomicExch(p.err, 1);
+        abort_flag = 1;
+      }
       for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++tl) {
         const int buf = tl & 1, use = tl >> 1;
         if (use > 0) {
@@ -236,7 +292,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
         }
-        const uint32_t d = tmem + (uint32_t)(buf * p.ntile);
+        const uint32_t dbase = tmem + (uint32_t)(buf * acc_cols);
         for (int q = 0; q < nq; ++q, ++it) {
           const int s = it % S;
           if (!mbar_wait(&full[s], (it / S) & 1)) {
@@ -246,19 +302,25 @@ __global__ void __launch_bounds__(kUThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint64_t ad0 = desc(su32(sA + (size_t)s * p.a_bytes), a_lbo, 128);
-          const uint64_t bd0 = desc(su32(sB + (size_t)s * p.b_bytes), p.ntile * 16, 128);
-          for (int t = 0; t < tq; ++t) {
-            // halo tiles: tap (dy, dx) starts hoff + dy (s + 2) + dx pixels into the plane
-            const int off_px =
-                p.lin && p.taps == 9 ? p.hoff + (t / 3 - 1) * p.sp_in + (t % 3 - 1) : 0;
-            for (int k = 0; k < p.kc / 16; ++k) {
-              const uint64_t ad = ad0 + (uint64_t)((2 * k * a_lbo + off_px * 16) >> 4);
-              const uint64_t bd = bd0 + (uint64_t)((t * b_tap + k * 2 * p.ntile * 16) >> 4);
+          const uint64_t bd0 =
+              p.bres ? desc(su32(sBres + (size_t)q * p.b_bytes), p.ntile * 16, 128)
+                     : desc(su32(sB + (size_t)s * p.b_bytes), p.ntile * 16, 128);
+          // taps outer, subtiles inner: consecutive MMAs go to independent accumulators
+#pragma unroll
+          for (int t = 0; t < TQ; ++t) {
+            for (int k = 0; k < kk; ++k) {
+              const uint64_t ad = ad0 + a_t[t] + (uint64_t)k * a_k;
+              const uint64_t bd = bd0 + (uint64_t)t * b_t + (uint64_t)k * b_k;
               const uint32_t acc = (q > 0 || t > 0 || k > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                if (r < R)
+                  asm volatile(
+                      "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
+                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(
+                          dbase + (uint32_t)(r * p.ntile)),
+                      "l"(ad + (uint64_t)(128 * r)), "l"(bd), "r"(idesc), "r"(acc));
+              }
             }
           }
           issued = true;
@@ -274,54 +336,57 @@ __global__ void __launch_bounds__(kUThreads, 1)
       }
     }
   } else {
-    // ------ epilogue: warp w owns TMEM lanes (pixels) 32 w .. 32 w + 31 ------
+    // ------ epilogue: warp w owns TMEM lanes (pixels) 32 w .. 32 w + 31 of each subtile ------
     int tl = 0;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const int pad_in = p.sp_in != p.s_in, pad_out = p.spo != p.so;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
       const int buf = tl & 1, use = tl >> 1;
       const int nt = tile % p.n_ntiles, mt = tile / p.n_ntiles;
-      const int m = mt * 128 + warp * 32 + lane;
-      if (!mbar_wait(&acc_full[buf], use & 1)) {
+      if (!mbar_wait_sleep(&acc_full[buf], use & 1)) {
         atomicExch(p.err, 1);
         abort_flag = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // input pixel of this row; rows on the zero border (or past the end) store nothing
-      const int b = m / img_px, r = m - b * img_px;
-      const int y = r / p.sp_in - pad_in, x = r % p.sp_in - pad_in;
-      const bool valid = m < p.m_px && y >= 0 && y < p.s_in && x >= 0 && x < p.s_in;
-      for (int c0 = 0; c0 < p.ntile; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)(buf * p.ntile + c0), v);
-        if (!valid) continue;
-        const int ng = nt * p.ntile + c0;
-        const float* bs = p.bias + ng;
+      for (int r = 0; r < p.R; ++r) {
+        const int m = mt * m_tile + 128 * r + warp * 32 + lane;
+        // input pixel of this row; rows on the zero border (or past the end) store nothing
+        const int b = fdiv(m, img_px, p.div_img), rr = m - b * img_px;
+        const int yq = fdiv(rr, p.sp_in, p.div_sp);
+        const int y = yq - pad_in, x = rr - yq * p.sp_in - pad_in;
+        const bool valid = m < p.m_px && y >= 0 && y < p.s_in && x >= 0 && x < p.s_in;
+        const size_t row_out = (size_t)b * p.spo;
+        for (int c0 = 0; c0 < p.ntile; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)(buf * acc_cols + r * p.ntile + c0), v);
+          if (!valid) continue;
+          const int ng = nt * p.ntile + c0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          v[j] += __ldg(bs + j);
-          if (p.relu) v[j] = fmaxf(v[j], 0.f);
+          for (int j = 0; j < 16; ++j) {
+            v[j] += sbias[ng + j];
+            if (p.relu) v[j] = fmaxf(v[j], 0.f);
+          }
+          int ch, oy = y, ox = x;
+          if (p.up) {
+            const int qd = ng / p.cout;
+            ch = ng - qd * p.cout;
+            oy = 2 * y + (qd >> 1), ox = 2 * x + (qd & 1);
+          } else {
+            ch = ng;
+          }
+          const size_t opix = (row_out + oy + pad_out) * p.spo + ox + pad_out;
+          uint4 lo, hi;
+          lo.x = pack_bf16x2(v[0], v[1]), lo.y = pack_bf16x2(v[2], v[3]);
+          lo.z = pack_bf16x2(v[4], v[5]), lo.w = pack_bf16x2(v[6], v[7]);
+          hi.x = pack_bf16x2(v[8], v[9]), hi.y = pack_bf16x2(v[10], v[11]);
+          hi.z = pack_bf16x2(v[12], v[13]), hi.w = pack_bf16x2(v[14], v[15]);
+          // two planes of 8 channels; consecutive lanes = consecutive pixels
+          __nv_bfloat16* dst = p.out + (size_t)(p.out_goff + ch / 8) * p.out_plane +
+                               (size_t)(p.out_guard + opix) * 8;
+          *reinterpret_cast<uint4*>(dst) = lo;
+          *reinterpret_cast<uint4*>(dst + p.out_plane) = hi;
         }
-        int ch, oy = y, ox = x;
-        if (p.up) {
-          const int qd = ng / p.cout;
-          ch = ng - qd * p.cout;
-          oy = 2 * y + (qd >> 1), ox = 2 * x + (qd & 1);
-        } else {
-          ch = ng;
-        }
-        const size_t opix = ((size_t)b * p.spo + oy + pad_out) * p.spo + ox + pad_out;
-        uint4 lo, hi;
-        lo.x = pack_bf16x2(v[0], v[1]), lo.y = pack_bf16x2(v[2], v[3]);
-        lo.z = pack_bf16x2(v[4], v[5]), lo.w = pack_bf16x2(v[6], v[7]);
-        hi.x = pack_bf16x2(v[8], v[9]), hi.y = pack_bf16x2(v[10], v[11]);
-        hi.z = pack_bf16x2(v[12], v[13]), hi.w = pack_bf16x2(v[14], v[15]);
-        // two planes of 8 channels; consecutive lanes = consecutive pixels
-        __nv_bfloat16* dst =
-            p.out + (size_t)(p.out_goff + ch / 8) * p.out_plane + (size_t)(p.out_guard + opix) * 8;
-        *reinterpret_cast<uint4*>(dst) = lo;
-        *reinterpret_cast<uint4*>(dst + p.out_plane) = hi;
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -433,10 +498,11 @@ __global__ void k_uinput(const float* __restrict__ summary, const double* __rest
     const size_t HW = (size_t)H * W;
     const float* S = summary + (size_t)seg * 2 * HW;
     const double* st = stats + 4 * seg;
-    const double zs = ((double)S[(size_t)y * W + x] - st[0]) * st[1];
-    const double zt = ((double)S[HW + (size_t)y * W + x] - st[2]) * st[3];
+    // (x - mean) / (std + eps) as one FP32 FMA with the FP64 statistics rounded once
+    const float zs = fmaf(S[(size_t)y * W + x], (float)st[1], (float)(-st[0] * st[1]));
+    const float zt = fmaf(S[HW + (size_t)y * W + x], (float)st[3], (float)(-st[2] * st[3]));
     uint4 a;
-    a.x = pack_bf16x2((float)zs, (float)zt);
+    a.x = pack_bf16x2(zs, zt);
     a.y = a.z = a.w = 0u;
     const size_t o = ((size_t)pt * sp + u + 1) * sp + v + 1;
     *reinterpret_cast<uint4*>(in0 + (guard + o) * 8) = a;
@@ -642,28 +708,77 @@ int setup_conv(vimg_unet* u, const vimg_unet::Act& in, int cin_real, int taps, i
   p.ntile = std::min(n_total, 256);
   p.n_ntiles = n_total / p.ntile;
   p.n_mtiles = (p.m_px + 127) / 128;
-  p.kc = std::min(cin, 64);
-  if (p.lin)  // all taps' weights of a chunk in one stage: keep them within 48 KB
-    while (p.kc > 16 && (size_t)taps * p.ntile * p.kc * 2 > 48 * 1024) p.kc /= 2;
+  // Halo tiles: pick channels per chunk (kc), 128-row subtiles per tile (R) and
+  // stages so that two CTAs fit an SM (shared memory <= 104 KB, 2 x 2 R ntile
+  // TMEM columns <= 512), preferring larger R (less halo per row), then larger
+  // kc; else one CTA per SM.  All taps' weights of a chunk sit in one stage
+  // (<= 48 KB); the whole layer's weights stay resident when they fit.
+  struct Cfg {
+    int kc, R, S, bres;
+    size_t smem;
+  };
+  auto halo_cfg = [&](int kc, int R, size_t budget) -> Cfg {
+    Cfg f{kc, R, 0, 0, 0};
+    if ((size_t)taps * p.ntile * kc * 2 > 48 * 1024 || cin % kc) return f;
+    const int hoff = taps == 9 ? p.sp_in + 1 : 0;
+    const size_t rows = (size_t)((128 * R + 2 * hoff + 7) & ~7);
+    const size_t a = (kc / 8) * rows * 16, b = (size_t)taps * p.ntile * kc * 2;
+    const size_t wbytes = (size_t)(cin / kc) * b;
+    f.bres = p.n_ntiles == 1 && wbytes <= 160 * 1024 && wbytes + 2 * a <= budget;
+    const size_t stage = a + (f.bres ? 0 : b), fixed = f.bres ? wbytes : 0;
+    if (fixed + 2 * stage > budget) return f;
+    f.S = (int)std::min<size_t>(4, (budget - fixed) / stage);
+    f.smem = fixed + f.S * stage;
+    return f;
+  };
+  if (p.lin) {
+    // best configuration for one budget: resident weights first, then the
+    // largest R, then the largest kc
+    auto search = [&](size_t budget) {
+      Cfg best{0, 0, 0, 0, 0};
+      const int rmax = std::max(1, std::min(4, (budget == kUSmemMax ? 256 : 128) / p.ntile));
+      for (int want_bres = 1; want_bres >= 0 && !best.S; --want_bres)
+        for (int R = rmax; R >= 1 && !best.S; --R)
+          for (int kc : {64, 32, 16})
+            if (!best.S && kc <= cin) {
+              Cfg f = halo_cfg(kc, R, budget);
+              if (f.S >= 2 && f.bres >= want_bres) best = f;
+            }
+      return best;
+    };
+    Cfg best = search(104 * 1024);
+    // two CTAs per SM unless that re-streams the weights for every tile and one
+    // CTA could keep them resident
+    const Cfg one = search(kUSmemMax);
+    if (!best.S || (!best.bres && one.S && one.bres)) best = one;
+    if (!best.S) return ufail(u, VIMG_ERR_ARG, "unet: no halo configuration fits");
+    p.kc = best.kc, p.R = best.R, p.stages = best.S, p.bres = best.bres;
+  } else {
+    p.kc = std::min(cin, 64);
+    p.R = 1;
+    p.bres = 0;
+  }
   p.nkc = cin / p.kc;
+  p.n_mtiles = (p.m_px + 128 * p.R - 1) / (128 * p.R);
   if (p.lin) {
     p.in = in.p, p.in_plane = in.plane, p.in_guard = in.guard;
     p.hoff = taps == 9 ? p.sp_in + 1 : 0;
-    const int rows = (128 + 2 * p.hoff + 7) & ~7;  // 128-byte multiple
+    const int rows = (128 * p.R + 2 * p.hoff + 7) & ~7;  // 128-byte multiple
     p.plane_bytes = (uint32_t)rows * 16;
     p.a_bytes = (uint32_t)(p.kc / 8) * p.plane_bytes;
     p.b_bytes = (uint32_t)taps * p.ntile * p.kc * 2;
     if (p.hoff > in.guard || rows - p.hoff > in.guard)
       return ufail(u, VIMG_ERR_ARG, "unet: halo exceeds the guard zone");
+    p.bres_bytes = p.bres ? (uint32_t)(p.nkc * p.b_bytes) : 0u;
   } else {
     p.bh = std::min(p.s_in, 128 / p.s_in);
     p.bb = std::max(1, 128 / (p.s_in * p.s_in));
     p.a_bytes = 128u * p.kc * 2u;
     p.b_bytes = (uint32_t)p.ntile * p.kc * 2u;
+    p.bres_bytes = 0;
+    p.stages = (int)std::min<size_t>(kUMaxStages, kUSmemMax / (p.a_bytes + p.b_bytes));
   }
-  const size_t stage = (size_t)p.a_bytes + p.b_bytes;
-  const int max_st = p.lin ? 4 : kUMaxStages;  // halo stages are few and large
-  p.stages = (int)std::min<size_t>(max_st, kUSmemMax / stage);
+  const size_t stage = (size_t)p.a_bytes + (p.bres ? 0 : p.b_bytes);
   if (p.stages < 2 || cin % 16 || p.ntile % 16 || n_total % p.ntile ||
       (!p.lin && (p.bh * p.bb * p.s_in != 128 || 8 * p.s_in > 256)))
     return ufail(u, VIMG_ERR_ARG, "unet: unsupported layer shape");
@@ -673,7 +788,10 @@ int setup_conv(vimg_unet* u, const vimg_unet::Act& in, int cin_real, int taps, i
   p.spo = stored(out.level);
   p.up = up, p.cout = cout, p.relu = relu, p.err = u->dev_err;
   c.cin_real = cin_real;
-  c.smem = (size_t)p.stages * stage;
+  c.smem = p.bres_bytes + (size_t)p.stages * stage;
+  p.div_img = ((1ull << 40) + (unsigned long long)(p.sp_in * p.sp_in) - 1) / (p.sp_in * p.sp_in);
+  p.div_sp = ((1ull << 40) + (unsigned long long)p.sp_in - 1) / p.sp_in;
+  if (p.n_ntiles * p.ntile > 4 * 256) return ufail(u, VIMG_ERR_ARG, "unet: too many columns");
   if (!p.lin) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return ufail(u, VIMG_ERR_CUDA, "unet: cuTensorMapEncodeTiled unavailable");
@@ -693,8 +811,9 @@ int setup_conv(vimg_unet* u, const vimg_unet::Act& in, int cin_real, int taps, i
   }
   // resident CTAs per SM: shared memory (228 KB per SM, ~1 KB reserved per CTA)
   // and tensor memory (512 columns)
-  const int tcols = std::max(32, 2 * p.ntile);
-  const int by_smem = (int)((228 * 1024) / (c.smem + 2048));
+  int tcols = 32;
+  while (tcols < 2 * p.R * p.ntile) tcols <<= 1;
+  const int by_smem = (int)((228 * 1024) / (c.smem + 6 * 1024));  // + static smem
   const int occ = std::max(1, std::min({by_smem, 512 / tcols, 4}));
   c.grid = u->sms * occ;
   u->convs.push_back(c);
@@ -756,7 +875,9 @@ extern "C" vimg_unet* vimg_unet_create(int H, int W, int max_segments, void* str
     return bail("vimg_unet_create: no CUDA device");
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_conv_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kUSmemMax) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kUSmemMax) != cudaSuccess)
       return bail("vimg_unet_create: kernel attribute");
     attr = true;
@@ -922,10 +1043,13 @@ int vimg_unet_run_on(vimg_unet* u, const float* d_summary, int k, float* d_prob,
       vimg_unet::Conv& c = u->convs[ci++];
       ConvParams p = c.p;
       p.m_px = np * p.sp_in * p.sp_in;
-      p.n_mtiles = (p.m_px + 127) / 128;
+      p.n_mtiles = (p.m_px + 128 * p.R - 1) / (128 * p.R);
       const int grid = std::min(c.grid, p.n_mtiles * p.n_ntiles);
       conv_ev.push_back(record(u, st));
-      k_conv_tc<<<grid, kUThreads, c.smem, st>>>(c.map, p);
+      if (p.lin && p.taps == 9)
+        k_conv_tc<9><<<grid, kUThreads, c.smem, st>>>(c.map, p);
+      else
+        k_conv_tc<1><<<grid, kUThreads, c.smem, st>>>(c.map, p);
       conv_ev.push_back(record(u, st));
       UCK(cudaGetLastError(), "unet convolution");
       return VIMG_OK;
