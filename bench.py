@@ -455,7 +455,7 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     ref = ref_shifts.clone()
     # voltage traces of the scene's neuron ROIs, fused into the temporal pass
     masks = synth.roi_masks(synth.paper_scale_config(seed=1002 + dist_env()[1])).to(dev)
-    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk)
+    h = vimg.Handle(H, W, stream=stream, max_chunk=args.chunk, flags=vimg.VIDEO_SUMMARY)
     h.set_template(T)
     h.set_rois(masks)
     tr = torch.empty((n, masks.shape[0]), device=dev)
@@ -463,12 +463,21 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     ms, prof = time_variant(h, frames, (sh, corrected, summary), args.steps, args.warmup, stream,
                             traces=tr)
     h.close()
+    avg_img = torch.empty((H, W), device=dev)
+    corr_img = torch.empty((H, W), device=dev)
+    h.video_summary(avg_img, corr_img)
+    torch.cuda.synchronize()
+    roi_any = masks.any(dim=0)
     out["voltage_traces"] = {
         "value": n * args.steps * ws / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / args.steps,
         "n_rois": int(masks.shape[0]), "roi_pixels": int(masks.sum().item()),
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "correlation_image_mean_in_rois": float(corr_img[roi_any].mean()),
+        "correlation_image_mean_outside": float(corr_img[~roi_any].mean()),
         "config": "full-window FP32 path, corrected frames and summaries as the main line, plus "
-                  "the mean corrected intensity of every neuron footprint of the scene per frame",
+                  "the mean corrected intensity of every neuron footprint of the scene per frame "
+                  "(traces) and the whole-video average and local correlation images "
+                  "(stage 'downstream' holds both)",
     }
     # spiking-pixel U-Net on every segment's summary pair (Sec. III-C), random
     # weights of the architecture: alone on the 200 summary pairs, and attached

@@ -66,6 +66,8 @@ extern "C" {
                                  VIMG_PROPOSAL_CNN                               */
 #define VIMG_PROPOSAL_CNN 2   /* learned shift proposal + narrow window          */
 #define VIMG_OUT_HIGHPASS 4   /* corrected output holds the high-passed video    */
+#define VIMG_VIDEO_SUMMARY 8  /* accumulate the whole-video average and local
+                                 correlation images (vimg_video_summary)          */
 
 typedef struct vimg_handle vimg_handle;
 
@@ -149,6 +151,18 @@ typedef struct {
  * an empty ROI gives 0.  Synchronises the handle's stream (it checks the
  * overlap limit).  Returns VIMG_OK or an error. */
 int vimg_set_rois(vimg_handle* h, const uint8_t* d_masks, int n_rois);
+
+/* Whole-video summary images of the motion-corrected video V over every frame
+ * since vimg_create / vimg_reset (handle created with VIMG_VIDEO_SUMMARY): the
+ * temporal average A(x) = mean_t V(x, t) and the local correlation image C(x) =
+ * mean over the in-image 8-neighbours y of the Pearson correlation over time of
+ * V(x, .) and V(y, .) (0 for a constant trace) -- the two images VolPy derives
+ * from a whole video, which Sec. III-A and Fig. 2 compare with the per-segment
+ * summaries.  Accumulated per pixel in FP32 within a call's internal batch and in
+ * FP64 across batches.  d_average, d_correlation: device float32 [H][W] (either
+ * may be NULL); enqueued on the handle's stream.  VIMG_ERR_ARG without the flag
+ * or before the first frame. */
+int vimg_video_summary(vimg_handle* h, float* d_average, float* d_correlation);
 
 /* Same as vimg_process with the vimg_io members.  Returns k or an error. */
 int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io);
@@ -267,13 +281,14 @@ int vimg_process_batch(vimg_handle* const* hs, int k, const uint16_t* const* d_f
 /* Per-stage timing with CUDA events recorded around each of the library's
  * launches on params.stream (off by default).  Stages:
  *   0 window statistics, 1 correlation numerators, 2 peak + refinement,
- *   3 fused temporal pass, 4 learned proposal, 5 carry copies (not a kernel).
+ *   3 fused temporal pass, 4 learned proposal, 5 carry copies (not a kernel),
+ *   6 downstream outputs (voltage-trace finalize, whole-video summary sums).
  * vimg_profile_read synchronises the stream, writes the summed milliseconds
  * and the launch counts of each stage into ms[VIMG_NSTAGES] and
  * launches[VIMG_NSTAGES] (either may be NULL), and clears them when reset != 0.
  * At most 65,536 launches are recorded between reads; later ones are counted
  * but not timed.  Returns VIMG_OK or an error. */
-#define VIMG_NSTAGES 6
+#define VIMG_NSTAGES 7
 int vimg_profile_enable(vimg_handle* h, int on);
 int vimg_profile_read(vimg_handle* h, double* ms, long long* launches, int reset);
 

@@ -92,6 +92,8 @@ struct vimg_handle {
   unsigned long long* roi_acc = nullptr;      // [max_chunk][n_rois] 2^-20 fixed-point sums
   int* roi_flag = nullptr;                    // [1] a pixel in more than 4 ROIs
   vimg_unet* unet = nullptr;                  // attached U-Net stage (not owned)
+  double* vs_acc = nullptr;                   // [6][H][W] whole-video summary sums
+  long long vs_frames = 0;
   // CUDA graphs of vimg_process_batch calls led by this handle
   struct GraphEntry {
     std::vector<long long> key;
@@ -175,7 +177,7 @@ static void free_all(vimg_handle* h) {
                   h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
                   h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
                   h->fb_total, h->tround, h->as, h->bgc, h->fc, h->dev_err, h->num,
-                  h->roi_members, h->roi_count, h->roi_acc, h->roi_flag};
+                  h->roi_members, h->roi_count, h->roi_acc, h->roi_flag, h->vs_acc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
@@ -229,7 +231,7 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     fail(nullptr, VIMG_ERR_ARG, "max_chunk must be in 1..4096");
     return nullptr;
   }
-  if (p.flags & ~(VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_OUT_HIGHPASS)) {
+  if (p.flags & ~(VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_OUT_HIGHPASS | VIMG_VIDEO_SUMMARY)) {
     fail(nullptr, VIMG_ERR_ARG, "unknown flag bits");
     return nullptr;
   }
@@ -295,6 +297,10 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     if (e == cudaSuccess && bf16_tensor_map(h->tmap, h->fc, p.max_chunk, H, W) != 0)
       e = cudaErrorNotSupported;
   }
+  if (p.flags & VIMG_VIDEO_SUMMARY) {
+    ALLOC(h->vs_acc, sizeof(double) * 6 * HW);
+    if (e == cudaSuccess) e = cudaMemset(h->vs_acc, 0, sizeof(double) * 6 * HW);
+  }
   if (p.flags & VIMG_PROPOSAL_CNN) {
     ALLOC(h->cnn_p, sizeof(float) * cnn_param_count());
     ALLOC(h->cnn_b, sizeof(__nv_bfloat16) * cnn_param_count());
@@ -337,6 +343,10 @@ extern "C" int vimg_reset(vimg_handle* h) {
   if (h->sticky) return h->sticky;
   h->frames_seen = 0;
   h->carry_n = 0;
+  if (h->vs_acc) {
+    CK(cudaMemsetAsync(h->vs_acc, 0, sizeof(double) * 6 * h->H * h->W, h->st), "summary reset");
+    h->vs_frames = 0;
+  }
   return VIMG_OK;
 }
 
@@ -352,6 +362,17 @@ extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
                           h->as, h->bgc, h->st),
        "tensor-core template prep");
   h->have_template = true;
+  return VIMG_OK;
+}
+
+extern "C" int vimg_video_summary(vimg_handle* h, float* d_average, float* d_correlation) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  if (!h->vs_acc) return fail(h, VIMG_ERR_ARG, "vimg_video_summary needs VIMG_VIDEO_SUMMARY");
+  if (h->vs_frames < 1) return fail(h, VIMG_ERR_ARG, "vimg_video_summary: no frames yet");
+  CK(launch_vsum_final(h->vs_acc, h->tmpl, h->vs_frames, h->H, h->W, d_average, d_correlation,
+                       h->st),
+     "video summary launch");
   return VIMG_OK;
 }
 
@@ -576,7 +597,17 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
     CK(launch_temporal(a, h->st), "temporal launch");
     prof_end(h, ps);
   }
-  if (traces) CK(roi_finalize(h->roi_acc, h->roi_count, n, h->n_rois, io.traces, h->st), "trace launch");
+  if (traces || h->vs_acc) {
+    const int ps = prof_begin(h, 6);
+    if (traces)
+      CK(roi_finalize(h->roi_acc, h->roi_count, n, h->n_rois, io.traces, h->st), "trace launch");
+    if (h->vs_acc) {
+      CK(launch_vsum(frames, shifts, n, h->H, h->W, h->tmpl, h->vs_acc, h->st),
+         "video summary launch");
+      h->vs_frames += n;
+    }
+    prof_end(h, ps);
+  }
   const int k = advance_state(h, frames, shifts, n, h->st);
   if (k > 0 && io.prob) {
     const int rc = vimg_unet_run_on(h->unet, io.summary + (size_t)k_before * 2 * HW, k,
@@ -757,9 +788,10 @@ extern "C" int vimg_process_batch(vimg_handle* const* hs, int k, const uint16_t*
       return hv->sticky;
     }
     if (hv->dev != h->dev) return fail(h, VIMG_ERR_ARG, "vimg_process_batch: handles on different devices");
-    if (hv->p.flags & (VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN))
+    if (hv->p.flags & (VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_VIDEO_SUMMARY))
       return fail(h, VIMG_ERR_ARG,
-                  "vimg_process_batch: handles must run the full-window FP32 method");
+                  "vimg_process_batch: handles must run the full-window FP32 method "
+                  "without whole-video summaries");
     if (!hv->have_template)
       return fail(h, VIMG_ERR_NO_TEMPLATE, "vimg_process_batch: a handle has no template");
     if (ns[v] < 0 || (ns[v] > 0 && !d_frames[v]))

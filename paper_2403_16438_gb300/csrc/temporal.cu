@@ -25,6 +25,7 @@
 // is summed over the lanes of a warp per ROI and added to a 64-bit per-frame,
 // per-ROI accumulator -- integer sums, so the result does not depend on the
 // order of the atomics, on the tiling or on the chunking of the stream.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -587,6 +588,115 @@ cudaError_t roi_finalize(const unsigned long long* acc, const int* counts, int n
   const long long want = (total + 255) / 256;
   const int blocks = want < 4096 ? (int)want : 4096;
   k_roi_finalize<<<blocks, 256, 0, st>>>(acc, counts, total, n_rois, traces);
+  return cudaGetLastError();
+}
+
+// ---- whole-video summary images -------------------------------------------------
+// VolPy's temporal average and local correlation images of V (compared in Sec.
+// III-A, Fig. 2).  Per pixel, over the launch's frames: sums of d, d^2 and of d
+// times its E, S, SE and SW neighbours (each unordered 8-neighbour pair once),
+// d = V - T (any per-pixel constant gives the same correlation; the template
+// keeps d small so that FP32 sums over one launch stay accurate), then added to
+// FP64 accumulators [6][H][W].  One CTA owns a 32 x 8 output tile and walks the
+// frames; V of the tile plus its E/S/SW halo is resampled into shared memory.
+constexpr int kVsX = 32, kVsY = 8;
+
+__global__ void __launch_bounds__(kVsX * kVsY) k_vsum(const uint16_t* __restrict__ frames,
+                                                      const float* __restrict__ shifts, int nf,
+                                                      int H, int W, const float* __restrict__ ref,
+                                                      double* __restrict__ acc) {
+  __shared__ float vs[kVsY + 1][kVsX + 2];  // rows y0..y0+8, columns x0-1..x0+32
+  const int tx = threadIdx.x % kVsX, ty = threadIdx.x / kVsX;
+  const int x0 = blockIdx.x * kVsX, y0 = blockIdx.y * kVsY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool in = x < W && y < H;
+  const bool hasE = x + 1 < W, hasS = y + 1 < H, hasSW = hasS && x >= 1, hasSE = hasS && hasE;
+  float s1 = 0.f, s2 = 0.f, pe = 0.f, ps = 0.f, pse = 0.f, psw = 0.f;
+  constexpr int nv = (kVsY + 1) * (kVsX + 2);
+  for (int f = 0; f < nf; ++f) {
+    const uint16_t* F = frames + (size_t)f * H * W;
+    const Split sy = split_shift(__ldg(shifts + 2 * f)), sx = split_shift(__ldg(shifts + 2 * f + 1));
+    __syncthreads();  // the previous frame's values are consumed
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      const int ry = i / (kVsX + 2), rx = i - ry * (kVsX + 2);
+      const int yy = y0 + ry, xx = x0 - 1 + rx;
+      float v = 0.f;
+      if (yy < H && xx >= 0 && xx < W)
+        v = bilin(F, H, W, yy, xx, sy, sx) - __ldg(ref + (size_t)yy * W + xx);
+      vs[ry][rx] = v;
+    }
+    __syncthreads();
+    const float d = vs[ty][tx + 1];
+    s1 += d;
+    s2 = fmaf(d, d, s2);
+    pe = fmaf(d, vs[ty][tx + 2], pe);
+    ps = fmaf(d, vs[ty + 1][tx + 1], ps);
+    pse = fmaf(d, vs[ty + 1][tx + 2], pse);
+    psw = fmaf(d, vs[ty + 1][tx], psw);
+  }
+  if (!in) return;
+  const size_t HW = (size_t)H * W, o = (size_t)y * W + x;
+  acc[o] += s1;
+  acc[HW + o] += s2;
+  if (hasE) acc[2 * HW + o] += pe;
+  if (hasS) acc[3 * HW + o] += ps;
+  if (hasSE) acc[4 * HW + o] += pse;
+  if (hasSW) acc[5 * HW + o] += psw;
+}
+
+// A(x) = T(x) + S_d / n; C(x) = mean over in-image 8-neighbours of the Pearson
+// correlation (0 where either trace is constant), FP64.
+__global__ void k_vsum_final(const double* __restrict__ acc, const float* __restrict__ ref,
+                             long long n, int H, int W, float* __restrict__ avg,
+                             float* __restrict__ corr) {
+  const size_t HW = (size_t)H * W;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < HW;
+       o += (size_t)gridDim.x * blockDim.x) {
+    const int y = (int)(o / W), x = (int)(o % W);
+    const double dn = (double)n;
+    auto var = [&](size_t q) {
+      const double v = acc[HW + q] - acc[q] * acc[q] / dn;
+      return v > 1e-9 * acc[HW + q] ? v : 0.0;  // constant traces (up to FP32 rounding)
+    };
+    const double vx = var(o);
+    double tot = 0.0;
+    int cnt = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dy && !dx) continue;
+        const int yy = y + dy, xx = x + dx;
+        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+        ++cnt;
+        const size_t q = (size_t)yy * W + xx;
+        // the pair's product sum is stored at its upper (or, in a row, left)
+        // pixel: slot 2 = E, 3 = S, 4 = SE, 5 = SW of that pixel
+        const bool here = dy > 0 || (dy == 0 && dx > 0);
+        const size_t at = here ? o : q;
+        const int slot = dy == 0 ? 2 : (dx == 0 ? 3 : (dx == dy ? 4 : 5));
+        const double vy = var(q);
+        if (vx > 0.0 && vy > 0.0) {
+          const double cov = acc[slot * HW + at] - acc[o] * acc[q] / dn;
+          tot += cov / sqrt(vx * vy);
+        }
+      }
+    if (avg) avg[o] = (float)((double)__ldg(ref + o) + acc[o] / dn);
+    if (corr) corr[o] = cnt ? (float)(tot / cnt) : 0.f;
+  }
+}
+
+cudaError_t launch_vsum(const uint16_t* frames, const float* shifts, int nf, int H, int W,
+                        const float* ref, double* acc, cudaStream_t st) {
+  if (nf <= 0) return cudaSuccess;
+  dim3 grid((W + kVsX - 1) / kVsX, (H + kVsY - 1) / kVsY);
+  k_vsum<<<grid, kVsX * kVsY, 0, st>>>(frames, shifts, nf, H, W, ref, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vsum_final(const double* acc, const float* ref, long long n, int H, int W,
+                              float* avg, float* corr, cudaStream_t st) {
+  const size_t HW = (size_t)H * W;
+  const int blocks = (int)std::min<size_t>((HW + 255) / 256, 4096);
+  k_vsum_final<<<blocks, 256, 0, st>>>(acc, ref, n, H, W, avg, corr);
   return cudaGetLastError();
 }
 

@@ -188,6 +188,12 @@ cudaError_t roi_build(const uint8_t* masks, int n_rois, int H, int W,
 cudaError_t roi_finalize(const unsigned long long* acc, const int* counts, int nf, int n_rois,
                          float* traces, cudaStream_t st);
 constexpr double kRoiFix = 1048576.0;  // 2^20: fixed-point scale of the trace sums
+// Whole-video summary images: per-pixel FP64 sums [6][H][W] of d = V - T, d^2 and
+// d times the E, S, SE, SW neighbours over nf frames; and the images from them.
+cudaError_t launch_vsum(const uint16_t* frames, const float* shifts, int nf, int H, int W,
+                        const float* ref, double* acc, cudaStream_t st);
+cudaError_t launch_vsum_final(const double* acc, const float* ref, long long n, int H, int W,
+                              float* avg, float* corr, cudaStream_t st);
 
 }  // namespace vimg
 

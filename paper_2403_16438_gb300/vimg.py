@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvimg.so")
 
 OK = 0
 ERR_ARG, ERR_NO_TEMPLATE, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_SIZE = -1, -2, -3, -4, -5, -6
-CORR_BF16, PROPOSAL_CNN, OUT_HIGHPASS = 1, 2, 4
+CORR_BF16, PROPOSAL_CNN, OUT_HIGHPASS, VIDEO_SUMMARY = 1, 2, 4, 8
 
 
 class Params(ctypes.Structure):
@@ -68,9 +68,10 @@ EXPORTS = [
     "vimg_unet_param_count", "vimg_unet_layers", "vimg_unet_create", "vimg_unet_destroy",
     "vimg_unet_last_error", "vimg_unet_load", "vimg_unet_run", "vimg_unet_synchronize",
     "vimg_unet_profile", "vimg_unet_profile_read", "vimg_attach_unet", "vimg_unet_activation",
+    "vimg_video_summary",
 ]
-NSTAGES = 6
-STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy"]
+NSTAGES = 7
+STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy", "downstream"]
 
 
 def _load():
@@ -86,6 +87,8 @@ def _load():
     L.vimg_destroy.restype = None
     L.vimg_set_template.argtypes = [vp, vp]
     L.vimg_set_template.restype = i
+    L.vimg_video_summary.argtypes = [vp, vp, vp]
+    L.vimg_video_summary.restype = i
     L.vimg_set_rois.argtypes = [vp, vp, i]
     L.vimg_set_rois.restype = i
     L.vimg_unet_param_count.argtypes = []
@@ -245,6 +248,11 @@ class Handle:
         m = masks.to(torch.uint8).contiguous()
         self._check(lib.vimg_set_rois(self._h, _ptr(m), m.shape[0]))
         self.n_rois = m.shape[0]
+
+    def video_summary(self, average=None, correlation=None):
+        """Whole-video average and local correlation images (handle created with
+        flags=VIDEO_SUMMARY) into cuda float32 [H, W] tensors."""
+        self._check(lib.vimg_video_summary(self._h, _ptr(average), _ptr(correlation)))
 
     def attach_unet(self, unet):
         """Attach a Unet of the same size (None detaches): process(prob=...)
