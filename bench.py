@@ -542,6 +542,26 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
                   "every 32 px (225 per segment), 8 segments per internal pass; random weights "
                   "of the U-Net reading (16..256 channels, 4 pooling steps)",
     }
+    # footprint reconstruction (Sec. III-D) on planted probability maps of the
+    # scene (the random-weight U-Net's maps carry no neurons): 200 segments
+    pm = synth.planted_prob_maps(synth.paper_scale_config(seed=1002 + dist_env()[1]), k_max,
+                                 seed=3).to(dev)
+    sg = vimg.Segmenter(H, W, k_max, stream=stream)
+    for _ in range(args.warmup):
+        sg.run(pm, max_neurons=512)
+    t0 = time.time()
+    reps = max(1, args.steps)
+    for _ in range(reps):
+        foot, actv, _, nreg = sg.run(pm, max_neurons=512)
+    t_seg = (time.time() - t0) / reps
+    sg.close()
+    out["footprints"] = {
+        "seconds_per_video": t_seg, "segments": k_max, "regions": nreg,
+        "neurons": int(foot.shape[0]), "scene_neurons": int(masks.shape[0]),
+        "config": "planted probability maps (scene footprints at 0.6-0.95 when a neuron spikes "
+                  "in the segment, p = 0.4; vessels and specks to be removed; background "
+                  "< 0.35); host-timed, synchronous call",
+    }
     # BF16 tensor-core correlation (tcgen05), FP32 accumulation
     h = vimg.Handle(H, W, stream=stream, max_chunk=args.bf16_chunk, flags=vimg.CORR_BF16)
     h.set_template(T)

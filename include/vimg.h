@@ -386,6 +386,34 @@ int vimg_unet_profile_read(vimg_unet* u, double* conv_ms, double* total_ms,
 int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_patches, int* side,
                          int* channels);
 
+/* ---- footprint reconstruction (Sec. III-D) -------------------------------------
+ * From per-segment spiking-probability maps p_i (e.g. vimg_io.prob): binary masks
+ * p_i > 0.5; 8-connected components kept if 20 <= area <= 1000 px, eccentricity
+ * (pixel-centre covariance) <= 0.95 and concaveness 1 - area / convex-hull area
+ * (hull of the pixel squares) <= 0.3; b = OR over segments; each 8-connected
+ * component of b ("region", at most 16,000 px) is factorised by NMF, P ~ F A
+ * (Eq. 3; rows = the region's pixels, columns = segments), with N = the number
+ * of clusters of its kept blobs (a blob joins the first cluster whose first blob
+ * it overlaps with IoU >= 1/2; at most 32) and 100 multiplicative updates from
+ * the clusters' union masks.  The constants are readings: the paper names the
+ * criteria, not their values.  Neurons are numbered by region (smallest pixel
+ * index), then cluster. */
+typedef struct vimg_segmenter vimg_segmenter;
+
+/* Workspace for H x W maps and up to max_segments of them; NULL on failure. */
+vimg_segmenter* vimg_segmenter_create(int H, int W, int max_segments, void* stream);
+void vimg_segmenter_destroy(vimg_segmenter* s);
+const char* vimg_segmenter_last_error(const vimg_segmenter* s);
+
+/* d_prob: device float32 [K][H][W].  Outputs (device, any may be NULL):
+ * d_footprints float32 [max_neurons][H][W] (F columns, 0 outside the region),
+ * d_activity float32 [max_neurons][K] (rows of A), d_region_map int32 [H][W]
+ * (region of each pixel of b, -1 elsewhere); *n_regions (host) = regions.
+ * Synchronous.  Returns the number of neurons found (only the first
+ * max_neurons are written) or an error code. */
+int vimg_segment(vimg_segmenter* s, const float* d_prob, int K, float* d_footprints,
+                 float* d_activity, int max_neurons, int* d_region_map, int* n_regions);
+
 /* Attaches a U-Net of the same H x W to a handle (NULL detaches); the handle
  * does not own it.  vimg_process_io then fills vimg_io.prob on the handle's
  * stream. */

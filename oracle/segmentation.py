@@ -18,10 +18,12 @@ The paper gives the steps but not their constants; readings taken here:
     order, then by smallest pixel index) are clustered greedily: a blob joins
     the first cluster whose first blob it overlaps with IoU >= 1/2 (the exact
     integer test 2 |a & b| >= |a | b|), else it starts a new cluster; N = the
-    number of clusters (neurons that spike in different segments separate even
-    where their footprints touch).  F column j starts as the indicator of the
+    number of clusters, at most 32 (a blob that would open a 33rd is ignored;
+    neurons that spike in different segments separate even where their
+    footprints touch).  F column j starts as the indicator of the
     union of cluster j's blobs, A[j][i] as the mean of p_i over that union,
     floored at 1e-6;
+  * regions larger than 16,000 pixels are not factorised (no neurons);
   * NMF by Lee & Seung's multiplicative updates for the Frobenius loss,
     100 iterations of A <- A * (F'P) / (F'F A + 1e-9), then
     F <- F * (P A') / (F A A' + 1e-9), over the region's pixels (rows of P,
@@ -43,6 +45,8 @@ AREA_MIN, AREA_MAX = 20, 1000
 ECC_MAX = 0.95
 CONCAVE_MAX = 0.3
 NMF_ITERS = 100
+MAX_N = 32
+MAX_REGION = 16000
 NMF_EPS = 1e-9
 A_FLOOR = 1e-6
 EIGHT = np.ones((3, 3), bool)
@@ -153,6 +157,8 @@ def footprints(prob):
             b[c] = True
     out = []
     for region in components(b.reshape(H, W)):
+        if region.size > MAX_REGION:
+            continue
         rset = set(region.tolist())
         blobs = [set(c.tolist()) for i in range(K) for c in kept[i] if int(c[0]) in rset]
         reps, unions = [], []
@@ -162,8 +168,9 @@ def footprints(prob):
                     unions[j] |= bl
                     break
             else:
-                reps.append(bl)
-                unions.append(set(bl))
+                if len(reps) < MAX_N:
+                    reps.append(bl)
+                    unions.append(set(bl))
         N = len(reps)
         pos = {p: r for r, p in enumerate(region)}
         P = prob.reshape(K, H * W)[:, region].T  # [M][K]

@@ -409,3 +409,29 @@ def summary_pair(cfg: VideoConfig, k: int, seed: int = 0) -> torch.Tensor:
                 t += 60.0 * fp
         out[i, 1] = t
     return out.to(torch.float32)
+
+
+def planted_prob_maps(cfg: VideoConfig, K: int, seed: int = 0) -> torch.Tensor:
+    """[K][H][W] float32 stand-ins for U-Net probability maps: a background of
+    uniform values below 0.35; in each segment every neuron of the scene spikes
+    with probability 0.4 and then shows its footprint interior at 0.6-0.95; a
+    few thin vessel-like lines and 2x2 specks appear above 0.5 as well (shapes
+    the cleanup has to remove)."""
+    g = torch.Generator().manual_seed(seed)
+    masks = roi_masks(cfg).to(torch.float32)
+    H, W = cfg.H, cfg.W
+    out = torch.rand((K, H, W), generator=g) * 0.35
+    for i in range(K):
+        for m in masks:
+            if torch.rand(1, generator=g).item() < 0.4:
+                level = 0.6 + 0.35 * torch.rand(1, generator=g).item()
+                out[i] = torch.maximum(out[i], m * level)
+        if torch.rand(1, generator=g).item() < 0.5:  # a vessel: 1 px wide, 40 px long
+            y = int(torch.randint(2, H - 2, (1,), generator=g))
+            x = int(torch.randint(0, max(1, W - 40), (1,), generator=g))
+            out[i, y, x:x + 40] = 0.9
+        for _ in range(2):  # specks
+            y = int(torch.randint(0, H - 2, (1,), generator=g))
+            x = int(torch.randint(0, W - 2, (1,), generator=g))
+            out[i, y:y + 2, x:x + 2] = 0.8
+    return out

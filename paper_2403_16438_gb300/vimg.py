@@ -68,7 +68,8 @@ EXPORTS = [
     "vimg_unet_param_count", "vimg_unet_layers", "vimg_unet_create", "vimg_unet_destroy",
     "vimg_unet_last_error", "vimg_unet_load", "vimg_unet_run", "vimg_unet_synchronize",
     "vimg_unet_profile", "vimg_unet_profile_read", "vimg_attach_unet", "vimg_unet_activation",
-    "vimg_video_summary",
+    "vimg_video_summary", "vimg_segmenter_create", "vimg_segmenter_destroy",
+    "vimg_segmenter_last_error", "vimg_segment",
 ]
 NSTAGES = 7
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy", "downstream"]
@@ -87,6 +88,14 @@ def _load():
     L.vimg_destroy.restype = None
     L.vimg_set_template.argtypes = [vp, vp]
     L.vimg_set_template.restype = i
+    L.vimg_segmenter_create.argtypes = [i, i, i, vp]
+    L.vimg_segmenter_create.restype = vp
+    L.vimg_segmenter_destroy.argtypes = [vp]
+    L.vimg_segmenter_destroy.restype = None
+    L.vimg_segmenter_last_error.argtypes = [vp]
+    L.vimg_segmenter_last_error.restype = ctypes.c_char_p
+    L.vimg_segment.argtypes = [vp, vp, i, vp, vp, i, vp, P(i)]
+    L.vimg_segment.restype = i
     L.vimg_video_summary.argtypes = [vp, vp, vp]
     L.vimg_video_summary.restype = i
     L.vimg_set_rois.argtypes = [vp, vp, i]
@@ -421,3 +430,43 @@ class Unet:
         self._check(lib.vimg_unet_profile_read(self._u, ctypes.byref(a), ctypes.byref(b),
                                                ctypes.byref(c), 1 if reset else 0))
         return a.value, b.value, c.value
+
+
+class Segmenter:
+    """Footprint reconstruction from probability maps (see vimg_segment)."""
+
+    def __init__(self, H, W, max_segments, stream=None):
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.H, self.W = H, W
+        self._s = lib.vimg_segmenter_create(H, W, max_segments,
+                                            ctypes.c_void_p(stream.cuda_stream))
+        if not self._s:
+            raise VimgError(ERR_OOM, "vimg_segmenter_create failed")
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib.vimg_segmenter_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, prob: torch.Tensor, max_neurons: int = 256):
+        """prob: cuda float32 [K, H, W] -> (footprints [n, H, W], activity [n, K],
+        region map int32 [H, W], number of regions)."""
+        assert prob.is_cuda and prob.dtype == torch.float32 and prob.is_contiguous()
+        K = prob.shape[0]
+        foot = torch.zeros((max_neurons, self.H, self.W), device=prob.device)
+        act = torch.zeros((max_neurons, K), device=prob.device)
+        rmap = torch.empty((self.H, self.W), device=prob.device, dtype=torch.int32)
+        nreg = ctypes.c_int()
+        n = lib.vimg_segment(self._s, _ptr(prob), K, _ptr(foot), _ptr(act), max_neurons,
+                             _ptr(rmap), ctypes.byref(nreg))
+        if n < 0:
+            raise VimgError(n, lib.vimg_segmenter_last_error(self._s).decode())
+        m = min(n, max_neurons)
+        return foot[:m], act[:m], rmap, nreg.value
