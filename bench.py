@@ -462,11 +462,11 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     sh = torch.empty_like(ref)
     ms, prof = time_variant(h, frames, (sh, corrected, summary), args.steps, args.warmup, stream,
                             traces=tr)
-    h.close()
     avg_img = torch.empty((H, W), device=dev)
     corr_img = torch.empty((H, W), device=dev)
     h.video_summary(avg_img, corr_img)
     torch.cuda.synchronize()
+    h.close()
     roi_any = masks.any(dim=0)
     out["voltage_traces"] = {
         "value": n * args.steps * ws / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / args.steps,

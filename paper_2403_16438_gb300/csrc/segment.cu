@@ -213,9 +213,10 @@ __global__ void k_blob_shape(int* __restrict__ list, const int* __restrict__ off
     }
     int* a = list + off[c];
     warp_sort(a, n);
+    const int base = (int)((a[0] / HW) * HW);  // the map's offset, same for every pixel
     long long sy = 0, sx = 0, syy = 0, sxx = 0, sxy = 0;
     for (int i = lane; i < n; i += 32) {
-      const int p = (int)(a[i] % HW), y = p / W, x = p - y * W;
+      const int p = a[i] - base, y = p / W, x = p - y * W;
       sy += y, sx += x, syy += (long long)y * y, sxx += (long long)x * x, sxy += (long long)x * y;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -243,10 +244,10 @@ __global__ void k_blob_shape(int* __restrict__ list, const int* __restrict__ off
     long long* hull = pts + 4 * kAreaMax;
     int npt = 0;
     for (int i = 0; i < n;) {
-      const int p0 = (int)(a[i] % HW), y = p0 / W, lo = p0 - y * W;
+      const int p0 = a[i] - base, y = p0 / W, lo = p0 - y * W;
       int j = i;
-      while (j + 1 < n && (int)(a[j + 1] % HW) / W == y) ++j;
-      const int hi = (int)(a[j] % HW) - y * W + 1;
+      while (j + 1 < n && (a[j + 1] - base) / W == y) ++j;
+      const int hi = a[j] - base - y * W + 1;
       pts[npt++] = ((long long)lo << 32) | (unsigned)y;
       pts[npt++] = ((long long)lo << 32) | (unsigned)(y + 1);
       pts[npt++] = ((long long)hi << 32) | (unsigned)y;
@@ -317,11 +318,13 @@ __global__ void k_blob_scatter(const int* __restrict__ breg, int n_comp, const i
     if (breg[c] >= 0) rblobs[roff[breg[c]] + atomicAdd(cursor + breg[c], 1)] = c;
 }
 
-// |a & b| of two ascending pixel lists (segment-local indices).
+// |a & b| of two ascending pixel lists of single maps (global indices; each
+// list's map offset is removed once, not per element).
 __device__ int inter_count(const int* a, int na, const int* b, int nb, long long HW) {
+  const int ba = (int)((a[0] / HW) * HW), bb = (int)((b[0] / HW) * HW);
   int i = 0, j = 0, k = 0;
   while (i < na && j < nb) {
-    const long long x = a[i] % HW, y = b[j] % HW;
+    const int x = a[i] - ba, y = b[j] - bb;
     if (x == y) ++k, ++i, ++j;
     else if (x < y) ++i;
     else ++j;
@@ -413,7 +416,8 @@ __global__ void __launch_bounds__(256) k_region_nmf(
   for (int q = 0; q < rcnt[r]; ++q) {
     const int c = rblobs[roff[r] + q], j = bclu[c];
     if (j < 0) continue;
-    for (int i = tid; i < cnt[c]; i += nt) F[(long long)row_of(pix, M, (int)(list[off[c] + i] % HW)) * N + j] = 1.f;
+    const int base = (int)((list[off[c]] / HW) * HW);
+    for (int i = tid; i < cnt[c]; i += nt) F[(long long)row_of(pix, M, list[off[c] + i] - base) * N + j] = 1.f;
     __syncthreads();
   }
   if (tid < N) {

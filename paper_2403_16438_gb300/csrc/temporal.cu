@@ -598,14 +598,16 @@ cudaError_t roi_finalize(const unsigned long long* acc, const int* counts, int n
 // d = V - T (any per-pixel constant gives the same correlation; the template
 // keeps d small so that FP32 sums over one launch stay accurate), then added to
 // FP64 accumulators [6][H][W].  One CTA owns a 32 x 8 output tile and walks the
-// frames; V of the tile plus its E/S/SW halo is resampled into shared memory.
+// frames, 8 at a time: V of the tile plus its E/S/SW halo for 8 frames is
+// resampled into shared memory in one pass, so those loads overlap.
 constexpr int kVsX = 32, kVsY = 8;
+constexpr int kVsF = 8;  // frames resampled per shared-memory pass (loads in flight together)
 
 __global__ void __launch_bounds__(kVsX * kVsY) k_vsum(const uint16_t* __restrict__ frames,
                                                       const float* __restrict__ shifts, int nf,
                                                       int H, int W, const float* __restrict__ ref,
                                                       double* __restrict__ acc) {
-  __shared__ float vs[kVsY + 1][kVsX + 2];  // rows y0..y0+8, columns x0-1..x0+32
+  __shared__ float vs[kVsF][kVsY + 1][kVsX + 2];  // rows y0..y0+8, columns x0-1..x0+32
   const int tx = threadIdx.x % kVsX, ty = threadIdx.x / kVsX;
   const int x0 = blockIdx.x * kVsX, y0 = blockIdx.y * kVsY;
   const int x = x0 + tx, y = y0 + ty;
@@ -613,26 +615,30 @@ __global__ void __launch_bounds__(kVsX * kVsY) k_vsum(const uint16_t* __restrict
   const bool hasE = x + 1 < W, hasS = y + 1 < H, hasSW = hasS && x >= 1, hasSE = hasS && hasE;
   float s1 = 0.f, s2 = 0.f, pe = 0.f, ps = 0.f, pse = 0.f, psw = 0.f;
   constexpr int nv = (kVsY + 1) * (kVsX + 2);
-  for (int f = 0; f < nf; ++f) {
-    const uint16_t* F = frames + (size_t)f * H * W;
-    const Split sy = split_shift(__ldg(shifts + 2 * f)), sx = split_shift(__ldg(shifts + 2 * f + 1));
-    __syncthreads();  // the previous frame's values are consumed
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-      const int ry = i / (kVsX + 2), rx = i - ry * (kVsX + 2);
-      const int yy = y0 + ry, xx = x0 - 1 + rx;
+  for (int f0 = 0; f0 < nf; f0 += kVsF) {
+    const int nb = min(kVsF, nf - f0);
+    __syncthreads();  // the previous pass's values are consumed
+    for (int i = threadIdx.x; i < nb * nv; i += blockDim.x) {
+      const int fk = i / nv, j = i - fk * nv;
+      const int ry = j / (kVsX + 2), rx = j - ry * (kVsX + 2);
+      const int yy = y0 + ry, xx = x0 - 1 + rx, f = f0 + fk;
       float v = 0.f;
-      if (yy < H && xx >= 0 && xx < W)
-        v = bilin(F, H, W, yy, xx, sy, sx) - __ldg(ref + (size_t)yy * W + xx);
-      vs[ry][rx] = v;
+      if (yy < H && xx >= 0 && xx < W) {
+        const Split sy = split_shift(__ldg(shifts + 2 * f)), sx = split_shift(__ldg(shifts + 2 * f + 1));
+        v = bilin(frames + (size_t)f * H * W, H, W, yy, xx, sy, sx) - __ldg(ref + (size_t)yy * W + xx);
+      }
+      vs[fk][ry][rx] = v;
     }
     __syncthreads();
-    const float d = vs[ty][tx + 1];
-    s1 += d;
-    s2 = fmaf(d, d, s2);
-    pe = fmaf(d, vs[ty][tx + 2], pe);
-    ps = fmaf(d, vs[ty + 1][tx + 1], ps);
-    pse = fmaf(d, vs[ty + 1][tx + 2], pse);
-    psw = fmaf(d, vs[ty + 1][tx], psw);
+    for (int fk = 0; fk < nb; ++fk) {
+      const float d = vs[fk][ty][tx + 1];
+      s1 += d;
+      s2 = fmaf(d, d, s2);
+      pe = fmaf(d, vs[fk][ty][tx + 2], pe);
+      ps = fmaf(d, vs[fk][ty + 1][tx + 1], ps);
+      pse = fmaf(d, vs[fk][ty + 1][tx + 2], pse);
+      psw = fmaf(d, vs[fk][ty + 1][tx], psw);
+    }
   }
   if (!in) return;
   const size_t HW = (size_t)H * W, o = (size_t)y * W + x;
