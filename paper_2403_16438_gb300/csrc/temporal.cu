@@ -608,6 +608,10 @@ __global__ void __launch_bounds__(kVsX * kVsY) k_vsum(const uint16_t* __restrict
                                                       int H, int W, const float* __restrict__ ref,
                                                       double* __restrict__ acc) {
   __shared__ float vs[kVsF][kVsY + 1][kVsX + 2];  // rows y0..y0+8, columns x0-1..x0+32
+  __shared__ float rt[kVsY + 1][kVsX + 2];        // template over the same window
+  __shared__ int si[kVsF][2];                      // integer parts of the shifts
+  __shared__ float sf[kVsF][2];                    // fractional parts
+  __shared__ int inside[kVsF];                     // source window inside the image
   const int tx = threadIdx.x % kVsX, ty = threadIdx.x / kVsX;
   const int x0 = blockIdx.x * kVsX, y0 = blockIdx.y * kVsY;
   const int x = x0 + tx, y = y0 + ty;
@@ -615,17 +619,41 @@ __global__ void __launch_bounds__(kVsX * kVsY) k_vsum(const uint16_t* __restrict
   const bool hasE = x + 1 < W, hasS = y + 1 < H, hasSW = hasS && x >= 1, hasSE = hasS && hasE;
   float s1 = 0.f, s2 = 0.f, pe = 0.f, ps = 0.f, pse = 0.f, psw = 0.f;
   constexpr int nv = (kVsY + 1) * (kVsX + 2);
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const int ry = j / (kVsX + 2), rx = j - ry * (kVsX + 2);
+    const int yy = y0 + ry, xx = x0 - 1 + rx;
+    rt[ry][rx] = (yy < H && xx >= 0 && xx < W) ? __ldg(ref + (size_t)yy * W + xx) : 0.f;
+  }
   for (int f0 = 0; f0 < nf; f0 += kVsF) {
     const int nb = min(kVsF, nf - f0);
     __syncthreads();  // the previous pass's values are consumed
+    if (threadIdx.x < nb) {
+      const Split a = split_shift(__ldg(shifts + 2 * (f0 + threadIdx.x)));
+      const Split b = split_shift(__ldg(shifts + 2 * (f0 + threadIdx.x) + 1));
+      si[threadIdx.x][0] = a.i, si[threadIdx.x][1] = b.i;
+      sf[threadIdx.x][0] = a.f, sf[threadIdx.x][1] = b.f;
+      // rows y0 + a.i .. y0 + 9 + a.i and columns x0 - 1 + b.i .. x0 + 34 + b.i in the image
+      inside[threadIdx.x] = y0 + a.i >= 0 && y0 + kVsY + 1 + a.i < H && x0 - 1 + b.i >= 0 &&
+                            x0 + kVsX + 1 + b.i < W;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < nb * nv; i += blockDim.x) {
       const int fk = i / nv, j = i - fk * nv;
       const int ry = j / (kVsX + 2), rx = j - ry * (kVsX + 2);
-      const int yy = y0 + ry, xx = x0 - 1 + rx, f = f0 + fk;
+      const int yy = y0 + ry, xx = x0 - 1 + rx;
       float v = 0.f;
       if (yy < H && xx >= 0 && xx < W) {
-        const Split sy = split_shift(__ldg(shifts + 2 * f)), sx = split_shift(__ldg(shifts + 2 * f + 1));
-        v = bilin(frames + (size_t)f * H * W, H, W, yy, xx, sy, sx) - __ldg(ref + (size_t)yy * W + xx);
+        const uint16_t* F = frames + (size_t)(f0 + fk) * H * W;
+        if (inside[fk]) {  // no clamping: the four taps are (yy + iy, xx + ix) and right/below
+          const uint16_t* q = F + (size_t)(yy + si[fk][0]) * W + xx + si[fk][1];
+          const float a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + W), d = __ldg(q + W + 1);
+          const float wx = sf[fk][1], wy = sf[fk][0];
+          const float top = fmaf(wx, b - a, a), bot = fmaf(wx, d - c, c);
+          v = fmaf(wy, bot - top, top);
+        } else {
+          v = bilin(F, H, W, yy, xx, Split{si[fk][0], sf[fk][0]}, Split{si[fk][1], sf[fk][1]});
+        }
+        v -= rt[ry][rx];
       }
       vs[fk][ry][rx] = v;
     }
