@@ -637,6 +637,9 @@ __global__ void __launch_bounds__(kVsX * kVsY) k_vsum(const uint16_t* __restrict
                             x0 + kVsX + 1 + b.i < W;
     }
     __syncthreads();
+    // unrolled so that several values' taps are in flight at once (the loop is
+    // bound by L2 latency, not by arithmetic)
+#pragma unroll 5
     for (int i = threadIdx.x; i < nb * nv; i += blockDim.x) {
       const int fk = i / nv, j = i - fk * nv;
       const int ry = j / (kVsX + 2), rx = j - ry * (kVsX + 2);
