@@ -95,7 +95,8 @@ size_t weight_count(const LayerDef& L) {
 // 128 + 2 (s + 2) + 2 pixels per plane, fetched by one bulk copy, serves all
 // nine taps ("halo" tiles, shifted descriptors).  The 8 and 4 px levels are
 // stored dense; their tiles take one TMA box per tap and plane (im2col boxes
-// with zero fill at the image border), which costs less there than a border.
+// with zero fill at the image border): a border would add 56 % and 125 % rows
+// there (measured: the 8 px level padded is 13 % slower).
 constexpr int kUPadLevels = 3;
 constexpr int kUGuard = 640;  // guard pixels before and after each padded plane
 
@@ -708,11 +709,10 @@ int setup_conv(vimg_unet* u, const vimg_unet::Act& in, int cin_real, int taps, i
   p.ntile = std::min(n_total, 256);
   p.n_ntiles = n_total / p.ntile;
   p.n_mtiles = (p.m_px + 127) / 128;
-  // Halo tiles: pick channels per chunk (kc), 128-row subtiles per tile (R) and
-  // stages so that two CTAs fit an SM (shared memory <= 104 KB, 2 x 2 R ntile
-  // TMEM columns <= 512), preferring larger R (less halo per row), then larger
-  // kc; else one CTA per SM.  All taps' weights of a chunk sit in one stage
-  // (<= 48 KB); the whole layer's weights stay resident when they fit.
+  // Halo tiles: channels per chunk (kc), 128-row subtiles per tile (R) and stages,
+  // for two CTAs per SM (shared memory <= 104 KB, 2 x 2 R ntile TMEM columns
+  // <= 512) or one; all taps' weights of a chunk sit in one stage (<= 48 KB),
+  // the whole layer's weights stay resident when they fit.
   struct Cfg {
     int kc, R, S, bres;
     size_t smem;
@@ -732,25 +732,26 @@ int setup_conv(vimg_unet* u, const vimg_unet::Act& in, int cin_real, int taps, i
     return f;
   };
   if (p.lin) {
-    // best configuration for one budget: resident weights first, then the
-    // largest R, then the largest kc
-    auto search = [&](size_t budget) {
-      Cfg best{0, 0, 0, 0, 0};
+    // Every feasible (budget, R, kc): estimated L2 -> shared-memory bytes per
+    // output row (halos of all planes, plus the weights unless resident),
+    // divided by 0.7 when only one CTA fits an SM (less latency hiding).
+    Cfg best{0, 0, 0, 0, 0};
+    double best_cost = 0.0;
+    for (size_t budget : {(size_t)104 * 1024, kUSmemMax}) {
       const int rmax = std::max(1, std::min(4, (budget == kUSmemMax ? 256 : 128) / p.ntile));
-      for (int want_bres = 1; want_bres >= 0 && !best.S; --want_bres)
-        for (int R = rmax; R >= 1 && !best.S; --R)
-          for (int kc : {64, 32, 16})
-            if (!best.S && kc <= cin) {
-              Cfg f = halo_cfg(kc, R, budget);
-              if (f.S >= 2 && f.bres >= want_bres) best = f;
-            }
-      return best;
-    };
-    Cfg best = search(104 * 1024);
-    // two CTAs per SM unless that re-streams the weights for every tile and one
-    // CTA could keep them resident
-    const Cfg one = search(kUSmemMax);
-    if (!best.S || (!best.bres && one.S && one.bres)) best = one;
+      for (int R = rmax; R >= 1; --R)
+        for (int kc : {64, 32, 16}) {
+          if (kc > cin) continue;
+          const Cfg f = halo_cfg(kc, R, budget);
+          if (f.S < 2) continue;
+          const int hoff = taps == 9 ? p.sp_in + 1 : 0;
+          const double rows = (double)((128 * R + 2 * hoff + 7) & ~7);
+          const double a_all = (cin / 8) * rows * 16.0;
+          const double b_all = f.bres ? 0.0 : (double)taps * p.ntile * cin * 2;
+          const double cost = (a_all + b_all) / (128.0 * R) / (budget == kUSmemMax ? 0.7 : 1.0);
+          if (!best.S || cost < best_cost) best = f, best_cost = cost;
+        }
+    }
     if (!best.S) return ufail(u, VIMG_ERR_ARG, "unet: no halo configuration fits");
     p.kc = best.kc, p.R = best.R, p.stages = best.S, p.bres = best.bres;
   } else {
