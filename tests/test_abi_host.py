@@ -80,3 +80,16 @@ def test_unet_create_rejects_small_images(vimg):
     assert not vimg.lib.vimg_unet_create(63, 128, 4, None)
     assert b"64" in vimg.lib.vimg_unet_last_error(None)
     assert vimg.lib.vimg_unet_load(None, None) == vimg.ERR_ARG
+
+
+def test_downstream_calls_reject_null_handles(vimg):
+    """Argument checks before any CUDA call: traces, summaries, U-Net and
+    footprint entry points on NULL handles."""
+    L = vimg.lib
+    assert L.vimg_set_rois(None, None, 0) == vimg.ERR_ARG
+    assert L.vimg_video_summary(None, None, None) == vimg.ERR_ARG
+    assert L.vimg_attach_unet(None, None) == vimg.ERR_ARG
+    assert L.vimg_unet_run(None, None, 0, None) == vimg.ERR_ARG
+    assert L.vimg_unet_activation(None, 0, None, None, None, None) == vimg.ERR_ARG
+    assert L.vimg_segment(None, None, 1, None, None, 0, None, None) == vimg.ERR_ARG
+    assert not L.vimg_segmenter_create(0, 64, 4, None)
