@@ -172,6 +172,8 @@ int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_
  * compute of the previous batch), and the shifts (host float32 [n][2]) and
  * the summaries (host float32 [k][2][H][W]) are copied back.  Either output
  * may be NULL.  d_corrected_out is an optional DEVICE buffer [n][H][W].
+ * Whole-video summary sums (VIMG_VIDEO_SUMMARY) accumulate as in vimg_process;
+ * voltage traces and probability maps need vimg_process_io.
  * Synchronises before returning.  Returns k or an error. */
 int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n, float* h_shifts_out,
                       float* h_summary_out, float* d_corrected_out);
@@ -253,8 +255,9 @@ int vimg_proposal_stats(vimg_handle* h, long long* frames, long long* fallbacks)
  * launch (more are split into groups of 8).
  *
  * Requirements: 1 <= k <= 64 distinct handles on one device, each with its
- * template set, created without VIMG_CORR_BF16 and VIMG_PROPOSAL_CNN (the
- * batched form runs the full-window FP32 method).  Work is enqueued on hs[0]'s
+ * template set, created without VIMG_CORR_BF16, VIMG_PROPOSAL_CNN and
+ * VIMG_VIDEO_SUMMARY (the batched form runs the full-window FP32 method and
+ * the outputs below; voltage traces and probability maps need vimg_process_io).  Work is enqueued on hs[0]'s
  * stream; the other handles' streams are ordered before and after the call
  * with events.  Output arrays have k entries; any entry (or the whole array)
  * may be NULL.  d_shifts_out[v] is [ns[v]][2]; d_summary_out[v] is
