@@ -448,7 +448,7 @@ def run_variants(args, frames, T, ref_shifts, corrected, summary, stream, dev, k
     """Other configurations on the same video: voltage traces of the neuron
     ROIs, the spiking-pixel U-Net on the summary pairs, the BF16 tensor-core
     correlation and the learned shift proposal (CNN + +-2 px window +
-    full-window fallback), the last two judged against the full-window shifts."""
+    full-window fallback), the last two compared with the full-window shifts."""
     from paper_2403_16438_gb300 import proposal, synth, vimg
     n = frames.shape[0]
     out = {}

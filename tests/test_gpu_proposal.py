@@ -1,7 +1,7 @@
 """Learned shift proposal on the GPU: the CUDA forward/backward against the FP64
 CPU oracle (gradient check), training progress with the library's own
 kernels, and the proposal path (CNN -> +-2 px window -> full-window fallback)
-against the full-window path, which stays the judge of its error."""
+against the full-window path, which stays the reference for its error."""
 import ctypes
 
 import numpy as np
@@ -98,7 +98,7 @@ def test_proposal_path_against_full_window(trained):
         h.close()
     sf, sp = outs["full"][0], outs["prop"][0]
     err = np.abs(sf - sp).max(axis=1)
-    # the full window judges the proposal: 0.05 px gate
+    # the full window is the reference for the proposal: 0.05 px gate
     assert np.mean(err <= 0.05) >= 0.95, err
     same = err <= 1e-4
     # frames that agree give the same corrected video
