@@ -358,9 +358,18 @@ __global__ void __launch_bounds__(kUThreads, 1)
         const int y = yq - pad_in, x = rr - yq * p.sp_in - pad_in;
         const bool valid = m < p.m_px && y >= 0 && y < p.s_in && x >= 0 && x < p.s_in;
         const size_t row_out = (size_t)b * p.spo;
-        for (int c0 = 0; c0 < p.ntile; c0 += 16) {
+        // two 16-column TMEM loads in flight per wait
+        for (int c2 = 0; c2 < p.ntile; c2 += 32) {
+          uint32_t raw[2][16];
+          const uint32_t ta = tmem + lane_base + (uint32_t)(buf * acc_cols + r * p.ntile + c2);
+          tmem_ld16_nowait(ta, raw[0]);
+          if (c2 + 16 < p.ntile) tmem_ld16_nowait(ta + 16, raw[1]);
+          tmem_wait_ld();
+          for (int hh = 0; hh < 2 && c2 + 16 * hh < p.ntile; ++hh) {
+          const int c0 = c2 + 16 * hh;
           float v[16];
-          tmem_ld16(tmem + lane_base + (uint32_t)(buf * acc_cols + r * p.ntile + c0), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(raw[hh][j]);
           if (!valid) continue;
           const int ng = nt * p.ntile + c0;
 #pragma unroll
@@ -387,6 +396,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
                                (size_t)(p.out_guard + opix) * 8;
           *reinterpret_cast<uint4*>(dst) = lo;
           *reinterpret_cast<uint4*>(dst + p.out_plane) = hi;
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
