@@ -387,6 +387,12 @@ def run_vimg(args):
         sm_h = torch.empty((max(1, k_max), 2, H, W), pin_memory=True)
         h.reset()
         h.process_host(fh, shifts_host=sh_h, summary_host=sm_h, corrected=corrected)
+        # the box's pinned host -> device bandwidth, which bounds the copies e2e overlaps
+        torch.cuda.synchronize()
+        tc0 = time.perf_counter()
+        frames.copy_(fh, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = fh.numel() * 2 / (time.perf_counter() - tc0) / 1e9
         barrier()
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -398,7 +404,7 @@ def run_vimg(args):
         line["e2e"] = {"value": n * ke * ws / te, "unit": UNIT,
                        "h2d_bytes_per_step": n * H * W * 2,
                        "d2h_bytes_per_step": n * 2 * 4 + k_max * 2 * H * W * 4,
-                       "steps": ke,
+                       "steps": ke, "h2d_GBs_measured": h2d_gbs,
                        "note": "vimg_process_host: pinned host frames in, shifts and summaries "
                                "out; corrected frames stay in device memory"}
         del fh
