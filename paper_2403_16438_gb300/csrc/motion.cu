@@ -79,7 +79,8 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 // The map covers the top-left positions of all windows of all patches:
 // rows y0 - R .. y0 + 21 (ny - 1) + R, likewise for columns.  One CTA per
 // 56 x 32 block of positions per frame: row sums slide along x, window sums
-// slide along y, all in 64-bit integers.
+// slide along y, in exact integers (32-bit squared sums for blocks of moderate
+// range, 64-bit otherwise; see box_sums).
 static int g_sms = 0;  // SM count, set by kernels_init()
 constexpr int kGroup = 11;  // patches per FP32 correlation work item (see k_corr_f32)
 constexpr int kBoxRows = 56, kBoxCols = 32, kBoxThreads = 256;
@@ -103,9 +104,76 @@ __host__ __device__ inline int stats_tiles(PatchGrid g, int R) {
   return ((sw + kBoxCols - 1) / kBoxCols) * ((sh + kBoxRows - 1) / kBoxRows);
 }
 
+// Pixels of a staged block are taken relative to c = the middle of their range:
+// SF = 441 S2 - S1^2 does not change under a common shift, and when every
+// |F - c| <= kBoxDev32 the squared sums stay below 2^32 (441 * 3100^2 < 2^32),
+// so they run in unsigned 32-bit arithmetic (a slide's intermediate value is
+// exact modulo 2^32 and its result is in range).  Wider blocks use 64 bits.
+constexpr int kBoxDev32 = 3100;
+constexpr int kBoxChunk = 11;  // row-sum positions per job: 76 rows x 3 jobs (11, 11, 10)
+
+template <typename Acc2>
+__device__ __forceinline__ Acc2 box_sq(int v) {
+  return (Acc2)((long long)v * v);
+}
+
+// Row sums, then window sums and the isf outputs of one staged block.
+template <typename Acc2>
+__device__ __forceinline__ void box_sums(const int* __restrict__ in, int* __restrict__ rs1,
+                                         Acc2* __restrict__ rs2, int c, int by, int bx, int sh,
+                                         int sw, float* __restrict__ out) {
+  for (int job = threadIdx.x; job < kBoxIR * 3; job += kBoxThreads) {
+    const int r = job / 3, c0 = (job - 3 * r) * kBoxChunk;
+    const int n = min(kBoxChunk, kBoxCols - c0);
+    const int* row = in + r * kBoxInStride + c0;
+    int s1 = 0;
+    Acc2 s2 = 0;
+#pragma unroll
+    for (int k = 0; k < kPatch; ++k) {
+      const int v = row[k] - c;
+      s1 += v;
+      s2 += box_sq<Acc2>(v);
+    }
+    int* o1 = rs1 + r * kBoxRsStride + c0;
+    Acc2* o2 = rs2 + r * kBoxRsStride + c0;
+#pragma unroll
+    for (int k = 0; k < kBoxChunk; ++k) {
+      if (k < n) {
+        o1[k] = s1;
+        o2[k] = s2;
+        if (k + 1 < n) {  // reads columns up to c0 + n - 1 + 20 <= 51
+          const int a = row[k + kPatch] - c, b = row[k] - c;
+          s1 += a - b;
+          s2 += box_sq<Acc2>(a) - box_sq<Acc2>(b);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // window sums: 32 columns x 8 chunks of 7 rows
+  const int col = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 7;
+  int s1 = 0;  // |S1| <= 441 * 65535 < 2^31
+  Acc2 s2 = 0;
+#pragma unroll
+  for (int k = 0; k < kPatch; ++k) {
+    s1 += rs1[(r0 + k) * kBoxRsStride + col];
+    s2 += rs2[(r0 + k) * kBoxRsStride + col];
+  }
+#pragma unroll
+  for (int r = r0; r < r0 + 7; ++r) {
+    const int y = by + r, x = bx + col;
+    const long long sf = (long long)kPatchArea * (long long)s2 - (long long)s1 * s1;
+    if (y < sh && x < sw) out[(size_t)y * sw + x] = sf > 0 ? rsqrtf((float)sf) : 0.f;
+    if (r + 1 < r0 + 7) {
+      s1 += rs1[(r + kPatch) * kBoxRsStride + col] - rs1[r * kBoxRsStride + col];
+      s2 += rs2[(r + kPatch) * kBoxRsStride + col] - rs2[r * kBoxRsStride + col];
+    }
+  }
+}
+
 // One CTA per (job, frame, block of positions); the job comes from the prefix
 // counts of the table.
-__global__ void __launch_bounds__(kBoxThreads)
+__global__ void __launch_bounds__(kBoxThreads, 4)
     k_boxstats(const __grid_constant__ MotionBatch b, const int* __restrict__ list,
                const int* __restrict__ list_n) {
   // Without a list every CTA takes one work item.  With a frame list (fallback
@@ -116,6 +184,10 @@ __global__ void __launch_bounds__(kBoxThreads)
     const MotionJob& J0 = b.j[0];
     n_items = min(J0.nf, *list_n) * stats_tiles(J0.g, J0.R);
   }
+  __shared__ int in[kBoxIR * kBoxInStride];
+  __shared__ int rs1[kBoxIR * kBoxRsStride];
+  __shared__ long long rs2[kBoxIR * kBoxRsStride];  // 32-bit sums use its first half
+  __shared__ unsigned wmin[kBoxThreads / 32], wmax[kBoxThreads / 32];
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
   const int jb = list ? 0 : job_of(b.stats_begin, b.n, item);
   const MotionJob& J = b.j[jb];
@@ -127,14 +199,9 @@ __global__ void __launch_bounds__(kBoxThreads)
   const int fi = local / per, rem = local - fi * per;
   const int f = list ? list[fi] : fi;
   const int by = (rem / ntx) * kBoxRows, bx = (rem % ntx) * kBoxCols;
-  const uint16_t* __restrict__ frames = J.frames;
-  float* __restrict__ isf = J.isf;
-  __shared__ int in[kBoxIR * kBoxInStride];
-  __shared__ int rs1[kBoxIR * kBoxRsStride];
-  __shared__ long long rs2[kBoxIR * kBoxRsStride];
-  const uint16_t* F = frames + (size_t)f * H * W;
+  const uint16_t* F = J.frames + (size_t)f * H * W;
   {
-    // all loads in flight at once, then the shared stores
+    // all loads in flight at once, then the shared stores and the block's range
     unsigned v[kBoxLoads];
 #pragma unroll
     for (int k = 0; k < kBoxLoads; ++k) {
@@ -143,57 +210,37 @@ __global__ void __launch_bounds__(kBoxThreads)
       const int y = min(oy + by + r, H - 1), x = min(ox + bx + c, W - 1);
       v[k] = i < kBoxIR * kBoxIC ? __ldg(F + (size_t)y * W + x) : 0u;
     }
+    unsigned mn = 0xffffu, mx = 0u;
 #pragma unroll
     for (int k = 0; k < kBoxLoads; ++k) {
       const int i = threadIdx.x + k * kBoxThreads;
       const int r = i / kBoxIC, c = i - r * kBoxIC;
-      if (i < kBoxIR * kBoxIC) in[r * kBoxInStride + c] = (int)v[k];
-    }
-  }
-  __syncthreads();
-  // row sums: 76 rows x 4 chunks of 8 positions
-  for (int job = threadIdx.x; job < kBoxIR * 4; job += kBoxThreads) {
-    const int r = job >> 2, c0 = (job & 3) * 8;
-    const int* row = in + r * kBoxInStride;
-    int s1 = 0;
-    long long s2 = 0;
-#pragma unroll
-    for (int k = 0; k < kPatch; ++k) {
-      const int v = row[c0 + k];
-      s1 += v;
-      s2 += (long long)v * v;
-    }
-#pragma unroll
-    for (int c = c0; c < c0 + 8; ++c) {
-      rs1[r * kBoxRsStride + c] = s1;
-      rs2[r * kBoxRsStride + c] = s2;
-      if (c + 1 < c0 + 8) {
-        const int a = row[c + kPatch], b = row[c];
-        s1 += a - b;
-        s2 += (long long)a * a - (long long)b * b;
+      if (i < kBoxIR * kBoxIC) {
+        in[r * kBoxInStride + c] = (int)v[k];
+        mn = min(mn, v[k]);
+        mx = max(mx, v[k]);
       }
     }
-  }
-  __syncthreads();
-  // window sums: 32 columns x 8 chunks of 7 rows
-  const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 7;
-  long long s1 = 0, s2 = 0;
-#pragma unroll
-  for (int k = 0; k < kPatch; ++k) {
-    s1 += rs1[(r0 + k) * kBoxRsStride + c];
-    s2 += rs2[(r0 + k) * kBoxRsStride + c];
-  }
-  float* out = isf + (size_t)f * sh * sw;
-#pragma unroll
-  for (int r = r0; r < r0 + 7; ++r) {
-    const int y = by + r, x = bx + c;
-    const long long sf = (long long)kPatchArea * s2 - s1 * s1;
-    if (y < sh && x < sw) out[(size_t)y * sw + x] = sf > 0 ? rsqrtf((float)sf) : 0.f;
-    if (r + 1 < r0 + 7) {
-      s1 += rs1[(r + kPatch) * kBoxRsStride + c] - rs1[r * kBoxRsStride + c];
-      s2 += rs2[(r + kPatch) * kBoxRsStride + c] - rs2[r * kBoxRsStride + c];
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) {
+      wmin[threadIdx.x >> 5] = mn;
+      wmax[threadIdx.x >> 5] = mx;
     }
   }
+  __syncthreads();
+  unsigned mn = wmin[0], mx = wmax[0];
+#pragma unroll
+  for (int w = 1; w < kBoxThreads / 32; ++w) {
+    mn = min(mn, wmin[w]);
+    mx = max(mx, wmax[w]);
+  }
+  const int c = (int)((mn + mx) >> 1);
+  float* out = J.isf + (size_t)f * sh * sw;
+  if ((int)mx - c <= kBoxDev32)
+    box_sums<unsigned>(in, rs1, reinterpret_cast<unsigned*>(rs2), c, by, bx, sh, sw, out);
+  else
+    box_sums<long long>(in, rs1, rs2, c, by, bx, sh, sw, out);
   __syncthreads();  // the shared buffers are reused by the next item
   }
 }
