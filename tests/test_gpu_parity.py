@@ -121,6 +121,25 @@ def test_temporal_stage_with_given_shifts(vimg, tiny, hp):
     compare_images(g["summary"][:, 1], r["summary"][:, 1], "T")
 
 
+def test_wide_range_blocks(vimg, tiny):
+    """Window statistics sum squares in 32 bits when a staged block's pixels lie
+    within 3,100 of the middle of their range, in 64 bits otherwise.  Scaling
+    the left half of the video (and template) by 10 puts blocks of both kinds
+    in one frame: those straddling column 64 span > 15,000 counts, those right
+    of it keep the tiny video's range."""
+    frames, _, T = tiny
+    f = np.clip(frames[:12].numpy().astype(np.int64) * np.where(np.arange(128) < 64, 10, 1),
+                0, 65535)
+    assert f[:, :, 60:68].max() - f[:, :, 60:68].min() > 15000
+    f = torch.from_numpy(f.astype(np.uint16))
+    T2 = T.clone()
+    T2[:, :64] *= 10
+    g = run_gpu(vimg, f, T2, want_surface=True)
+    r = run_oracle(f, T2, want_surface=True)
+    assert np.abs(g["surface"] - r["surface"]).max() < 2e-6
+    compare_shifts(g["shifts"], g["info"], r)
+
+
 @pytest.mark.parametrize("H,W,R,L", [(75, 100, 8, 50), (97, 61, 5, 13), (53, 53, 16, 50)])
 def test_ragged_sizes_and_radii(vimg, H, W, R, L):
     cfg = synth.tiny_config(H=H, W=W, seed=77 + H, clamp=min(8.0, R))
