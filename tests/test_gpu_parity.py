@@ -136,7 +136,10 @@ def test_wide_range_blocks(vimg, tiny):
     T2[:, :64] *= 10
     g = run_gpu(vimg, f, T2, want_surface=True)
     r = run_oracle(f, T2, want_surface=True)
-    assert np.abs(g["surface"] - r["surface"]).max() < 2e-6
+    # Ten times larger pixel terms: the FP32 numerators (441 products each) carry
+    # more rounding than on the plain video; bound = 441 u, u = 2^-24, the
+    # worst-case relative error of an FP32 sum of 441 terms.
+    assert np.abs(g["surface"] - r["surface"]).max() < 441 * 2.0 ** -24
     compare_shifts(g["shifts"], g["info"], r)
 
 
