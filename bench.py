@@ -193,6 +193,16 @@ def cpu_oracle_fps(frames_cpu, template, budget_s=15.0, max_frames=64):
     return n / dt, n, dt, oracle.num_threads()
 
 
+def workload_desc(bf16=False, learned=False):
+    """The workload string of the JSON line's config (shared by both arms)."""
+    return ("paper-scale synthetic video: 512x512 uint16, 10,000 frames per step, "
+            + ("full-window BF16 tensor-core ZNCC" if bf16 else
+               "learned proposal + +-2 px FP32 ZNCC window, full-window fallback"
+               if learned else "full-window FP32 ZNCC")
+            + " +-16 px (484 patches x 1089 shifts), bilinear "
+            "resampling, L=50 mean and max-median summaries")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -226,8 +236,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "512x512 uint16 video, full-window ZNCC +-16 px, L=50 summaries",
-                   "frames_per_step": per_step},
+        "config": {"workload": workload_desc(), "frames_per_step": per_step, "H": H, "W": W,
+                   "search_radius": R, "segment_len": L, "parallelism": "single",
+                   "sample": f"each step runs {per_step} of the workload's 10,000 frames "
+                             "(a bounded CPU sample; frames/s is per frame)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -350,12 +362,7 @@ def run_vimg(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if bf16 else "f32",
         "data": "synthetic",
         "config": {
-            "workload": "paper-scale synthetic video: 512x512 uint16, 10,000 frames per step, "
-                        + ("full-window BF16 tensor-core ZNCC" if bf16 else
-                           "learned proposal + +-2 px FP32 ZNCC window, full-window fallback"
-                           if learned else "full-window FP32 ZNCC")
-                        + " +-16 px (484 patches x 1089 shifts), bilinear "
-                        "resampling, L=50 mean and max-median summaries",
+            "workload": workload_desc(bf16, learned),
             "frames_per_step": n, "H": H, "W": W, "search_radius": R, "segment_len": L,
             "l2": "no flush: each step reads 5.2 GB of frames, larger than L2",
             "parallelism": f"replicas{ws}" if ws > 1 else "single",
