@@ -93,3 +93,50 @@ def test_downstream_calls_reject_null_handles(vimg):
     assert L.vimg_unet_activation(None, 0, None, None, None, None) == vimg.ERR_ARG
     assert L.vimg_segment(None, None, 1, None, None, 0, None, None) == vimg.ERR_ARG
     assert not L.vimg_segmenter_create(0, 64, 4, None)
+
+
+def test_remaining_entry_points_reject_bad_arguments(vimg):
+    """Argument checks that run before any CUDA call, for the entry points not
+    covered above: host-buffer, batch, profiling, proposal, CNN training and
+    allocation-free calls.  Every case returns before a pointer is used on the
+    device (checked by reading each function's validation order)."""
+    import numpy as np
+    L = vimg.lib
+    ARG, SIZE = vimg.ERR_ARG, vimg.ERR_SIZE
+    assert L.vimg_process_io(None, None, 0, None) == ARG
+    assert L.vimg_process_host(None, None, 0, None, None, None) == ARG
+    assert L.vimg_profile_enable(None, 1) == ARG
+    assert L.vimg_profile_read(None, None, None, 1) == ARG
+    assert L.vimg_synchronize(None) == ARG
+    assert L.vimg_load_proposal(None, None) == ARG
+    assert L.vimg_proposal_stats(None, None, None) == ARG
+    # several videos per call: no handles, too few / too many, null frame tables
+    nulls = (ctypes.c_void_p * 65)()
+    assert L.vimg_process_batch(None, 1, None, None, None, None, None, None, None) == ARG
+    assert L.vimg_process_batch(nulls, 0, None, None, None, None, None, None, None) == ARG
+    assert L.vimg_process_batch(nulls, 65, nulls, nulls, None, None, None, None, None) == ARG
+    assert L.vimg_process_batch(nulls, 1, None, None, None, None, None, None, None) == ARG
+    counts = (ctypes.c_int * 1)(0)
+    assert L.vimg_process_batch(nulls, 1, nulls, counts, None, None, None, None, None) == ARG
+    # proposal network training calls
+    assert L.vimg_cnn_prepare(None, -1, 128, 128, None, 0, None, None) == ARG
+    assert L.vimg_cnn_prepare(None, 0, 64, 128, None, 0, None, None) == ARG
+    assert L.vimg_cnn_pack_bf16(None, None, None) == ARG
+    assert L.vimg_cnn_forward(None, None, None, 1, None, None) == ARG
+    assert L.vimg_cnn_loss(None, None, 1, None, None, None) == ARG
+    assert L.vimg_cnn_backward(None, None, None, None, 1, None, None, None) == ARG
+    assert L.vimg_cnn_adam(None, None, None, None, 1e-3, 0.9, 0.999, 1e-8, 0, None) == ARG
+    # allocation-free motion estimate: a host buffer stands in for the template
+    # pointer; every case below returns before it is used
+    buf = np.zeros(16, np.float32)
+    tp = ctypes.c_void_p(buf.ctypes.data)
+    assert L.vimg_motion_noalloc(None, None, 0, 128, 128, 16, None, None, None) == ARG
+    assert L.vimg_motion_noalloc(tp, None, -1, 128, 128, 16, None, None, None) == ARG
+    assert L.vimg_motion_noalloc(tp, None, 1, 128, 128, 16, None, None, None) == ARG
+    assert L.vimg_motion_noalloc(tp, None, 0, 128, 128, 17, None, None, None) == ARG
+    assert L.vimg_motion_noalloc(tp, None, 0, 52, 128, 16, None, None, None) == SIZE
+    assert L.vimg_motion_noalloc(tp, None, 0, 1 << 20, 128, 16, None, None, None) == SIZE
+    # U-Net stage
+    assert L.vimg_unet_synchronize(None) == ARG
+    assert L.vimg_unet_profile(None, 1) == ARG
+    assert L.vimg_unet_profile_read(None, None, None, None, 1) == ARG
