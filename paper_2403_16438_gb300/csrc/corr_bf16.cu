@@ -500,18 +500,14 @@ cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
                              cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   if (R != kMaxR) return cudaErrorInvalidValue;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_corr_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e != cudaSuccess) {
-      sms = 0;
-      return e;
-    }
-  }
+  static unsigned char attr[kMaxDevices] = {};
+  cudaError_t ea = once_per_device(attr, [](int) {
+    return cudaFuncSetAttribute(k_corr_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmem);
+  });
+  if (ea != cudaSuccess) return ea;
+  const int sms = sm_count();
+  if (sms <= 0) return cudaErrorInvalidDevice;
   const int np = g.ny * g.nx, groups = (nf + kNF - 1) / kNF;
   const CUtensorMap* map = static_cast<const CUtensorMap*>(tmap);
   k_corr_bf16<<<std::min(groups * np, sms), kThreads, kSmem, st>>>(*map, nf, g, as, bgc, num, err);

@@ -81,7 +81,6 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
 // 56 x 32 block of positions per frame: row sums slide along x, window sums
 // slide along y, in exact integers (32-bit squared sums for blocks of moderate
 // range, 64-bit otherwise; see box_sums).
-static int g_sms = 0;  // SM count, set by kernels_init()
 constexpr int kGroup = 11;  // patches per FP32 correlation work item (see k_corr_f32)
 constexpr int kBoxRows = 56, kBoxCols = 32, kBoxThreads = 256;
 constexpr int kBoxIR = kBoxRows + kPatch - 1, kBoxIC = kBoxCols + kPatch - 1;  // 76 x 52 inputs
@@ -284,7 +283,7 @@ cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st, const int*
   if (list) {  // one wave of CTAs that stride over the listed frames' items
     cudaError_t e = kernels_init();
     if (e != cudaSuccess) return e;
-    blocks = std::min(blocks, 4 * g_sms);
+    blocks = std::min(blocks, 4 * sm_count());
   }
   k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b, list, list_n);
   return cudaGetLastError();
@@ -506,17 +505,30 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
   if (grp == 0 && !released) asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
 }
 
+static int g_sms[kMaxDevices] = {};
+static unsigned char g_sms_done[kMaxDevices] = {};
+static unsigned char g_kernels_done[kMaxDevices] = {};
+
+int sm_count() {
+  const cudaError_t e = once_per_device(g_sms_done, [](int dev) {
+    int sms = 0;
+    const cudaError_t r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (r == cudaSuccess) g_sms[dev] = sms;
+    return r;
+  });
+  const int dev = current_device();
+  return e == cudaSuccess && dev >= 0 ? g_sms[dev] : 0;
+}
+
 cudaError_t kernels_init() {
-  if (g_sms) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * kGroupSmem));
-  if (e == cudaSuccess) e = temporal_init();
-  if (e == cudaSuccess) g_sms = sms;
-  return e;
+  return once_per_device(g_kernels_done, [](int) {
+    if (sm_count() <= 0) return cudaErrorInvalidDevice;
+    cudaError_t e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * kGroupSmem));
+    if (e == cudaSuccess) e = temporal_init();
+    return e;
+  });
 }
 
 cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st, const int* list,
@@ -525,7 +537,7 @@ cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st, const i
   if (items <= 0) return cudaSuccess;
   cudaError_t e = kernels_init();
   if (e != cudaSuccess) return e;
-  const int grid = std::min(g_sms, (items + 1) / 2);
+  const int grid = std::min(sm_count(), (items + 1) / 2);
   k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(b, list, list_n);
   return cudaGetLastError();
 }
@@ -878,13 +890,12 @@ cudaError_t launch_corr_narrow(const uint16_t* frames, int nf, int H, int W, Pat
                                unsigned long long* csum, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   const size_t smem = sizeof(float) * (kNarrow + kPatch - 1) * kNarrowStride;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_corr_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static unsigned char attr[kMaxDevices] = {};
+  cudaError_t e = once_per_device(attr, [smem](int) {
+    return cudaFuncSetAttribute(k_corr_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   const int groups = g.ny * ((g.nx + kNarrowGroup - 1) / kNarrowGroup);
   k_corr_narrow<<<dim3(groups, nf), kNarrowGroup * 8, smem, st>>>(frames, H, W, g, R, td.tc, td.tn2,
                                                                    isf, prop, csum);

@@ -1,23 +1,25 @@
 // Motion estimate without any allocation: vimg_motion_noalloc.
 //
 // Some callers cannot allocate device memory at the moment they need shifts:
-// code running inside a CUDA-graph capture that must not grow the memory
-// pool, real-time acquisition loops that forbid allocator calls (they can
-// block on the driver and break the frame deadline), and hosts that hand the
-// GPU to this library with every byte of device memory already reserved for
-// frame buffers.  For them this entry point runs the same kernels as
-// vimg_process's motion estimate (template preparation, exact window
-// statistics, FP32 ZNCC correlation, integer peak and parabola) with all of its
-// scratch in one fixed array that lives in the library's static device memory.
+// real-time acquisition loops that forbid allocator calls (cudaMalloc can
+// synchronise the device and block on the driver, which breaks the frame
+// deadline), and hosts that hand the GPU to this library with every byte of
+// device memory already reserved for their own frame buffers.  For them this
+// entry point runs the same kernels as vimg_process's motion estimate (template
+// preparation, exact window statistics, FP32 ZNCC correlation, integer peak and
+// parabola) with all of its scratch in one fixed array that lives in the
+// library's static device memory.
 //
 // Limits and rules:
 //   - The array holds kNoAllocBytes (12 MiB); frames up to 1024 x 1024 with a
 //     search radius up to 16 fit.  Larger frames are rejected with
-//     VIMG_ERR_SIZE before any work is enqueued.
+//     VIMG_ERR_SIZE before any work is enqueued.  At 1024 x 1024 and R = 16 the
+//     statistics maps of two frames fill the array, so frames go two per launch
+//     there.
 //   - Every GPU that loads the library holds the array until the process exits.
 //   - The first call on a device looks up the array's device address with that
-//     device current (cudaGetSymbolAddress).  Make that first call before any
-//     stream capture begins.
+//     device current (cudaGetSymbolAddress) and sets the kernels' attributes for
+//     that device.  Make that first call before any stream capture begins.
 //   - Every call shares the one array and leaves its contents behind; the call
 //     clears what must start at zero itself.  Calls whose work overlaps on the
 //     GPU (different streams, or different host threads without ordering) race
@@ -38,7 +40,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 namespace {
 
 constexpr int kNoAllocMaxSide = 1024;
-constexpr int kMaxDevices = 64;
 constexpr int kNoAllocBatch = 16;  // frames per stats/correlation launch (as vimg_process)
 
 std::mutex g_noalloc_mu;
@@ -89,10 +90,12 @@ extern "C" int vimg_motion_noalloc(const float* d_template, const uint16_t* d_fr
     return VIMG_ERR_SIZE;
   int batch = (int)((kNoAllocBytes - fixed - 512) / (per_frame_isf + per_frame_cs));
   if (batch > kNoAllocBatch) batch = kNoAllocBatch;
+  if (batch < 1) return VIMG_ERR_SIZE;  // not one frame's scratch: nothing is enqueued
   if (n == 0) return VIMG_OK;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VIMG_ERR_CUDA;
+  const int dev = current_device();
+  if (dev < 0) return VIMG_ERR_CUDA;
+  if (kernels_init() != cudaSuccess) return VIMG_ERR_CUDA;
   unsigned char* base = nullptr;
   if (noalloc_scratch(dev, &base) != cudaSuccess) return VIMG_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

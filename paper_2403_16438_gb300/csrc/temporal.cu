@@ -530,12 +530,11 @@ static size_t temporal_smem(int L) {
 }
 
 cudaError_t temporal_init() {
-  static bool attr_set = false;
-  if (attr_set) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)temporal_smem(kMaxL));
-  if (e == cudaSuccess) attr_set = true;
-  return e;
+  static unsigned char done[kMaxDevices] = {};
+  return once_per_device(done, [](int) {
+    return cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)temporal_smem(kMaxL));
+  });
 }
 
 // ---- voltage-trace ROIs ----------------------------------------------------------

@@ -884,15 +884,16 @@ extern "C" vimg_unet* vimg_unet_create(int H, int W, int max_segments, void* str
   if (cudaGetDevice(&u->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&u->sms, cudaDevAttrMultiProcessorCount, u->dev) != cudaSuccess)
     return bail("vimg_unet_create: no CUDA device");
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_conv_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kUSmemMax) != cudaSuccess ||
-        cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kUSmemMax) != cudaSuccess)
-      return bail("vimg_unet_create: kernel attribute");
-    attr = true;
-  }
+  static unsigned char attr[kMaxDevices] = {};
+  if (once_per_device(attr, [](int) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kUSmemMax);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kUSmemMax);
+        return e;
+      }) != cudaSuccess)
+    return bail("vimg_unet_create: kernel attribute");
   const size_t P = u->P;
   cudaError_t e = cudaSuccess;
   auto A = [&](auto*& ptr, size_t n) {

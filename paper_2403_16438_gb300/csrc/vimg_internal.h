@@ -105,6 +105,34 @@ __host__ __device__ __forceinline__ int job_of(const int* begin, int n, int item
   return j;
 }
 
+// ---- one-time set-up per device ------------------------------------------------
+// Kernel attributes (cudaFuncSetAttribute) and the SM count belong to a device:
+// the set-up below runs once for every device the library is used on, with that
+// device current.
+constexpr int kMaxDevices = 64;
+
+// Index of the current device, or -1 (no device, or beyond kMaxDevices).
+inline int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+  return dev;
+}
+
+// Runs fn() once per device; done[] holds one flag per device.  Concurrent first
+// calls may both run fn, which must therefore be idempotent.
+template <class Fn>
+cudaError_t once_per_device(unsigned char (&done)[kMaxDevices], Fn fn) {
+  const int dev = current_device();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  if (__atomic_load_n(&done[dev], __ATOMIC_ACQUIRE)) return cudaSuccess;
+  const cudaError_t e = fn(dev);
+  if (e == cudaSuccess) __atomic_store_n(&done[dev], (unsigned char)1, __ATOMIC_RELEASE);
+  return e;
+}
+
+// SM count of the current device (0 if unknown); cached per device.
+int sm_count();
+
 // Fills the prefix counts; returns false if a job is malformed.
 bool motion_batch_finalize(MotionBatch& b);
 bool temporal_batch_finalize(TemporalBatch& b);
@@ -116,7 +144,7 @@ cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st,
 cudaError_t launch_peak_multi(const MotionBatch& b, cudaStream_t st, const int* list = nullptr,
                               const int* list_n = nullptr);
 cudaError_t launch_temporal_multi(const TemporalBatch& b, cudaStream_t st);
-// Sets kernel attributes once (before any stream capture).
+// Sets kernel attributes once per device (before any stream capture).
 cudaError_t kernels_init();
 cudaError_t temporal_init();
 
