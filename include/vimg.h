@@ -296,11 +296,11 @@ int vimg_profile_enable(vimg_handle* h, int on);
 int vimg_profile_read(vimg_handle* h, double* ms, long long* launches, int reset);
 
 /* Motion estimate with no allocation at all, for callers that cannot allocate
- * device memory when they need shifts: code inside a CUDA-graph capture that
- * must not grow the memory pool, real-time acquisition loops that forbid
- * allocator calls (an allocation can block on the driver and miss the frame
- * deadline), and hosts that have already reserved all device memory for frame
- * buffers.  The paper has no counterpart; it is an interface of this library.
+ * device memory when they need shifts: real-time acquisition loops that forbid
+ * allocator calls (an allocation can synchronise the device or block on the
+ * driver and miss the frame deadline), and hosts that have already reserved all
+ * device memory for their own frame buffers.  The paper has no counterpart; it
+ * is an interface of this library.
  *
  * Computes, for n frames (device uint16 [n][H][W]) against the template
  * (device float32 [H][W]), the same shifts as vimg_process's motion estimate:
@@ -310,7 +310,8 @@ int vimg_profile_read(vimg_handle* h, double* ms, long long* launches, int reset
  * that loads the library holds until the process exits.  Frames up to
  * 1024 x 1024 (search_radius <= 16) fit; larger ones return VIMG_ERR_SIZE with
  * nothing enqueued.  The first call on a device looks up the array's device
- * address with that device current: make it before any stream capture.  Every
+ * address and sets the kernels' attributes with that device current: make it
+ * before any stream capture.  Every
  * call shares the array (and clears what must start at zero); calls whose work
  * overlaps on the GPU race and give wrong results, so serialise them.  Work is
  * enqueued on `stream` (NULL = default stream).  Returns VIMG_OK or an error
@@ -394,13 +395,19 @@ int vimg_unet_activation(vimg_unet* u, int i, void* d_out, int* n_patches, int* 
  * p_i > 0.5; 8-connected components kept if 20 <= area <= 1000 px, eccentricity
  * (pixel-centre covariance) <= 0.95 and concaveness 1 - area / convex-hull area
  * (hull of the pixel squares) <= 0.3; b = OR over segments; each 8-connected
- * component of b ("region", at most 16,000 px) is factorised by NMF, P ~ F A
- * (Eq. 3; rows = the region's pixels, columns = segments), with N = the number
- * of clusters of its kept blobs (a blob joins the first cluster whose first blob
- * it overlaps with IoU >= 1/2; at most 32) and 100 multiplicative updates from
- * the clusters' union masks.  The constants are readings: the paper names the
- * criteria, not their values.  Neurons are numbered by region (smallest pixel
- * index), then cluster. */
+ * component of b ("region") is factorised by NMF, P ~ F A (Eq. 3; rows = the
+ * region's pixels, columns = segments), with N = the number of clusters of its
+ * kept blobs (a blob joins the first cluster whose first blob it overlaps with
+ * IoU >= 1/2) and 100 multiplicative updates from the clusters' union masks.
+ * The constants are readings: the paper names the criteria, not their values.
+ * Neurons are numbered by region (smallest pixel index), then cluster.
+ *
+ * Capacity: the NMF kernel holds a region of at most 16,000 pixels and 32
+ * clusters.  A region beyond either limit is not factorised (it contributes no
+ * neuron) and is reported by vimg_segment_status; every other region's result
+ * is unaffected. */
+#define VIMG_REGION_TOO_LARGE 1 /* more than 16,000 pixels */
+#define VIMG_REGION_TOO_MANY 2  /* more than 32 clusters */
 typedef struct vimg_segmenter vimg_segmenter;
 
 /* Workspace for H x W maps and up to max_segments of them; NULL on failure. */
@@ -416,6 +423,13 @@ const char* vimg_segmenter_last_error(const vimg_segmenter* s);
  * max_neurons are written) or an error code. */
 int vimg_segment(vimg_segmenter* s, const float* d_prob, int K, float* d_footprints,
                  float* d_activity, int max_neurons, int* d_region_map, int* n_regions);
+
+/* Per-region status of the last vimg_segment call, in region order (host int
+ * array of n entries; the first min(n, regions) are written): 0 = factorised,
+ * VIMG_REGION_TOO_LARGE or VIMG_REGION_TOO_MANY = beyond the NMF kernel's
+ * capacity, not factorised.  Returns the number of regions of that call (0
+ * after a failed call) or VIMG_ERR_ARG. */
+int vimg_segment_status(const vimg_segmenter* s, int* status, int n);
 
 /* Attaches a U-Net of the same H x W to a handle (NULL detaches); the handle
  * does not own it.  vimg_process_io then fills vimg_io.prob on the handle's

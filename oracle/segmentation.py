@@ -18,12 +18,13 @@ The paper gives the steps but not their constants; readings taken here:
     order, then by smallest pixel index) are clustered greedily: a blob joins
     the first cluster whose first blob it overlaps with IoU >= 1/2 (the exact
     integer test 2 |a & b| >= |a | b|), else it starts a new cluster; N = the
-    number of clusters, at most 32 (a blob that would open a 33rd is ignored;
-    neurons that spike in different segments separate even where their
-    footprints touch).  F column j starts as the indicator of the
-    union of cluster j's blobs, A[j][i] as the mean of p_i over that union,
-    floored at 1e-6;
-  * regions larger than 16,000 pixels are not factorised (no neurons);
+    number of clusters (neurons that spike in different segments separate
+    even where their footprints touch).  F column j starts as the indicator of
+    the union of cluster j's blobs, A[j][i] as the mean of p_i over that
+    union, floored at 1e-6;
+  * every region is factorised, whatever its size and its N (the paper sets
+    no limit; a GPU implementation may have capacity limits of its own, which
+    it must report rather than change the answer);
   * NMF by Lee & Seung's multiplicative updates for the Frobenius loss,
     100 iterations of A <- A * (F'P) / (F'F A + 1e-9), then
     F <- F * (P A') / (F A A' + 1e-9), over the region's pixels (rows of P,
@@ -45,8 +46,6 @@ AREA_MIN, AREA_MAX = 20, 1000
 ECC_MAX = 0.95
 CONCAVE_MAX = 0.3
 NMF_ITERS = 100
-MAX_N = 32
-MAX_REGION = 16000
 NMF_EPS = 1e-9
 A_FLOOR = 1e-6
 EIGHT = np.ones((3, 3), bool)
@@ -144,10 +143,11 @@ def nmf(P, F, A, iters=NMF_ITERS):
     return F, A
 
 
-def footprints(prob):
+def regions(prob):
     """prob [K][H][W] -> list of regions (by smallest pixel index): dict(pixels =
-    raster indices of the region, N, F [M][N], A [N][K], blobs = kept
-    per-segment components inside)."""
+    raster indices of the region, blobs = kept per-segment components inside,
+    unions = per cluster the union of its blobs' pixels, N = number of clusters).
+    The structure of the factorisation, without the NMF itself."""
     prob = np.asarray(prob, np.float64)
     K, H, W = prob.shape
     kept = cleaned_masks(prob)
@@ -157,8 +157,6 @@ def footprints(prob):
             b[c] = True
     out = []
     for region in components(b.reshape(H, W)):
-        if region.size > MAX_REGION:
-            continue
         rset = set(region.tolist())
         blobs = [set(c.tolist()) for i in range(K) for c in kept[i] if int(c[0]) in rset]
         reps, unions = [], []
@@ -168,18 +166,35 @@ def footprints(prob):
                     unions[j] |= bl
                     break
             else:
-                if len(reps) < MAX_N:
-                    reps.append(bl)
-                    unions.append(set(bl))
-        N = len(reps)
-        pos = {p: r for r, p in enumerate(region)}
-        P = prob.reshape(K, H * W)[:, region].T  # [M][K]
-        F0 = np.zeros((region.size, N))
-        A0 = np.zeros((N, K))
-        for j, un in enumerate(unions):
-            idx = np.array(sorted(un))
-            F0[[pos[p] for p in idx], j] = 1.0
-            A0[j] = np.maximum(prob.reshape(K, H * W)[:, idx].mean(axis=1), A_FLOOR)
-        F, A = nmf(P, F0, A0)
-        out.append(dict(pixels=region, N=N, F=F, A=A, blobs=len(blobs)))
+                reps.append(bl)
+                unions.append(set(bl))
+        out.append(dict(pixels=region, blobs=len(blobs), unions=unions, N=len(reps)))
+    return out
+
+
+def factorise(prob, region):
+    """NMF of one region (a dict of regions()): returns (F [M][N], A [N][K])."""
+    prob = np.asarray(prob, np.float64)
+    K, H, W = prob.shape
+    pix = region["pixels"]
+    N = region["N"]
+    pos = {p: r for r, p in enumerate(pix)}
+    P = prob.reshape(K, H * W)[:, pix].T  # [M][K]
+    F0 = np.zeros((pix.size, N))
+    A0 = np.zeros((N, K))
+    for j, un in enumerate(region["unions"]):
+        idx = np.array(sorted(un))
+        F0[[pos[p] for p in idx], j] = 1.0
+        A0[j] = np.maximum(prob.reshape(K, H * W)[:, idx].mean(axis=1), A_FLOOR)
+    return nmf(P, F0, A0)
+
+
+def footprints(prob):
+    """prob [K][H][W] -> list of regions (by smallest pixel index): dict(pixels =
+    raster indices of the region, N, F [M][N], A [N][K], blobs = kept
+    per-segment components inside)."""
+    out = []
+    for r in regions(prob):
+        F, A = factorise(prob, r)
+        out.append(dict(pixels=r["pixels"], N=r["N"], F=F, A=A, blobs=r["blobs"]))
     return out

@@ -33,8 +33,11 @@ constexpr int kAreaMin = 20, kAreaMax = 1000;
 constexpr double kEccMax = 0.95, kConcaveMax = 0.3;
 constexpr int kNmfIters = 100;
 constexpr float kNmfEps = 1e-9f, kAFloor = 1e-6f;
-constexpr int kMaxN = 32;          // neurons per region handled by the NMF kernel
-constexpr int kMaxRegion = 16000;  // larger regions are not factorised
+// Capacity of the NMF kernel (not a rule of the method): a region with more
+// pixels or more clusters is not factorised here and is reported through the
+// per-region status (vimg_segment_status) instead.
+constexpr int kMaxN = 32;          // clusters (neurons) per region
+constexpr int kMaxRegion = 16000;  // pixels per region
 constexpr int kShapeWarps = 1216;  // warps of the shape kernel (hull scratch each)
 constexpr int kHullScratch = 12 * kAreaMax;  // corners (4 n) + chain (<= 8 n)
 
@@ -334,19 +337,22 @@ __device__ int inter_count(const int* a, int na, const int* b, int nb, long long
 
 // Per region (one warp): sort its blobs and pixels, cluster the blobs greedily
 // by overlap (the first blob of a cluster represents it), record N and each
-// blob's cluster (-1: dropped beyond kMaxN clusters).
+// blob's cluster.  A region beyond the NMF kernel's capacity gets N = 0, every
+// blob cluster -1 and status VIMG_REGION_TOO_LARGE (more than kMaxRegion
+// pixels) or VIMG_REGION_TOO_MANY (more than kMaxN clusters); else status 0.
 __global__ void k_region_cluster(int* __restrict__ rblobs, const int* __restrict__ roff,
                                  const int* __restrict__ rcnt, int* __restrict__ rpix,
                                  const int* __restrict__ poff, const int* __restrict__ pcnt,
                                  int n_reg, const int* __restrict__ list,
                                  const int* __restrict__ off, const int* __restrict__ cnt,
-                                 long long HW, int* __restrict__ bclu, int* __restrict__ nreg) {
+                                 long long HW, int* __restrict__ bclu, int* __restrict__ nreg,
+                                 int* __restrict__ status) {
   const int lane = threadIdx.x & 31, warps = (gridDim.x * blockDim.x) >> 5;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reg; r += warps) {
     int* bl = rblobs + roff[r];
     const int nb = rcnt[r];
-    if (pcnt[r] > kMaxRegion) {  // not factorised
-      if (lane == 0) nreg[r] = 0;
+    if (pcnt[r] > kMaxRegion) {  // beyond capacity: reported, not factorised
+      if (lane == 0) nreg[r] = 0, status[r] = VIMG_REGION_TOO_LARGE;
       for (int q = lane; q < nb; q += 32) bclu[bl[q]] = -1;
       continue;
     }
@@ -355,7 +361,8 @@ __global__ void k_region_cluster(int* __restrict__ rblobs, const int* __restrict
     if (lane) continue;
     int reps[kMaxN];
     int N = 0;
-    for (int q = 0; q < nb; ++q) {
+    bool over = false;
+    for (int q = 0; q < nb && !over; ++q) {
       const int c = bl[q];
       const int* a = list + off[c];
       int j = 0;
@@ -365,12 +372,18 @@ __global__ void k_region_cluster(int* __restrict__ rblobs, const int* __restrict
         if (2 * in >= cnt[c] + cnt[rc] - in) break;
       }
       if (j == N) {
-        if (N < kMaxN) reps[N++] = c;
-        else j = -1;
+        if (N == kMaxN) {
+          over = true;
+          break;
+        }
+        reps[N++] = c;
       }
       bclu[c] = j;
     }
-    nreg[r] = N;
+    if (over)
+      for (int q = 0; q < nb; ++q) bclu[bl[q]] = -1;
+    nreg[r] = over ? 0 : N;
+    status[r] = over ? VIMG_REGION_TOO_MANY : 0;
   }
 }
 
@@ -520,6 +533,7 @@ struct vimg_segmenter {
   int* Lb = nullptr;           // [HW]
   int* rid = nullptr;          // [HW]
   int* rpix = nullptr;         // [HW]
+  std::vector<int> status;     // per region of the last vimg_segment call
 };
 
 namespace {
@@ -610,12 +624,20 @@ extern "C" const char* vimg_segmenter_last_error(const vimg_segmenter* s) {
   return s ? s->err.c_str() : "";
 }
 
+extern "C" int vimg_segment_status(const vimg_segmenter* s, int* status, int n) {
+  if (!s || n < 0 || (n > 0 && !status)) return VIMG_ERR_ARG;
+  const int m = (int)s->status.size();
+  for (int i = 0; i < n && i < m; ++i) status[i] = s->status[i];
+  return m;
+}
+
 extern "C" int vimg_segment(vimg_segmenter* s, const float* d_prob, int K, float* d_footprints,
                             float* d_activity, int max_neurons, int* d_region_map, int* n_regions) {
   if (!s) return VIMG_ERR_ARG;
   if (K < 1 || K > s->Kmax || !d_prob || max_neurons < 0)
     return sfail(s, VIMG_ERR_ARG, "vimg_segment: bad arguments");
   const long long HW = (long long)s->H * s->W, total = HW * K;
+  s->status.clear();
   // 1. per-segment components, ids by ascending pixel index, pixel lists
   int rc = label(s, d_prob, nullptr, total, s->L);
   if (rc) return rc;
@@ -661,6 +683,7 @@ extern "C" int vimg_segment(vimg_segmenter* s, const float* d_prob, int K, float
   int* roff = dev_alloc<int>(s, tmp, n_reg, e);
   int* rcur = dev_alloc<int>(s, tmp, n_reg, e);
   int* nreg = dev_alloc<int>(s, tmp, n_reg, e);
+  int* rstat = dev_alloc<int>(s, tmp, n_reg, e);
   int* rblobs = dev_alloc<int>(s, tmp, n_comp, e);
   for (int* z : {pcnt, rcnt, rcur})
     if (e == cudaSuccess) e = cudaMemsetAsync(z, 0, sizeof(int) * std::max(n_reg, 1), s->st);
@@ -668,6 +691,7 @@ extern "C" int vimg_segment(vimg_segmenter* s, const float* d_prob, int K, float
     cleanup();
     return sfail(s, VIMG_ERR_CUDA, std::string("vimg_segment: ") + cudaGetErrorString(e));
   }
+  s->status.assign(n_reg, 0);
   if (n_reg == 0) {
     e = cudaStreamSynchronize(s->st);
     cleanup();
@@ -685,11 +709,13 @@ extern "C" int vimg_segment(vimg_segmenter* s, const float* d_prob, int K, float
   k_blob_scatter<<<grid_of(n_comp, 256), 256, 0, s->st>>>(breg, n_comp, roff, rcur, rblobs);
   // 3. clustering: N per region
   k_region_cluster<<<grid_of((long long)n_reg * 32, 256), 256, 0, s->st>>>(
-      rblobs, roff, rcnt, s->rpix, poff, pcnt, n_reg, s->list, off, cnt, HW, bclu, nreg);
+      rblobs, roff, rcnt, s->rpix, poff, pcnt, n_reg, s->list, off, cnt, HW, bclu, nreg, rstat);
   SCK(cudaGetLastError(), "clustering");
   std::vector<int> hN(n_reg), hM(n_reg);
   SCK(cudaMemcpyAsync(hN.data(), nreg, sizeof(int) * n_reg, cudaMemcpyDeviceToHost, s->st), "N");
   SCK(cudaMemcpyAsync(hM.data(), pcnt, sizeof(int) * n_reg, cudaMemcpyDeviceToHost, s->st), "M");
+  SCK(cudaMemcpyAsync(s->status.data(), rstat, sizeof(int) * n_reg, cudaMemcpyDeviceToHost, s->st),
+      "status");
   SCK(cudaStreamSynchronize(s->st), "N");
   std::vector<long long> hso(n_reg);
   std::vector<int> hno(n_reg);

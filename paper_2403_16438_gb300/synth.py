@@ -435,3 +435,28 @@ def planted_prob_maps(cfg: VideoConfig, K: int, seed: int = 0) -> torch.Tensor:
             x = int(torch.randint(0, W - 2, (1,), generator=g))
             out[i, y:y + 2, x:x + 2] = 0.8
     return out
+
+
+def disc_chain_maps() -> torch.Tensor:
+    """[2][96][760] float32 probability maps that stress the footprint
+    reconstruction's region size and neuron count.  Background 0.05; discs at
+    0.85 lighting up in alternate segments (disc k in segment k mod 2), so that
+    neighbours, which overlap, are separate blobs of different segments:
+      * a chain of 24 discs of radius 17 (908 px each) along row 24, centres
+        every 30 px from x = 20: one region of about 20,000 px made of 24 blobs;
+      * a chain of 40 discs of radius 4 (49 px each) along row 70, centres every
+        6 px from x = 10: one region of about 1,700 px made of 40 blobs;
+      * a lone disc of radius 6 at (75, 500) in segment 0: an ordinary region."""
+    H, W = 96, 760
+    yy, xx = torch.meshgrid(torch.arange(H), torch.arange(W), indexing="ij")
+    out = torch.full((2, H, W), 0.05)
+
+    def disc(cy, cx, r):
+        return ((yy - cy) ** 2 + (xx - cx) ** 2) <= r * r
+
+    for k in range(24):
+        out[k % 2][disc(24, 20 + 30 * k, 17)] = 0.85
+    for k in range(40):
+        out[k % 2][disc(70, 10 + 6 * k, 4)] = 0.85
+    out[0][disc(75, 500, 6)] = 0.85
+    return out

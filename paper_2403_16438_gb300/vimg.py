@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvimg.so")
 
 OK = 0
 ERR_ARG, ERR_NO_TEMPLATE, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_SIZE = -1, -2, -3, -4, -5, -6
+REGION_TOO_LARGE, REGION_TOO_MANY = 1, 2  # vimg_segment_status
 CORR_BF16, PROPOSAL_CNN, OUT_HIGHPASS, VIDEO_SUMMARY = 1, 2, 4, 8
 
 
@@ -69,7 +70,7 @@ EXPORTS = [
     "vimg_unet_last_error", "vimg_unet_load", "vimg_unet_run", "vimg_unet_synchronize",
     "vimg_unet_profile", "vimg_unet_profile_read", "vimg_attach_unet", "vimg_unet_activation",
     "vimg_video_summary", "vimg_segmenter_create", "vimg_segmenter_destroy",
-    "vimg_segmenter_last_error", "vimg_segment",
+    "vimg_segmenter_last_error", "vimg_segment", "vimg_segment_status",
 ]
 NSTAGES = 7
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy", "downstream"]
@@ -96,6 +97,8 @@ def _load():
     L.vimg_segmenter_last_error.restype = ctypes.c_char_p
     L.vimg_segment.argtypes = [vp, vp, i, vp, vp, i, vp, P(i)]
     L.vimg_segment.restype = i
+    L.vimg_segment_status.argtypes = [vp, vp, i]
+    L.vimg_segment_status.restype = i
     L.vimg_video_summary.argtypes = [vp, vp, vp]
     L.vimg_video_summary.restype = i
     L.vimg_set_rois.argtypes = [vp, vp, i]
@@ -470,3 +473,13 @@ class Segmenter:
             raise VimgError(n, lib.vimg_segmenter_last_error(self._s).decode())
         m = min(n, max_neurons)
         return foot[:m], act[:m], rmap, nreg.value
+
+    def status(self):
+        """Per-region status of the last run: 0 factorised, REGION_TOO_LARGE or
+        REGION_TOO_MANY (beyond the NMF kernel's capacity, not factorised)."""
+        n = lib.vimg_segment_status(self._s, None, 0)
+        if n < 0:
+            raise VimgError(n, "vimg_segment_status failed")
+        out = (ctypes.c_int * max(n, 1))()
+        lib.vimg_segment_status(self._s, out, n)
+        return [out[i] for i in range(n)]

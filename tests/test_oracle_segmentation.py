@@ -3,6 +3,7 @@ cleanup, OR over segments, connected components, NMF of Eq. 3)."""
 import math
 
 import numpy as np
+from scipy import ndimage
 from scipy.spatial import ConvexHull
 
 import oracle.segmentation as SG
@@ -146,3 +147,28 @@ def test_touching_pair_separates_into_two_footprints():
         assert max(mass) > 0.8            # each footprint concentrates on one disc
     m0 = [r["F"][own[0], j].sum() / r["F"][:, j].sum() for j in range(2)]
     assert (m0[0] > 0.8) != (m0[1] > 0.8)  # ... and on different discs
+
+
+def test_no_capacity_limit_on_region_size_or_neuron_count():
+    """The oracle factorises every region, however large and however many
+    clusters it holds: a 24-disc chain of about 20,000 px and a 40-disc chain
+    (N = 40) come out with one cluster per disc, and each footprint of the
+    40-disc chain concentrates on its own disc."""
+    from paper_2403_16438_gb300 import synth
+    prob = synth.disc_chain_maps().double().numpy()
+    K, H, W = prob.shape
+    regs = SG.regions(prob)
+    assert [r["N"] for r in regs] == [24, 40, 1]
+    lab, n = ndimage.label(prob.max(axis=0) > 0.5, structure=np.ones((3, 3), bool))
+    sizes = sorted(np.bincount(lab.ravel())[1:].tolist())
+    assert sorted(r["pixels"].size for r in regs) == sizes and sizes[-1] > 16000
+    big = regs[0]
+    F, A = SG.factorise(prob, regs[1])
+    assert F.shape == (regs[1]["pixels"].size, 40) and A.shape == (40, K)
+    yy, xx = np.divmod(regs[1]["pixels"], W)
+    for j in range(40):  # clusters in blob order: segment 0's discs, then segment 1's
+        k = 2 * j if j < 20 else 2 * (j - 20) + 1
+        own = (yy - 70) ** 2 + (xx - (10 + 6 * k)) ** 2 <= 16
+        assert F[own, j].sum() > 0.5 * F[:, j].sum()
+        assert A[j, k % 2] > 10 * A[j, 1 - k % 2]
+    assert big["pixels"].size > 16000
