@@ -128,8 +128,12 @@ typedef struct {
   float* corrected;       /* [n][H][W]                                          */
   float* summary;         /* [k][2][H][W]                                       */
   float* peak_info;       /* [n][4]: dy*, dx*, C(d*), second-largest C          */
-  double* surface;        /* [n][2R+1][2R+1] aggregated surface C_t (full window
-                             only; for diagnostics and parity checks)           */
+  double* surface;        /* [n][2R+1][2R+1] aggregated surface C_t, for
+                             diagnostics and parity checks.  With
+                             VIMG_PROPOSAL_CNN: the full surface for frames that
+                             fell back to the full window; for the others only
+                             the 7x7 narrow window is computed and every other
+                             entry is NaN                                       */
   const float* shifts_in; /* [n][2]: apply these shifts instead of estimating
                              them (the temporal stage alone)                    */
   float* traces;          /* [n][n_rois] voltage traces: the mean of the corrected
@@ -139,6 +143,10 @@ typedef struct {
                              call completes (U-Net of Sec. III-C on each summary
                              pair); needs `summary` and a U-Net attached with
                              vimg_attach_unet                                   */
+  float* proposal;        /* [n][2] the learned proposal (dy, dx) in px before
+                             rounding (VIMG_PROPOSAL_CNN only): the narrow window
+                             is centred on it, rounded to the nearest integer
+                             and clamped to [-(R-3), R-3]                       */
 } vimg_io;
 
 /* Voltage-trace ROIs (Sec. II: the third stage of the pipeline takes the mean

@@ -17,6 +17,9 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   peak (subpixel parabola): pinned to its closed form on exact quadratics;
   the paper itself prints no subpixel method, so agreement with the paper is
   a reading, not a pin.
+  narrow_center, narrow_estimate (learned-proposal window and fallback rule):
+  pinned to the full window's values and decisions; a reading of the task's
+  configuration, not of the paper.
 """
 from __future__ import annotations
 
@@ -139,6 +142,38 @@ def peak(C, dy0, dx0):
     info = np.zeros(3, np.float64)
     lib().orc_peak(_p(C), dy0, dx0, wy, wx, _p(s), _p(d), _p(info))
     return s, d, info
+
+
+def narrow_center(proposal_px, R, half=3):
+    """Centre of the narrow window: the proposal (dy, dx) in px rounded to the
+    nearest integer (halves to even), then clamped so that the window of
+    +-half stays inside [-R, R]; a non-finite proposal counts as 0."""
+    lim = R - half
+    c = []
+    for v in proposal_px:
+        v = float(v)
+        v = float(np.rint(min(64.0, max(-64.0, v)))) if np.isfinite(v) else 0.0
+        c.append(int(max(-lim, min(lim, v))))
+    return tuple(c)
+
+
+def narrow_estimate(F, T, R, proposal_px, thresh=0.5, half=3, P=21):
+    """Learned-proposal reading (task config 4; not in the paper): the surface
+    on the (2 half + 1)^2 displacements around narrow_center(proposal), its peak
+    and parabola (the peak() rules on that window); when d* lies on the window's
+    border (no neighbour for the parabola) or C(d*) < thresh, the full +-R
+    window decides instead.  Returns dict(center, fallback, shifts, dstar, info,
+    narrow = the window's surface)."""
+    cy, cx = narrow_center(proposal_px, R, half)
+    w = 2 * half + 1
+    Cn = surface(F, T, R, P, window=(cy - half, cx - half, w, w))
+    s, d, info = peak(Cn, cy - half, cx - half)
+    edge = int(info[2]) != 0
+    out = dict(center=(cy, cx), narrow=Cn, fallback=bool(edge or info[0] < thresh))
+    if out["fallback"]:
+        s, d, info = peak(surface(F, T, R, P), -R, -R)
+    out.update(shifts=s, dstar=d, info=info)
+    return out
 
 
 def resample(F, sy, sx):

@@ -433,7 +433,7 @@ extern "C" int vimg_set_rois(vimg_handle* h, const uint8_t* d_masks, int n_rois)
 
 // Motion estimate of nf frames (nf <= max_chunk) into shifts[nf][2].
 static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shifts,
-                    float* peak_info, double* surface) {
+                    float* peak_info, double* surface, float* prop_px) {
   const int R = h->p.search_radius;
   CK(cudaMemsetAsync(h->csum, 0, sizeof(unsigned long long) * (size_t)nf * h->nwin, h->st),
      "surface reset");
@@ -457,8 +457,11 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
        "narrow correlation launch");
     prof_end(h, ps);
     ps = prof_begin(h, 2);
+    if (surface)  // all-ones bytes: NaN wherever no displacement is evaluated
+      CK(cudaMemsetAsync(surface, 0xff, sizeof(double) * (size_t)nf * h->nwin, h->st),
+         "surface fill");
     CK(launch_peak_narrow(h->csum_n, nf, R, h->np, h->prop, h->p.fallback_zncc, shifts, peak_info,
-                          h->fb_list, h->fb_n, h->st),
+                          h->fb_list, h->fb_n, surface, prop_px, h->st),
        "narrow peak launch");
     prof_end(h, ps);
     ps = prof_begin(h, 0);
@@ -471,7 +474,7 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
        "fallback correlation launch");
     prof_end(h, ps);
     ps = prof_begin(h, 2);
-    CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, nullptr, h->st, h->fb_list, h->fb_n),
+    CK(launch_peak(h->csum, nf, R, h->np, shifts, peak_info, surface, h->st, h->fb_list, h->fb_n),
        "fallback peak launch");
     prof_end(h, ps);
     CK(launch_count_add(h->fb_n, h->fb_total, h->st), "fallback count");
@@ -578,7 +581,7 @@ static int process_batch(vimg_handle* h, const uint16_t* frames, int n, const vi
     shifts = io.shifts_in;
   } else {
     float* out = io.shifts ? io.shifts : h->shift_tmp;
-    int rc = estimate(h, frames, n, out, io.peak_info, io.surface);
+    int rc = estimate(h, frames, n, out, io.peak_info, io.surface, io.proposal);
     if (rc) return rc;
     shifts = out;
   }
@@ -642,6 +645,7 @@ extern "C" int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, 
     if (io->corrected) sub.corrected = io->corrected + HW * done;
     if (io->peak_info) sub.peak_info = io->peak_info + 4 * (size_t)done;
     if (io->surface) sub.surface = io->surface + (size_t)h->nwin * done;
+    if (io->proposal) sub.proposal = io->proposal + 2 * (size_t)done;
     if (io->traces) sub.traces = io->traces + (size_t)h->n_rois * done;
     int k = process_batch(h, d_frames + HW * done, m, sub, k_total);
     if (k < 0) return k;

@@ -854,10 +854,13 @@ cudaError_t launch_stats_narrow(const uint16_t* frames, int nf, int H, int W, Pa
 
 // Peak of the narrow window.  Falls back to the full window (frame appended to
 // the device-side list) when d* lies on the 7x7 border or C(d*) < threshold.
+// surface (optional): the 7x7 values at their places in the full (2R+1)^2 grid;
+// prop_px (optional): the proposal in px.
 __global__ void k_peak_narrow(const unsigned long long* __restrict__ csum, int R, int np,
                               const float* __restrict__ prop, float thresh,
                               float* __restrict__ shifts, float* __restrict__ info,
-                              int* __restrict__ list, int* __restrict__ list_n) {
+                              int* __restrict__ list, int* __restrict__ list_n,
+                              double* __restrict__ surface, float* __restrict__ prop_px) {
   const int f = blockIdx.x, lane = threadIdx.x, nw = kNarrow * kNarrow;
   const long long* C = reinterpret_cast<const long long*>(csum) + (size_t)f * nw;
   int cy, cx;
@@ -865,7 +868,18 @@ __global__ void k_peak_narrow(const unsigned long long* __restrict__ csum, int R
   Cand b, s2;
   float s[2];
   peak_of(C, kNarrow, kNarrow, cy - kNarrow / 2, cx - kNarrow / 2, np, lane, b, s2, s);
+  if (surface) {
+    const int w = 2 * R + 1;
+    for (int i = lane; i < nw; i += 32) {
+      const int y = cy - kNarrow / 2 + i / kNarrow + R, x = cx - kNarrow / 2 + i % kNarrow + R;
+      surface[(size_t)f * w * w + (size_t)y * w + x] = (double)C[i] / kFix / np;
+    }
+  }
   if (lane != 0) return;
+  if (prop_px) {
+    prop_px[2 * f] = prop[2 * f] * kShiftScale;
+    prop_px[2 * f + 1] = prop[2 * f + 1] * kShiftScale;
+  }
   const int iy = b.idx / kNarrow, ix = b.idx % kNarrow;
   const float cpk = (float)((double)b.v / kFix / np);
   const bool edge = iy == 0 || ix == 0 || iy == kNarrow - 1 || ix == kNarrow - 1;
@@ -913,9 +927,11 @@ cudaError_t launch_count_add(const int* n, long long* total, cudaStream_t st) {
 
 cudaError_t launch_peak_narrow(const unsigned long long* csum, int nf, int R, int np,
                                const float* prop, float thresh, float* shifts, float* info,
-                               int* list, int* list_n, cudaStream_t st) {
+                               int* list, int* list_n, double* surface, float* prop_px,
+                               cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
-  k_peak_narrow<<<nf, 32, 0, st>>>(csum, R, np, prop, thresh, shifts, info, list, list_n);
+  k_peak_narrow<<<nf, 32, 0, st>>>(csum, R, np, prop, thresh, shifts, info, list, list_n, surface,
+                                   prop_px);
   return cudaGetLastError();
 }
 

@@ -170,9 +170,12 @@ cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, f
 cudaError_t launch_corr_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                                const TemplateDev& td, const float* isf, const float* prop,
                                unsigned long long* csum, cudaStream_t st);
+// surface (optional): the 7x7 values placed in the full grid; prop_px (optional):
+// the proposals in px.
 cudaError_t launch_peak_narrow(const unsigned long long* csum, int nf, int R, int np,
                                const float* prop, float thresh, float* shifts, float* info,
-                               int* list, int* list_n, cudaStream_t st);
+                               int* list, int* list_n, double* surface, float* prop_px,
+                               cudaStream_t st);
 
 cudaError_t launch_count_add(const int* n, long long* total, cudaStream_t st);
 

@@ -46,6 +46,7 @@ class IO(ctypes.Structure):
         ("shifts_in", ctypes.c_void_p),
         ("traces", ctypes.c_void_p),
         ("prob", ctypes.c_void_p),
+        ("proposal", ctypes.c_void_p),
     ]
 
 
@@ -273,14 +274,15 @@ class Handle:
         self._check(lib.vimg_attach_unet(self._h, None if unet is None else unet._u))
 
     def process(self, frames, shifts=None, corrected=None, summary=None, peak_info=None,
-                surface=None, shifts_in=None, traces=None, prob=None) -> int:
+                surface=None, shifts_in=None, traces=None, prob=None, proposal=None) -> int:
         """frames: cuda uint16 [n,H,W].  Outputs are optional preallocated cuda
         tensors (see vimg_io; traces: float32 [n, n_rois]; prob: float32
-        [k, H, W], needs summary).  Returns k, the segments written."""
+        [k, H, W], needs summary; proposal: float32 [n, 2], learned proposals in
+        px).  Returns k, the segments written."""
         assert frames.is_cuda and frames.dtype == torch.uint16 and frames.is_contiguous()
         n = frames.shape[0]
         io = IO(_ptr(shifts), _ptr(corrected), _ptr(summary), _ptr(peak_info), _ptr(surface),
-                _ptr(shifts_in), _ptr(traces), _ptr(prob))
+                _ptr(shifts_in), _ptr(traces), _ptr(prob), _ptr(proposal))
         return self._check(lib.vimg_process_io(self._h, _ptr(frames), n, ctypes.byref(io)))
 
     def process_host(self, frames_host, shifts_host=None, summary_host=None,

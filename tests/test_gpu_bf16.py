@@ -7,13 +7,17 @@ import torch
 
 import oracle
 from paper_2403_16438_gb300 import synth
-from parity_util import NEAR_TIE, compare_images
+from parity_util import compare_images
+
+# Integer peaks of the BF16 path may differ from the oracle's where the
+# oracle's own top-2 gap is below this bound on the BF16 surface error.
+BF16_NEAR_TIE = 1e-3
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def run(vimg, frames, T, flags, **kw):
+def run(vimg, frames, T, flags, summary=False, **kw):
     n, H, W = frames.shape
     h = vimg.Handle(H, W, flags=flags, **kw)
     h.set_template(T.to(DEV))
@@ -22,10 +26,12 @@ def run(vimg, frames, T, flags, **kw):
     info = torch.zeros((n, 4), device=DEV)
     surf = torch.zeros((n, 33, 33), device=DEV, dtype=torch.float64)
     corr = torch.zeros((n, H, W), device=DEV)
-    h.process(fd, shifts=s, peak_info=info, surface=surf, corrected=corr)
+    summ = torch.zeros((max(n // 50, 1), 2, H, W), device=DEV) if summary else None
+    h.process(fd, shifts=s, peak_info=info, surface=surf, corrected=corr, summary=summ)
     assert h.synchronize() == 0
     h.close()
-    return s.cpu().numpy(), info.cpu().numpy(), surf.cpu().numpy(), corr.cpu().numpy()
+    out = [s.cpu().numpy(), info.cpu().numpy(), surf.cpu().numpy(), corr.cpu().numpy()]
+    return out + [summ.cpu().numpy()] if summary else out
 
 
 @pytest.fixture(scope="module")
@@ -35,19 +41,56 @@ def vimg():
 
 
 def test_bf16_against_oracle_paper_scale(vimg):
+    """Shifts against the oracle's own estimate (surface within 2e-3, integer
+    peak identical except near-ties, shift within 0.05 px).  Resampling and the
+    temporal state stay FP32 in this variant, so given the GPU's shifts the
+    corrected frames and the segment's summary images must equal the oracle's
+    within 1e-4, like the FP32 path."""
     cfg = synth.paper_scale_config(seed=77)
-    frames, planted, T = synth.make_video(cfg, 20)
-    s, info, surf, corr = run(vimg, frames, T, vimg.CORR_BF16)
+    frames, planted, T = synth.make_video(cfg, 50)
+    s, info, surf, corr, summ = run(vimg, frames, T, vimg.CORR_BF16, summary=True)
     o = oracle.Oracle(cfg.H, cfg.W)
     o.set_template(T.double().numpy())
-    r = o.process(frames.numpy(), want_surface=True)
+    r = o.process(frames.numpy(), want_surface=True, want_corrected=False, want_summary=False)
     assert np.abs(surf - r["surface"]).max() < 2e-3
     gap = r["info"][:, 0] - r["info"][:, 1]
     same = np.all(info[:, :2].astype(int) == r["dstar"], axis=1)
-    assert np.all(same | (gap < 1e-3))
+    assert np.all(same | (gap < BF16_NEAR_TIE))
     err = np.abs(s - r["shifts"]).max()
     assert err <= 0.05, err
-    compare_images(corr, r["corrected"], "corrected", tol=1e-3)
+    o = oracle.Oracle(cfg.H, cfg.W)
+    o.set_template(T.double().numpy())
+    rg = o.process(frames.numpy(), shifts_in=s.astype(np.float64))
+    compare_images(corr, rg["corrected"], "corrected")
+    compare_images(summ[0], rg["summary"][0], "summary")
+
+
+def test_bf16_shift_differences_on_the_benchmark_video_are_near_ties(vimg):
+    """On the whole 10,000-frame benchmark video, every frame whose BF16 shift
+    is more than 0.05 px from the FP32 path's has an integer peak that the
+    oracle itself rates a near-tie at BF16 precision: its top-2 gap is below
+    BF16_NEAR_TIE (the BF16 surface error bound)."""
+    cfg = synth.paper_scale_config()
+    frames, _, T = synth.make_video(cfg, cfg.n_frames, device=DEV)
+    outs = {}
+    for name, flags in (("bf16", vimg.CORR_BF16), ("fp32", 0)):
+        h = vimg.Handle(cfg.H, cfg.W, flags=flags, max_chunk=250)
+        h.set_template(T)
+        sh = torch.zeros((cfg.n_frames, 2), device=DEV)
+        h.process(frames, shifts=sh)
+        assert h.synchronize() == 0
+        h.close()
+        outs[name] = sh.cpu().numpy()
+    d = np.abs(outs["bf16"] - outs["fp32"]).max(axis=1)
+    idx = np.nonzero(d > 0.05)[0]
+    assert len(idx) <= 5, d[idx]
+    if len(idx):
+        o = oracle.Oracle(cfg.H, cfg.W)
+        o.set_template(T.cpu().double().numpy())
+        r = o.process(np.stack([frames[int(i)].cpu().numpy() for i in idx]), want_corrected=False,
+                      want_summary=False)
+        gap = r["info"][:, 0] - r["info"][:, 1]
+        assert np.all(gap < BF16_NEAR_TIE), (idx, gap, d[idx])
 
 
 @pytest.mark.parametrize("H,W,n,chunk", [(300, 250, 37, 24), (128, 128, 16, 24),

@@ -1,15 +1,19 @@
 """Learned shift proposal on the GPU: the CUDA forward/backward against the FP64
 CPU oracle (gradient check), training progress with the library's own
-kernels, and the proposal path (CNN -> +-2 px window -> full-window fallback)
-against the full-window path, which stays the reference for its error."""
+kernels, the proposal path (CNN -> +-2 px window -> full-window fallback)
+against the FP64 oracle's narrow-window estimate frame by frame (window
+values, peak, parabola and the fallback decision), and against the
+full-window path, which stays the reference for its error."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from oracle import cnn as ocnn
 from paper_2403_16438_gb300 import synth
+from parity_util import NEAR_TIE, SHIFT_TOL
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -106,3 +110,64 @@ def test_proposal_path_against_full_window(trained):
     if len(idx):
         a, b = outs["full"][2][idx], outs["prop"][2][idx]
         assert ((a - b).abs().max() / a.abs().max()).item() <= 1e-4
+
+
+@pytest.mark.parametrize("thresh", [0.5, 0.99])
+def test_narrow_window_against_the_oracle(trained, thresh):
+    """For every frame, with the GPU's own proposal as the window centre: the
+    7x7 surface within 2e-6 of the oracle's, the integer peak identical (except
+    near-ties), the shift within 0.01 px, and the fallback decision (peak on the
+    window border, or C(d*) below the threshold) the oracle's.  A threshold of
+    0.99 forces fallbacks, and frame 5 is a frame of another scene (a weak peak
+    everywhere); frames that fall back carry the full surface, checked too."""
+    from paper_2403_16438_gb300 import vimg
+    cfg = synth.paper_scale_config(seed=2025)
+    n, R = 16, 16
+    frames, _, T = synth.make_video(cfg, n)
+    other, _, _ = synth.make_video(synth.paper_scale_config(seed=99), 1)
+    frames[5] = other[0]
+    h = vimg.Handle(cfg.H, cfg.W, flags=vimg.PROPOSAL_CNN, fallback_zncc=thresh)
+    h.set_template(T.to(DEV))
+    h.load_proposal(trained)
+    s = torch.zeros((n, 2), device=DEV)
+    info = torch.zeros((n, 4), device=DEV)
+    surf = torch.zeros((n, 2 * R + 1, 2 * R + 1), device=DEV, dtype=torch.float64)
+    prop = torch.zeros((n, 2), device=DEV)
+    h.process(frames.to(DEV), shifts=s, peak_info=info, surface=surf, proposal=prop)
+    assert h.synchronize() == 0
+    fr, fb = h.proposal_stats()
+    h.close()
+    s, info, surf, prop = (t.cpu().numpy() for t in (s, info, surf, prop))
+    Tn = T.double().numpy()
+    n_fb = 0
+    for f in range(n):
+        F = frames[f].numpy()
+        r = oracle.narrow_estimate(F, Tn, R, prop[f], thresh=thresh)
+        cy, cx = r["center"]
+        win = (slice(cy - 3 + R, cy + 4 + R), slice(cx - 3 + R, cx + 4 + R))
+        gpu_fb = bool(np.isfinite(surf[f]).all())
+        near_thr = abs(r["info"][0] - thresh) < NEAR_TIE if not r["fallback"] else False
+        if not gpu_fb:
+            inside = np.zeros_like(surf[f], bool)
+            inside[win] = True
+            assert np.isnan(surf[f][~inside]).all()
+            assert np.abs(surf[f][win] - r["narrow"]).max() < 2e-6
+        else:
+            n_fb += 1
+            full = oracle.surface(F, Tn, R)
+            assert np.abs(surf[f] - full).max() < 2e-6
+        # the decision; only a peak within rounding of the threshold, or a
+        # near-tie between a border and an inner displacement, may differ
+        if gpu_fb != r["fallback"]:
+            Cn = np.sort(r["narrow"].ravel())
+            assert near_thr or Cn[-1] - Cn[-2] < NEAR_TIE, (f, gpu_fb, r["info"])
+            continue
+        gap = r["info"][0] - r["info"][1]
+        if gap >= NEAR_TIE:
+            assert tuple(info[f, :2].astype(int)) == tuple(r["dstar"]), f
+            assert np.abs(s[f] - r["shifts"]).max() <= SHIFT_TOL, (f, s[f], r["shifts"])
+    assert fr == n and fb == n_fb
+    if thresh > 0.9:
+        assert n_fb >= n // 2  # the high threshold forces fallbacks
+    else:
+        assert n_fb < n and bool(np.isfinite(surf[5]).all())  # the foreign frame falls back

@@ -148,6 +148,51 @@ def test_planted_integer_shift_noise_free(sy, sx):
     assert abs(info[0] - 1.0) < 1e-12 and info[1] < 1.0 - 1e-3
 
 
+def test_narrow_center_rounding_and_clamp():
+    """Round to nearest, halves to even (as the proposal is rounded on the GPU);
+    clamp so the 7x7 window stays in [-R, R]; non-finite -> 0."""
+    c = oracle.narrow_center
+    assert c((2.5, -2.5), 16) == (2, -2) and c((3.5, -0.49), 16) == (4, 0)
+    assert c((14.0, -30.0), 16) == (13, -13) and c((float("nan"), float("inf")), 16) == (0, 0)
+    assert c((1.6, 5.0), 4) == (1, 1)
+
+
+def test_narrow_window_agrees_with_the_full_window_near_the_truth():
+    """Noise-free integer shift with a proposal within 2 px of it: the full
+    window's peak lies inside the narrow window, off its border, so the narrow
+    estimate uses the same three values per axis as the full window and gives
+    its shift exactly, without falling back."""
+    m = 12
+    S = np.round(_texture((90 + 2 * m, 94 + 2 * m), 9))
+    T = S[m:m + 90, m:m + 94]
+    for (sy, sx), prop in [((3, -5), (4.2, -3.6)), ((-6, 7), (-6.4, 8.9)), ((0, 0), (1.1, 0.3))]:
+        F = S[m - sy:m - sy + 90, m - sx:m - sx + 94].astype(np.uint16)
+        r = oracle.narrow_estimate(F, T, 10, prop)
+        C = oracle.surface(F, T, 10)
+        s, d, info = oracle.peak(C, -10, -10)
+        assert not r["fallback"] and tuple(r["dstar"]) == (sy, sx) == tuple(d)
+        assert np.array_equal(r["shifts"], s)
+        cy, cx = r["center"]
+        assert np.array_equal(r["narrow"], C[cy - 3 + 10:cy + 4 + 10, cx - 3 + 10:cx + 4 + 10])
+
+
+def test_narrow_window_falls_back_far_from_the_truth_or_below_threshold():
+    """A proposal 7 px off puts the narrow peak on the window border (the
+    surface rises towards the true shift); a threshold above 1 rejects every
+    peak: both fall back to exactly the full window's estimate."""
+    m = 12
+    S = np.round(_texture((90 + 2 * m, 94 + 2 * m), 10))
+    T = S[m:m + 90, m:m + 94]
+    F = S[m - 4:m - 4 + 90, m + 2:m + 2 + 94].astype(np.uint16)
+    s, d, info = oracle.peak(oracle.surface(F, T, 10), -10, -10)
+    for prop, thr in [((-3.0, -2.0), 0.5), ((4.0, -2.0), 1.01)]:
+        r = oracle.narrow_estimate(F, T, 10, prop, thresh=thr)
+        assert r["fallback"] and tuple(r["dstar"]) == (4, -2) == tuple(d)
+        assert np.array_equal(r["shifts"], s)
+    r = oracle.narrow_estimate(F, T, 10, (4.0, -2.0), thresh=0.5)
+    assert not r["fallback"] and tuple(r["dstar"]) == (4, -2)
+
+
 def test_constant_frame_gives_zero_surface_and_origin():
     F = np.full((64, 64), 1234, np.uint16)
     C = oracle.surface(F, _texture((64, 64), 6), 5)
