@@ -14,19 +14,27 @@
 // Every 3x3 convolution and up-convolution is an implicit GEMM on the tensor
 // cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulation in TMEM):
 //   D[pixel][n] = sum_{tap, ci} A[pixel][(tap, ci)] * B[(tap, ci)][n]
-// M = 128 consecutive pixels of the NHWC activations (whole image rows, or
-// whole images below 128 px), N = output channels (x 4 quadrants for an
-// up-convolution), K = taps x input channels in chunks of up to 64 channels.
-// A chunk (one tap) arrives by TMA from the activations as 8-channel boxes of
-// 128 pixels shifted by the tap (zero fill outside the image gives the
-// padding); these boxes are exactly the K-major core-matrix layout (8 pixels x
-// 16 B per core matrix, 2 KB between 8-channel groups).  B chunks are weights
-// pre-packed in the same layout and fetched by one bulk copy.
+// M = 128 consecutive pixels of the activation array, N = output channels (x 4
+// quadrants for an up-convolution), K = taps x input channels in chunks.
+// Activations live in 8-channel planes [C/8][guard + pixels + guard][8] (BF16),
+// so the 8 channels of 8 consecutive pixels form one K-major core matrix
+// (8 rows x 16 B).  On the 64, 32 and 16 px levels every image carries a
+// one-pixel zero border and the planes zero guard zones that no kernel
+// writes: tap (dy, dx) of a 3x3 convolution then reads pixel i + dy (s + 2) +
+// dx of the same plane, so one contiguous halo per plane, fetched by one bulk
+// copy, serves all nine taps through shifted shared-memory descriptors, and up
+// to four 128-row subtiles share a halo (independent accumulators, interleaved
+// MMAs).  The 8 and 4 px levels are stored dense and take one im2col TMA box
+// per tap and plane (zero fill outside the image gives the padding).  B chunks
+// are weights pre-packed in the same core-matrix layout; a layer's weights
+// stay in shared memory when they fit.  Per layer, the configuration (channels
+// per chunk, subtiles, stages, one or two CTAs per SM) is chosen by the
+// estimated L2 -> SM bytes per output row.
 //
 // Warp roles (persistent CTAs, 192 threads): warp 4 producer, warp 5 MMA
 // issuer, warps 0-3 epilogue (TMEM lane = pixel): + bias, ReLU, BF16 stores
-// into NHWC at a channel offset (which forms the concatenations in place), or
-// the 2x2 scatter of an up-convolution.  Two TMEM accumulators let the
+// into the planes at a plane offset (which forms the concatenations in place),
+// or the 2x2 scatter of an up-convolution.  Two TMEM accumulators let the
 // epilogue of one tile overlap the MMAs of the next.  Every wait is bounded:
 // on timeout the CTA records an error, stops issuing, drains its own copies and
 // MMAs, frees its tensor memory and returns.
