@@ -68,6 +68,12 @@ extern "C" {
 #define VIMG_OUT_HIGHPASS 4   /* corrected output holds the high-passed video    */
 #define VIMG_VIDEO_SUMMARY 8  /* accumulate the whole-video average and local
                                  correlation images (vimg_video_summary)          */
+#define VIMG_TEMPORAL_SMEM 16 /* run the general temporal kernel (segment history
+                                 in shared memory) even where the faster one
+                                 (history in tensor memory, TMA-staged frames)
+                                 applies; same results, for comparisons. The
+                                 faster kernel needs W a multiple of 8, 16-byte
+                                 aligned frame buffers and no high-pass output   */
 
 typedef struct vimg_handle vimg_handle;
 

@@ -231,7 +231,8 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     fail(nullptr, VIMG_ERR_ARG, "max_chunk must be in 1..4096");
     return nullptr;
   }
-  if (p.flags & ~(VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_OUT_HIGHPASS | VIMG_VIDEO_SUMMARY)) {
+  if (p.flags & ~(VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_OUT_HIGHPASS | VIMG_VIDEO_SUMMARY |
+                  VIMG_TEMPORAL_SMEM)) {
     fail(nullptr, VIMG_ERR_ARG, "unknown flag bits");
     return nullptr;
   }
@@ -530,6 +531,8 @@ static TemporalArgs temporal_args(const vimg_handle* h, const uint16_t* frames, 
             ((reinterpret_cast<uintptr_t>(a.src.carry) & 3) == 0);
   a.corrected = corrected;
   a.summary = summary;
+  a.err = h->dev_err;
+  a.smem_history = (h->p.flags & VIMG_TEMPORAL_SMEM) ? 1 : 0;
   return a;
 }
 

@@ -28,7 +28,9 @@
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <cstring>
 
+#include "tc_ptx.h"
 #include "vimg_internal.h"
 
 namespace vimg {
@@ -76,12 +78,12 @@ __device__ __forceinline__ void sort_net(float* v) {
 
 // Median of 50 values: sort both halves, then the k-th smallest of two sorted
 // runs A, B is min_i max(A[i-1], B[k-1-i]).
-__device__ __forceinline__ float median50(const float* __restrict__ h, int stride) {
+__device__ __forceinline__ float median50_v(const float (&h)[50]) {
   float a[32], b[32];
 #pragma unroll
   for (int i = 0; i < 25; ++i) {
-    a[i] = h[i * stride];
-    b[i] = h[(25 + i) * stride];
+    a[i] = h[i];
+    b[i] = h[25 + i];
   }
   sort_net<32, 25>(a);
   sort_net<32, 25>(b);
@@ -94,11 +96,11 @@ __device__ __forceinline__ float median50(const float* __restrict__ h, int strid
   return 0.5f * (m25 + m26);
 }
 
-// Median of n <= 50 values (any n): pad to 64 with +inf, sort, pick.
-__device__ __forceinline__ float median_any(const float* __restrict__ h, int stride, int n) {
+// Median of the first n <= 50 values (any n): pad to 64 with +inf, sort, pick.
+__device__ __forceinline__ float median_any_v(const float (&h)[50], int n) {
   float v[64];
 #pragma unroll
-  for (int i = 0; i < 64; ++i) v[i] = i < n ? h[i * stride] : FLT_MAX;
+  for (int i = 0; i < 64; ++i) v[i] = (i < 50 && i < n) ? h[i] : FLT_MAX;
   sort_net<64, 64>(v);
   float lo = 0.f, hi = 0.f;
   const int il = (n - 1) / 2, ih = n / 2;
@@ -108,6 +110,20 @@ __device__ __forceinline__ float median_any(const float* __restrict__ h, int str
     if (i == ih) hi = v[i];
   }
   return 0.5f * (lo + hi);
+}
+
+__device__ __forceinline__ float median50(const float* __restrict__ h, int stride) {
+  float v[50];
+#pragma unroll
+  for (int i = 0; i < 50; ++i) v[i] = h[i * stride];
+  return median50_v(v);
+}
+
+__device__ __forceinline__ float median_any(const float* __restrict__ h, int stride, int n) {
+  float v[50];
+#pragma unroll
+  for (int i = 0; i < 50; ++i) v[i] = i < n ? h[i * stride] : FLT_MAX;
+  return median_any_v(v, n);
 }
 
 // ---- resampling ----------------------------------------------------------------
@@ -529,12 +545,421 @@ static size_t temporal_smem(int L) {
          sizeof(unsigned short) * (kFstRows * kFst);
 }
 
-cudaError_t temporal_init() {
-  static unsigned char done[kMaxDevices] = {};
-  return once_per_device(done, [](int) {
-    return cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)temporal_smem(kMaxL));
-  });
+
+
+// ---- the fused pass with the segment history in tensor memory -------------------
+// Same arithmetic as k_temporal (corrected frames and T_i bit for bit; S_i adds
+// the frames in two interleaved partial sums), for launches without the
+// high-pass output, widths that are multiples of 8 and 16-byte aligned frame
+// buffers.  A CTA still owns one 32x32 output tile for one segment slot, but:
+//   * the segment's smoothed history (up to 50 frames x 1,024 pixels) lives in
+//     the SM's tensor memory (128 lanes x 512 columns) instead of 200 KB of
+//     shared memory;
+//   * two groups of 8 warps take alternate frames, each with its own buffers
+//     and named barrier, so that one group computes while the other waits;
+//   * each frame's 57 x 64 source window arrives as one TMA box (3-D map over
+//     [frames][H][W]) in a double buffer per group, two of the group's frames
+//     ahead; rows and columns of a window outside the image are then filled
+//     from the nearest edge (the clamped coordinates of the resampling).
+// Tensor memory: warp w (0..7) of a group reaches lanes 32 (w mod 4) .. +31.
+// Thread (w, lane) owns the tile pixels (4 w + i, lane), i = 0..3, and keeps
+// pixel i's smoothed value of segment frame t at column 64 q + t, q = 4 (w / 4)
+// + i.  The other group's thread with the same (w, lane) owns the same pixels
+// (and lanes): at the segment's end each group takes two of them for the median.
+constexpr int kTmThreads = 512, kTmGroup = 256;
+constexpr int kStCols = 64, kStRows = kFstRows;       // source window of one frame (uint16)
+constexpr int kStBytes = kStCols * kStRows * 2;        // 7,296 B: one TMA box
+constexpr int kStStride = 7424;                        // stage buffer pitch (128-byte multiple)
+constexpr int kVS = 60;   // resampled-tile row stride: 128-bit row-pass loads without conflicts
+constexpr int kHS = 36;   // row-pass output row stride: 128-bit stores without conflicts
+constexpr int kTmCols = 512;
+constexpr size_t kTmSmemUsed = 4 * (size_t)kStStride +
+                               sizeof(float) * (2 * (size_t)kExt * (kVS + kHS) + 2 * kMaxL);
+// Shared memory requested per CTA: more than half of the SM's, so that one CTA
+// (which holds all of the SM's tensor memory) runs per SM.
+constexpr size_t kTmSmem = kTmSmemUsed > 120 * 1024 ? kTmSmemUsed : 120 * 1024;
+static_assert(2 * 2 * 2 * kTmGroup * sizeof(float) <= 2 * sizeof(float) * kExt * kVS,
+              "partial-sum exchange fits the resampled-tile buffers");
+
+struct TemporalMaps {
+  CUtensorMap m[kMaxVideos][2];  // per job: [0] carry buffer, [1] caller's batch
+};
+
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTmGroup) : "memory");
+}
+
+// Group barrier that also returns the OR of `v` over the group's threads.
+__device__ __forceinline__ bool group_bar_or(int id, bool v) {
+  int r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\nselp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((int)v), "r"(id), "r"(kTmGroup)
+      : "memory");
+  return r != 0;
+}
+
+// One uint16 half of a 32-bit word as an exact float: the byte permute builds
+// the bits of 2^23 + u, and subtracting 2^23 is exact.
+__device__ __forceinline__ float u16f(unsigned w, unsigned sel) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.0f;
+}
+constexpr unsigned kSelLo = 0x7410u, kSelHi = 0x7432u;
+
+// Source window of frame fi for a tile: rows r0 .. r0 + 56 and columns c0e ..
+// c0e + 63, c0e = the window's first column rounded down to a multiple of 8
+// (TMA boxes start on 16-byte boundaries), ox = the remainder.
+struct WinGeom {
+  float fy, fx;
+  int r0, c0e, ox;
+  bool meets;   // the window overlaps the image (its edge rows / columns are inside it)
+  bool inside;  // the window lies inside the image
+};
+
+__device__ __forceinline__ WinGeom win_geom(const float* shs, int fi, int ty0, int tx0, int H,
+                                            int W) {
+  // shifts beyond +-2^20 px resample to the same edge pixels; bounding them
+  // keeps the integer arithmetic in range
+  const float sy = fminf(fmaxf(shs[2 * fi], -1048576.f), 1048576.f);
+  const float sx = fminf(fmaxf(shs[2 * fi + 1], -1048576.f), 1048576.f);
+  const Split a = split_shift(sy), b = split_shift(sx);
+  WinGeom g;
+  g.fy = a.f;
+  g.fx = b.f;
+  g.r0 = ty0 - kGaussMaxRadius + a.i;
+  const int c0 = tx0 - kGaussMaxRadius + b.i;
+  g.c0e = c0 & ~7;
+  g.ox = c0 - g.c0e;
+  g.meets = g.r0 + kStRows - 1 >= 0 && g.r0 <= H - 1 && g.c0e + kStCols - 1 >= 0 && g.c0e <= W - 1;
+  g.inside = g.r0 >= 0 && g.r0 + kStRows - 1 <= H - 1 && g.c0e >= 0 && g.c0e + kStCols - 1 <= W - 1;
+  return g;
+}
+
+__global__ void __launch_bounds__(kTmThreads, 1)
+    k_temporal_tm(const __grid_constant__ TemporalBatch b, const __grid_constant__ TemporalMaps maps) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t full[2][2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_any;
+  const int jb = job_of(b.begin, b.n, blockIdx.x);
+  const TemporalArgs& a = b.a[jb];
+  const int H = a.H, W = a.W, L = a.L, HW = H * W;
+  const int ntx = (W + kTile - 1) / kTile, tiles = ntx * ((H + kTile - 1) / kTile);
+  const int local = blockIdx.x - b.begin[jb];
+  const int slot = local / tiles, tile = local - slot * tiles;
+  const int ty0 = (tile / ntx) * kTile, tx0 = (tile % ntx) * kTile;
+  const int tid = threadIdx.x, grp = tid >> 8, gt = tid & (kTmGroup - 1), wg = gt >> 5;
+  const int lane = tid & 31, bar_id = 1 + grp;
+  unsigned char* stage = smraw + grp * 2 * kStStride;  // [2][kStStride] this group's windows
+  float* fbase = reinterpret_cast<float*>(smraw + 4 * kStStride);
+  float* vext = fbase + grp * (kExt * kVS);                   // [56][kVS] resampled tile + halo
+  float* hbuf = fbase + 2 * kExt * kVS + grp * (kExt * kHS);  // [56][kHS] row-smoothed
+  float* shs = fbase + 2 * kExt * (kVS + kHS);                // [L][2] shifts of the slot
+  const FrameSource& src = a.src;
+  const long long t_end = src.t_first + src.n_carry + src.n_batch;
+  const long long s0 = a.seg_base + (long long)slot * L;
+  const long long s1 = s0 + L < t_end ? s0 + L : t_end;
+  const int nfr = (int)(s1 - s0);
+  const bool complete = s0 + L <= t_end;
+
+  if (tid < 32) tc::tmem_alloc(&tmem_slot, kTmCols);
+  if (tid == 0) {
+    for (int g = 0; g < 2; ++g)
+      for (int k = 0; k < 2; ++k) tc::mbar_init(&full[g][k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_any = 0;
+  }
+  for (int i = tid; i < 2 * nfr; i += kTmThreads) {
+    const long long v = s0 + (i >> 1) - src.t_first;
+    shs[i] = v < src.n_carry ? src.carry_shift[2 * v + (i & 1)]
+                             : src.batch_shift[2 * (v - src.n_carry) + (i & 1)];
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tlane = tmem_slot + ((uint32_t)(32 * (wg & 3)) << 16);
+  const uint32_t tcol0 = (uint32_t)(64 * 4 * (wg >> 2));
+
+  float w[kTaps];
+#pragma unroll
+  for (int i = 0; i < kTaps; ++i) w[i] = a.gw[i];
+
+  // this thread's pixels: (yb + i, x), i = 0..3
+  const int x = tx0 + lane, yb = ty0 + 4 * wg;
+  bool myroi = false;
+  if (a.roi_acc && x < W)
+    for (int i = 0; i < 4; ++i)
+      if (yb + i < H && __ldg(a.roi_members + (size_t)(yb + i) * W + x)) myroi = true;
+  const bool roi_warp = __any_sync(0xffffffffu, myroi);
+  const bool mirror_rows = ty0 - kGaussMaxRadius < 0 || ty0 + kTile + kGaussMaxRadius > H;
+  const bool mirror_cols = tx0 - kGaussMaxRadius < 0 || tx0 + kTile + kGaussMaxRadius > W;
+
+  // frames grp, grp + 2, ... of the slot; the k-th goes to buffer k mod 2
+  const int nmine = nfr > grp ? (nfr - grp + 1) / 2 : 0;
+  auto issue = [&](int fi, int buf) {
+    const WinGeom g = win_geom(shs, fi, ty0, tx0, H, W);
+    if (!g.meets) return;  // filled by plain loads when consumed
+    const long long v = s0 + fi - src.t_first;
+    const int which = v < src.n_carry ? 0 : 1;
+    const int z = (int)(which ? v - src.n_carry : v);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::mbar_expect_tx(&full[grp][buf], kStBytes);
+    tc::tma_load_3d(stage + buf * kStStride, &maps.m[jb][which], g.c0e, g.r0, z, &full[grp][buf]);
+  };
+  uint32_t pending = 0;  // (thread gt == 0) buffers with a copy in flight
+  if (gt == 0) {
+    for (int k = 0; k < 2 && k < nmine; ++k) {
+      issue(grp + 2 * k, k);
+      if (win_geom(shs, grp + 2 * k, ty0, tx0, H, W).meets) pending |= 1u << k;
+    }
+  }
+
+  float sum[4] = {0.f, 0.f, 0.f, 0.f};
+  float mx[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+  uint32_t phase = 0;  // bit k: parity of buffer k's next completion
+  bool aborted = false;
+  for (int k = 0; k < nmine; ++k) {
+    const int fi = grp + 2 * k, buf = k & 1;
+    const long long t = s0 + fi;
+    const WinGeom g = win_geom(shs, fi, ty0, tx0, H, W);
+    unsigned short* st16 = reinterpret_cast<unsigned short*>(stage + buf * kStStride);
+    bool late = false;
+    if (g.meets) {
+      late = !tc::mbar_wait(&full[grp][buf], (phase >> buf) & 1);
+      phase ^= 1u << buf;
+      if (gt == 0 && !late) pending &= ~(1u << buf);
+    }
+    if (group_bar_or(bar_id, late)) {
+      aborted = true;
+      break;
+    }
+    // 1. the window at clamped coordinates
+    if (!g.meets) {
+      // entirely outside: every sample is an edge pixel of the frame
+      const long long v = t - src.t_first;
+      const uint16_t* F = v < src.n_carry ? src.carry + (size_t)v * HW
+                                          : src.batch + (size_t)(v - src.n_carry) * HW;
+      for (int i = gt; i < kStRows * kStCols; i += kTmGroup) {
+        const int r = i >> 6, c = i & 63;
+        const int rr = min(max(g.r0 + r, 0), H - 1), cc = min(max(g.c0e + c, 0), W - 1);
+        st16[i] = __ldg(F + (size_t)rr * W + cc);
+      }
+      group_bar(bar_id);
+    } else if (!g.inside) {
+      // rows / columns outside the image (zeros from the TMA) take the value at
+      // the clamped position, which lies inside the image and inside the window
+      for (int i = gt; i < kStRows * kStCols; i += kTmGroup) {
+        const int r = i >> 6, c = i & 63;
+        const int rr = min(max(g.r0 + r, 0), H - 1) - g.r0;
+        const int cc = min(max(g.c0e + c, 0), W - 1) - g.c0e;
+        if (rr != r || cc != c) st16[i] = st16[(rr << 6) + cc];
+      }
+      group_bar(bar_id);
+    }
+    // 2. resample the tile + halo: thread = 2 columns x 7 rows; each source row
+    //    is read as two 32-bit words, lerped along x once and shared by the two
+    //    output rows it feeds (same formula and order as k_temporal)
+    if (gt < 224) {
+      const int p = gt % 28, kc = gt / 28;
+      const unsigned* sw =
+          reinterpret_cast<const unsigned*>(st16) + kc * 7 * (kStCols / 2) + ((2 * p + g.ox) >> 1);
+      const bool odd = g.ox & 1;
+      const unsigned sa = odd ? kSelHi : kSelLo, sb = odd ? kSelLo : kSelHi;
+      float* vo = vext + kc * 7 * kVS + 2 * p;
+      float ph0 = 0.f, ph1 = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const unsigned w0 = sw[j * (kStCols / 2)], w1 = sw[j * (kStCols / 2) + 1];
+        const float va = u16f(w0, sa), vb = u16f(odd ? w1 : w0, sb), vc = u16f(w1, sa);
+        const float h0 = fmaf(g.fx, vb - va, va), h1 = fmaf(g.fx, vc - vb, vb);
+        if (j > 0)
+          *reinterpret_cast<float2*>(vo + (j - 1) * kVS) =
+              make_float2(fmaf(g.fy, h0 - ph0, ph0), fmaf(g.fy, h1 - ph1, ph1));
+        ph0 = h0;
+        ph1 = h1;
+      }
+    }
+    group_bar(bar_id);  // window consumed, tile resampled
+    if (gt == 0 && k + 2 < nmine) {
+      issue(fi + 4, buf);
+      if (win_geom(shs, fi + 4, ty0, tx0, H, W).meets) pending |= 1u << buf;
+    }
+    // 3. halo rows, then halo columns, outside the image: mirrored (Eq. 2's border)
+    if (mirror_rows) {
+      const int nt = max(0, kGaussMaxRadius - ty0), nb = max(0, ty0 + kTile + kGaussMaxRadius - H);
+      for (int i = gt; i < (nt + nb) * 64; i += kTmGroup) {
+        const int kk = i >> 6, rx = i & 63;
+        if (rx >= kExt) continue;
+        const int ry = kk < nt ? kk : kExt - nb + (kk - nt);
+        const int rs = mirror_idx(ty0 - kGaussMaxRadius + ry, H) - (ty0 - kGaussMaxRadius);
+        if (rs >= 0 && rs < kExt) vext[ry * kVS + rx] = vext[rs * kVS + rx];
+      }
+      group_bar(bar_id);
+    }
+    if (mirror_cols) {
+      const int nl = max(0, kGaussMaxRadius - tx0), nr = max(0, tx0 + kTile + kGaussMaxRadius - W);
+      for (int i = gt; i < (nl + nr) * 64; i += kTmGroup) {
+        const int kk = i >> 6, ry = i & 63;
+        if (ry >= kExt) continue;
+        const int rx = kk < nl ? kk : kExt - nr + (kk - nl);
+        const int cs = mirror_idx(tx0 - kGaussMaxRadius + rx, W) - (tx0 - kGaussMaxRadius);
+        if (cs >= 0 && cs < kExt) vext[ry * kVS + rx] = vext[ry * kVS + cs];
+      }
+      group_bar(bar_id);
+    }
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      v[i] = vext[(kGaussMaxRadius + 4 * wg + i) * kVS + kGaussMaxRadius + lane];
+    // 4. row pass of the Gaussian: thread = one row x 8 output columns
+    if (gt < 224) {
+      const int r = gt >> 2, cg = gt & 3;
+      const float* in = vext + r * kVS + cg * 8;
+      float xv[32];
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(in + i);
+        xv[i] = q.x, xv[i + 1] = q.y, xv[i + 2] = q.z, xv[i + 3] = q.w;
+      }
+      float o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) o[j] = 0.f;
+#pragma unroll
+      for (int m = 0; m < kTaps; ++m)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = fmaf(w[m], xv[j + m], o[j]);
+      float* out = hbuf + r * kHS + cg * 8;
+      *reinterpret_cast<float4*>(out) = make_float4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<float4*>(out + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    group_bar(bar_id);
+    // 5. column pass: four output rows of one column per thread, each in two
+    //    chains (even and odd taps) as in k_temporal
+    float col[kTaps + 3];
+#pragma unroll
+    for (int kk = 0; kk < kTaps + 3; ++kk) col[kk] = hbuf[(4 * wg + kk) * kHS + lane];
+    float vb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float be = 0.f, bo = 0.f;
+#pragma unroll
+      for (int m = 0; m + 1 < kTaps; m += 2) {
+        be = fmaf(w[m], col[i + m], be);
+        bo = fmaf(w[m + 1], col[i + m + 1], bo);
+      }
+      vb[i] = fmaf(w[kTaps - 1], col[i + kTaps - 1], be) + bo;
+    }
+    // 6. outputs of frames new to this call, traces, segment accumulators and
+    //    the smoothed history
+    const bool fresh = t >= src.t_new;
+    if (fresh && a.corrected && x < W) {
+      float* out = a.corrected + (size_t)(t - src.t_new) * HW + x;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (yb + i < H) out[(size_t)(yb + i) * W] = v[i];
+    }
+    if (roi_warp && fresh) {
+      unsigned long long m[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        m[i] = (x < W && yb + i < H) ? __ldg(a.roi_members + (size_t)(yb + i) * W + x) : 0ull;
+      unsigned long long* acc = a.roi_acc + (size_t)(t - src.t_new) * a.n_rois;
+      roi_add(m[0], m[1], v[0], v[1], acc);
+      roi_add(m[2], m[3], v[2], v[3], acc);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      sum[i] += v[i];
+      mx[i] = fmaxf(mx[i], vb[i]);
+      tc::tmem_st1(tlane + tcol0 + (uint32_t)(64 * i + fi), vb[i]);
+    }
+    tc::tmem_wait_st();
+  }
+  if (aborted) {
+    if (gt == 0) {
+      if (a.err) atomicExch(a.err, 1);
+      abort_any = 1;
+      // wait (bounded) for this group's copies still in flight
+      for (int bb = 0; bb < 2; ++bb)
+        if (pending & (1u << bb)) tc::mbar_wait(&full[grp][bb], (phase >> bb) & 1);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (complete && a.summary && !abort_any) {
+    // partial sums and maxima: each group publishes those of the two pixels the
+    // other group finishes (group 0's partial sum is always added first)
+    float* xs = fbase;  // [group][pixel 0..1][sum, max][256]
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int i = 2 * (1 - grp) + j;
+      xs[((grp * 2 + j) * 2 + 0) * kTmGroup + gt] = sum[i];
+      xs[((grp * 2 + j) * 2 + 1) * kTmGroup + gt] = mx[i];
+    }
+    __syncthreads();
+    float* S = a.summary + (size_t)slot * 2 * HW;
+    float* T = S + HW;
+    const float invL = 1.0f / (float)L;
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const int i = 2 * grp + j, og = 1 - grp;
+      const float os = xs[((og * 2 + j) * 2 + 0) * kTmGroup + gt];
+      const float om = xs[((og * 2 + j) * 2 + 1) * kTmGroup + gt];
+      const float st = grp == 0 ? sum[i] + os : os + sum[i];
+      const float mt = fmaxf(mx[i], om);
+      const uint32_t ta = tlane + tcol0 + (uint32_t)(64 * i);
+      uint32_t r0[16], r1[16], r2[16], r3[2];
+      tc::tmem_ld16_nowait(ta, r0);
+      tc::tmem_ld16_nowait(ta + 16, r1);
+      tc::tmem_ld16_nowait(ta + 32, r2);
+      tc::tmem_ld2_nowait(ta + 48, r3);
+      tc::tmem_wait_ld();
+      float h[50];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        h[q] = __uint_as_float(r0[q]);
+        h[16 + q] = __uint_as_float(r1[q]);
+        h[32 + q] = __uint_as_float(r2[q]);
+      }
+      h[48] = __uint_as_float(r3[0]);
+      h[49] = __uint_as_float(r3[1]);
+      const float med = L == 50 ? median50_v(h) : median_any_v(h, L);
+      const int y = yb + i;
+      if (x < W && y < H) {
+        S[(size_t)y * W + x] = st * invL;
+        T[(size_t)y * W + x] = mt - med;
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (tid < 32) tc::tmem_dealloc(tmem_slot, kTmCols);
+}
+
+// TMA map of a uint16 frame buffer [n][H][W]: boxes of 64 columns x 57 rows x 1
+// frame; coordinates outside the buffer read zeros.
+static bool tm_frame_map(CUtensorMap* m, const uint16_t* base, int n, int H, int W) {
+  tc::EncodeTiledFn fn = tc::encode_fn();
+  if (!fn || !base) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(n > 0 ? n : 1)};
+  cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)H * W * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kStCols, (cuuint32_t)kStRows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor-memory kernel applies: no high-pass output, W a multiple of 8 (rows
+// on 16-byte boundaries), 16-byte aligned buffers, and not switched off.
+static bool tm_applies(const TemporalArgs& a) {
+  const bool hp = a.out_hp && a.hp_w > 0 && a.corrected;
+  const uintptr_t bb = reinterpret_cast<uintptr_t>(a.src.batch);
+  const uintptr_t cb = reinterpret_cast<uintptr_t>(a.src.carry);
+  return !a.smem_history && !hp && a.W % 8 == 0 && a.src.n_batch > 0 && bb && (bb & 15) == 0 &&
+         (a.src.n_carry == 0 || (cb && (cb & 15) == 0));
 }
 
 // ---- voltage-trace ROIs ----------------------------------------------------------
@@ -750,11 +1175,38 @@ bool temporal_batch_finalize(TemporalBatch& b) {
   return true;
 }
 
+cudaError_t temporal_init() {
+  static unsigned char done[kMaxDevices] = {};
+  return once_per_device(done, [](int) {
+    cudaError_t e = cudaFuncSetAttribute(k_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)temporal_smem(kMaxL));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_temporal_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTmSmem);
+    return e;
+  });
+}
+
 cudaError_t launch_temporal_multi(const TemporalBatch& b, cudaStream_t st) {
   const int blocks = b.begin[b.n];
   if (blocks <= 0) return cudaSuccess;
   cudaError_t e = temporal_init();
   if (e != cudaSuccess) return e;
+  // the tensor-memory kernel when every job qualifies and its maps encode
+  bool tm = true;
+  TemporalMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int i = 0; i < b.n && tm; ++i) {
+    const TemporalArgs& a = b.a[i];
+    tm = tm_applies(a) &&
+         tm_frame_map(&maps.m[i][0], a.src.n_carry > 0 ? a.src.carry : a.src.batch,
+                      a.src.n_carry > 0 ? a.src.n_carry : a.src.n_batch, a.H, a.W) &&
+         tm_frame_map(&maps.m[i][1], a.src.batch, a.src.n_batch, a.H, a.W);
+  }
+  if (tm) {
+    k_temporal_tm<<<blocks, kTmThreads, kTmSmem, st>>>(b, maps);
+    return cudaGetLastError();
+  }
   int L = 1;
   for (int i = 0; i < b.n; ++i) L = L > b.a[i].L ? L : b.a[i].L;
   k_temporal<<<blocks, kTempThreads, temporal_smem(L), st>>>(b);

@@ -62,6 +62,8 @@ struct TemporalArgs {
   int n_rois;
   float* corrected;                   // [n_batch][H][W] or null
   float* summary;                     // [k][2][H][W] or null (slot j -> index j)
+  int* err;                           // sticky device error flag (bounded waits), or null
+  int smem_history;                   // force the shared-memory-history kernel
 };
 
 // ---- several videos per launch ----------------------------------------------

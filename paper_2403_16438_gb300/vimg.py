@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvimg.so")
 OK = 0
 ERR_ARG, ERR_NO_TEMPLATE, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_SIZE = -1, -2, -3, -4, -5, -6
 REGION_TOO_LARGE, REGION_TOO_MANY = 1, 2  # vimg_segment_status
-CORR_BF16, PROPOSAL_CNN, OUT_HIGHPASS, VIDEO_SUMMARY = 1, 2, 4, 8
+CORR_BF16, PROPOSAL_CNN, OUT_HIGHPASS, VIDEO_SUMMARY, TEMPORAL_SMEM = 1, 2, 4, 8, 16
 
 
 class Params(ctypes.Structure):
