@@ -44,6 +44,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   return done != 0;
 }
 
+// Same as mbar_wait with a 32-bit poll counter (a short loop for waits that
+// are expected to be satisfied already).
+__device__ __forceinline__ bool mbar_wait_short(uint64_t* bar, uint32_t parity,
+                                                int spins = (int)kTcSpin) {
+  uint32_t done = 0;
+  for (int s = 0; s < spins && !done; ++s)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }

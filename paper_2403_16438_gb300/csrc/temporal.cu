@@ -555,30 +555,37 @@ static size_t temporal_smem(int L) {
 //   * the segment's smoothed history (up to 50 frames x 1,024 pixels) lives in
 //     the SM's tensor memory (128 lanes x 512 columns) instead of 200 KB of
 //     shared memory;
-//   * two groups of 8 warps take alternate frames, each with its own buffers
-//     and named barrier, so that one group computes while the other waits;
+//   * four groups of 4 warps take every fourth frame, each with its own
+//     buffers and named barrier, so that some groups compute while others wait;
 //   * each frame's 57 x 64 source window arrives as one TMA box (3-D map over
 //     [frames][H][W]) in a double buffer per group, two of the group's frames
-//     ahead; rows and columns of a window outside the image are then filled
-//     from the nearest edge (the clamped coordinates of the resampling).
-// Tensor memory: warp w (0..7) of a group reaches lanes 32 (w mod 4) .. +31.
-// Thread (w, lane) owns the tile pixels (4 w + i, lane), i = 0..3, and keeps
-// pixel i's smoothed value of segment frame t at column 64 q + t, q = 4 (w / 4)
-// + i.  The other group's thread with the same (w, lane) owns the same pixels
-// (and lanes): at the segment's end each group takes two of them for the median.
-constexpr int kTmThreads = 512, kTmGroup = 256;
+//     ahead; samples outside the image are read at clamped indices of the
+//     window (the clamped coordinates of the resampling).
+// Work of a group per frame: its 4 warps resample (7 rows x 2 columns per thread
+// and chunk, two chunks), run the row pass (one row x 16 columns per thread) and
+// the column pass (4 rows x 2 columns per thread), keep the smoothed history,
+// store the corrected pixels and add the traces and segment sums.  Thread (w,
+// lane) owns the 8 pixels at rows 4 (2 w + lane / 16) + i and columns 2 (lane
+// mod 16) + e (i < 4, e < 2) -- the same pixels in every group.
+// Tensor memory: warp w (0..3) of a group reaches lanes 32 w .. +31; pixel q =
+// 2 i + e of a thread keeps its smoothed value of segment frame t at column
+// 64 q + t, whichever group smoothed that frame.  At the segment's end group g
+// takes pixels 2 g, 2 g + 1 of every thread for the median.
+constexpr int kTmGroups = 4, kTmGroup = 128, kTmThreads = kTmGroups * kTmGroup;
 constexpr int kStCols = 64, kStRows = kFstRows;       // source window of one frame (uint16)
 constexpr int kStBytes = kStCols * kStRows * 2;        // 7,296 B: one TMA box
 constexpr int kStStride = 7424;                        // stage buffer pitch (128-byte multiple)
 constexpr int kVS = 60;   // resampled-tile row stride: 128-bit row-pass loads without conflicts
 constexpr int kHS = 36;   // row-pass output row stride: 128-bit stores without conflicts
 constexpr int kTmCols = 512;
-constexpr size_t kTmSmemUsed = 4 * (size_t)kStStride +
-                               sizeof(float) * (2 * (size_t)kExt * (kVS + kHS) + 2 * kMaxL);
+constexpr size_t kTmSmemUsed = 2 * kTmGroups * (size_t)kStStride +
+                               sizeof(float) * (kTmGroups * (size_t)kExt * (kVS + kHS) + 2 * kMaxL) +
+                               (sizeof(float2) + 2 * sizeof(int4)) * kMaxL;
 // Shared memory requested per CTA: more than half of the SM's, so that one CTA
 // (which holds all of the SM's tensor memory) runs per SM.
 constexpr size_t kTmSmem = kTmSmemUsed > 120 * 1024 ? kTmSmemUsed : 120 * 1024;
-static_assert(2 * 2 * 2 * kTmGroup * sizeof(float) <= 2 * sizeof(float) * kExt * kVS,
+static_assert(2 * kTmGroups * 8 * kTmGroup * sizeof(float) <=
+                  kTmGroups * sizeof(float) * kExt * kVS,
               "partial-sum exchange fits the resampled-tile buffers");
 
 struct TemporalMaps {
@@ -600,21 +607,26 @@ __device__ __forceinline__ bool group_bar_or(int id, bool v) {
   return r != 0;
 }
 
-// One uint16 half of a 32-bit word as an exact float: the byte permute builds
-// the bits of 2^23 + u, and subtracting 2^23 is exact.
-__device__ __forceinline__ float u16f(unsigned w, unsigned sel) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.0f;
+// 2^23 + u for one uint16 half u of a 32-bit word, exactly: the byte permute
+// builds its bits.  Subtracting 2^23, or another such value, is exact.
+__device__ __forceinline__ float u16m(unsigned w, unsigned sel) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, sel));
 }
 constexpr unsigned kSelLo = 0x7410u, kSelHi = 0x7432u;
 
 // Source window of frame fi for a tile: rows r0 .. r0 + 56 and columns c0e ..
 // c0e + 63, c0e = the window's first column rounded down to a multiple of 8
-// (TMA boxes start on 16-byte boundaries), ox = the remainder.
+// (TMA boxes start on 16-byte boundaries), ox = the remainder.  Of the window,
+// rows [top, bot) and columns [left, right) lie inside the image; a sample
+// outside takes the value at the clamped position (the resampling's clamped
+// coordinates), so the window is read at clamped indices and the zeros that
+// the TMA writes outside the image are never used.
 struct WinGeom {
   float fy, fx;
-  int r0, c0e, ox;
-  bool meets;   // the window overlaps the image (its edge rows / columns are inside it)
-  bool inside;  // the window lies inside the image
+  int r0, c0e, ox, top, bot, left, right;
+  bool meets;    // the window overlaps the image (TMA); else filled by plain loads
+  bool rows_in;  // no row clamping needed
+  bool cols_in;  // the columns the resampling reads lie inside the image
 };
 
 __device__ __forceinline__ WinGeom win_geom(const float* shs, int fi, int ty0, int tx0, int H,
@@ -632,14 +644,83 @@ __device__ __forceinline__ WinGeom win_geom(const float* shs, int fi, int ty0, i
   g.c0e = c0 & ~7;
   g.ox = c0 - g.c0e;
   g.meets = g.r0 + kStRows - 1 >= 0 && g.r0 <= H - 1 && g.c0e + kStCols - 1 >= 0 && g.c0e <= W - 1;
-  g.inside = g.r0 >= 0 && g.r0 + kStRows - 1 <= H - 1 && g.c0e >= 0 && g.c0e + kStCols - 1 <= W - 1;
+  g.top = min(kStRows - 1, max(0, -g.r0));
+  g.bot = max(g.top + 1, min(kStRows, H - g.r0));
+  g.left = min(kStCols - 1, max(0, -g.c0e));
+  g.right = max(g.left + 1, min(kStCols, W - g.c0e));
+  // a window that misses the image is filled at clamped coordinates already
+  g.rows_in = !g.meets || (g.top == 0 && g.bot == kStRows);
+  g.cols_in = !g.meets || (g.ox >= g.left && g.ox + kExt + 1 <= g.right);
   return g;
+}
+
+// Resampling of the tile + halo, one warp per 7 output rows, lane p < 28 = the
+// output columns 2p, 2p + 1 (same formula and order as k_temporal: lerp along x
+// on each source row, then along y).  Each source row's lerps feed two output
+// rows.  kRowClamp: source rows read at clamped indices.
+// Contiguous form: the two columns' three samples per row are two 32-bit words.
+template <bool kRowClamp>
+__device__ __forceinline__ void resample_words(const unsigned short* st16, float* vext, int kc,
+                                               int p, int ox, float fy, float fx, int top,
+                                               int bot) {
+  const unsigned* sw = reinterpret_cast<const unsigned*>(st16) + ((2 * p + ox) >> 1);
+  const bool odd = ox & 1;
+  const unsigned sa = odd ? kSelHi : kSelLo, sb = odd ? kSelLo : kSelHi;
+  float* vo = vext + kc * 7 * kVS + 2 * p;
+  float ph0 = 0.f, ph1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int r = kc * 7 + j;
+    if (kRowClamp) r = min(max(r, top), bot - 1);
+    const unsigned w0 = sw[r * (kStCols / 2)], w1 = sw[r * (kStCols / 2) + 1];
+    // 2^23 + u of the three samples; differences of these are exact
+    const float ma = u16m(w0, sa), mb = u16m(odd ? w1 : w0, sb), mc = u16m(w1, sa);
+    const float va = ma - 8388608.0f, vb = mb - 8388608.0f;
+    const float h0 = fmaf(fx, mb - ma, va), h1 = fmaf(fx, mc - mb, vb);
+    if (j > 0)
+      *reinterpret_cast<float2*>(vo + (j - 1) * kVS) =
+          make_float2(fmaf(fy, h0 - ph0, ph0), fmaf(fy, h1 - ph1, ph1));
+    ph0 = h0;
+    ph1 = h1;
+  }
+}
+
+// General form: output column 2p + e reads window columns s[e][0], s[e][1]
+// (mirrored at the image border for the Gaussian's halo, clamped to the image).
+template <bool kRowClamp>
+__device__ __forceinline__ void resample_cols(const unsigned short* st16, float* vext, int kc,
+                                              int p, const int (&s)[2][2], float fy, float fx,
+                                              int top, int bot) {
+  float* vo = vext + kc * 7 * kVS + 2 * p;
+  float ph0 = 0.f, ph1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int r = kc * 7 + j;
+    if (kRowClamp) r = min(max(r, top), bot - 1);
+    const unsigned short* row = st16 + r * kStCols;
+    const float a0 = __uint_as_float(0x4B000000u | row[s[0][0]]) - 8388608.0f;
+    const float b0 = __uint_as_float(0x4B000000u | row[s[0][1]]) - 8388608.0f;
+    const float a1 = __uint_as_float(0x4B000000u | row[s[1][0]]) - 8388608.0f;
+    const float b1 = __uint_as_float(0x4B000000u | row[s[1][1]]) - 8388608.0f;
+    const float h0 = fmaf(fx, b0 - a0, a0), h1 = fmaf(fx, b1 - a1, a1);
+    if (j > 0)
+      *reinterpret_cast<float2*>(vo + (j - 1) * kVS) =
+          make_float2(fmaf(fy, h0 - ph0, ph0), fmaf(fy, h1 - ph1, ph1));
+    ph0 = h0;
+    ph1 = h1;
+  }
+}
+
+// Tile coordinate of the in-image position mirrored at the border ("d c b a |
+// a b c d"); positions that only feed outputs outside the image stay in the tile.
+__device__ __forceinline__ int mirror_local(int i, int o, int n) {
+  return min(max(mirror_idx(o + i, n) - o, 0), kExt - 1);
 }
 
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_temporal_tm(const __grid_constant__ TemporalBatch b, const __grid_constant__ TemporalMaps maps) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[2][2];
+  __shared__ __align__(8) uint64_t full[kTmGroups][2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_any;
   const int jb = job_of(b.begin, b.n, blockIdx.x);
@@ -649,13 +730,16 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   const int local = blockIdx.x - b.begin[jb];
   const int slot = local / tiles, tile = local - slot * tiles;
   const int ty0 = (tile / ntx) * kTile, tx0 = (tile % ntx) * kTile;
-  const int tid = threadIdx.x, grp = tid >> 8, gt = tid & (kTmGroup - 1), wg = gt >> 5;
+  const int tid = threadIdx.x, grp = tid / kTmGroup, gt = tid % kTmGroup, wg = gt >> 5;
   const int lane = tid & 31, bar_id = 1 + grp;
   unsigned char* stage = smraw + grp * 2 * kStStride;  // [2][kStStride] this group's windows
-  float* fbase = reinterpret_cast<float*>(smraw + 4 * kStStride);
-  float* vext = fbase + grp * (kExt * kVS);                   // [56][kVS] resampled tile + halo
-  float* hbuf = fbase + 2 * kExt * kVS + grp * (kExt * kHS);  // [56][kHS] row-smoothed
-  float* shs = fbase + 2 * kExt * (kVS + kHS);                // [L][2] shifts of the slot
+  float* fbase = reinterpret_cast<float*>(smraw + 2 * kTmGroups * kStStride);
+  float* vext = fbase + grp * (kExt * kVS);                            // [56][kVS] tile + halo
+  float* hbuf = fbase + kTmGroups * kExt * kVS + grp * (kExt * kHS);   // [56][kHS] row-smoothed
+  float* shs = fbase + kTmGroups * kExt * (kVS + kHS);                 // [L][2] shifts of the slot
+  float2* geo_f = reinterpret_cast<float2*>(shs + 2 * kMaxL);  // [L] (fy, fx)
+  int4* geo_i = reinterpret_cast<int4*>(geo_f + kMaxL);         // [L] (r0, c0e, ox, flags)
+  int4* geo_b = geo_i + kMaxL;                                  // [L] (top, bot, left, right)
   const FrameSource& src = a.src;
   const long long t_end = src.t_first + src.n_carry + src.n_batch;
   const long long s0 = a.seg_base + (long long)slot * L;
@@ -665,7 +749,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
 
   if (tid < 32) tc::tmem_alloc(&tmem_slot, kTmCols);
   if (tid == 0) {
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < kTmGroups; ++g)
       for (int k = 0; k < 2; ++k) tc::mbar_init(&full[g][k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_any = 0;
@@ -675,58 +759,81 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     shs[i] = v < src.n_carry ? src.carry_shift[2 * v + (i & 1)]
                              : src.batch_shift[2 * (v - src.n_carry) + (i & 1)];
   }
+  __syncthreads();
+  if (tid < nfr) {  // source-window geometry of every frame of the slot, once
+    const WinGeom g = win_geom(shs, tid, ty0, tx0, H, W);
+    geo_f[tid] = make_float2(g.fy, g.fx);
+    geo_i[tid] = make_int4(g.r0, g.c0e, g.ox,
+                           (g.meets ? 1 : 0) | (g.rows_in ? 2 : 0) | (g.cols_in ? 4 : 0));
+    geo_b[tid] = make_int4(g.top, g.bot, g.left, g.right);
+  }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tlane = tmem_slot + ((uint32_t)(32 * (wg & 3)) << 16);
-  const uint32_t tcol0 = (uint32_t)(64 * 4 * (wg >> 2));
+  const uint32_t tlane = tmem_slot + ((uint32_t)(32 * wg) << 16);
 
   float w[kTaps];
 #pragma unroll
   for (int i = 0; i < kTaps; ++i) w[i] = a.gw[i];
 
-  // this thread's pixels: (yb + i, x), i = 0..3
-  const int x = tx0 + lane, yb = ty0 + 4 * wg;
+  // this thread's 8 pixels: rows yb + i, columns xb + e
+  const int cp = lane & 15, rg = 2 * wg + (lane >> 4);
+  const int xb = tx0 + 2 * cp, yb = ty0 + 4 * rg;
+  const bool xin0 = xb < W, xin1 = xb + 1 < W;
   bool myroi = false;
-  if (a.roi_acc && x < W)
+  if (a.roi_acc)
     for (int i = 0; i < 4; ++i)
-      if (yb + i < H && __ldg(a.roi_members + (size_t)(yb + i) * W + x)) myroi = true;
+      for (int e = 0; e < 2; ++e)
+        if (yb + i < H && xb + e < W && __ldg(a.roi_members + (size_t)(yb + i) * W + xb + e))
+          myroi = true;
   const bool roi_warp = __any_sync(0xffffffffu, myroi);
+  // the Gaussian's mirrored halo: the row pass reads mirrored rows, and the
+  // resampling computes halo columns at their mirrored positions
   const bool mirror_rows = ty0 - kGaussMaxRadius < 0 || ty0 + kTile + kGaussMaxRadius > H;
   const bool mirror_cols = tx0 - kGaussMaxRadius < 0 || tx0 + kTile + kGaussMaxRadius > W;
+  const int oy = ty0 - kGaussMaxRadius, oxt = tx0 - kGaussMaxRadius;
+  const int rp_row = gt >> 1;  // row-pass row of this thread (gt < 112)
+  const int rp_src = mirror_rows ? mirror_local(rp_row, oy, H) : rp_row;
+  const int cm0 = mirror_cols ? mirror_local(2 * lane, oxt, W) : 2 * lane;
+  const int cm1 = mirror_cols ? mirror_local(2 * lane + 1, oxt, W) : 2 * lane + 1;
 
-  // frames grp, grp + 2, ... of the slot; the k-th goes to buffer k mod 2
-  const int nmine = nfr > grp ? (nfr - grp + 1) / 2 : 0;
-  auto issue = [&](int fi, int buf) {
-    const WinGeom g = win_geom(shs, fi, ty0, tx0, H, W);
-    if (!g.meets) return;  // filled by plain loads when consumed
+  // frames grp, grp + 4, ... of the slot; the k-th goes to buffer k mod 2
+  const int nmine = nfr > grp ? (nfr - grp + kTmGroups - 1) / kTmGroups : 0;
+  // TMA of frame fi's window into buffer buf (windows that miss the image are
+  // filled by plain loads when consumed); returns whether a copy was issued
+  auto issue = [&](int fi, int buf) -> bool {
+    const int4 gi = geo_i[fi];
+    if (!(gi.w & 1)) return false;
     const long long v = s0 + fi - src.t_first;
     const int which = v < src.n_carry ? 0 : 1;
     const int z = (int)(which ? v - src.n_carry : v);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc::mbar_expect_tx(&full[grp][buf], kStBytes);
-    tc::tma_load_3d(stage + buf * kStStride, &maps.m[jb][which], g.c0e, g.r0, z, &full[grp][buf]);
+    tc::tma_load_3d(stage + buf * kStStride, &maps.m[jb][which], gi.y, gi.x, z, &full[grp][buf]);
+    return true;
   };
   uint32_t pending = 0;  // (thread gt == 0) buffers with a copy in flight
-  if (gt == 0) {
-    for (int k = 0; k < 2 && k < nmine; ++k) {
-      issue(grp + 2 * k, k);
-      if (win_geom(shs, grp + 2 * k, ty0, tx0, H, W).meets) pending |= 1u << k;
-    }
-  }
+  if (gt == 0)
+    for (int k = 0; k < 2 && k < nmine; ++k)
+      if (issue(grp + kTmGroups * k, k)) pending |= 1u << k;
+  float* const obase = a.corrected ? a.corrected + (size_t)yb * W + xb : nullptr;
 
-  float sum[4] = {0.f, 0.f, 0.f, 0.f};
-  float mx[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+  float mx[8], sm[8];  // running maxima of the smoothed values, sums of V
+#pragma unroll
+  for (int q = 0; q < 8; ++q) mx[q] = -FLT_MAX, sm[q] = 0.f;
   uint32_t phase = 0;  // bit k: parity of buffer k's next completion
   bool aborted = false;
   for (int k = 0; k < nmine; ++k) {
-    const int fi = grp + 2 * k, buf = k & 1;
+    const int fi = grp + kTmGroups * k, buf = k & 1;
     const long long t = s0 + fi;
-    const WinGeom g = win_geom(shs, fi, ty0, tx0, H, W);
+    const float2 gf = geo_f[fi];
+    const int4 gi = geo_i[fi];
+    const int r0 = gi.x, c0e = gi.y, ox = gi.z;
+    const bool meets = gi.w & 1, rows_in = gi.w & 2, cols_in = gi.w & 4;
     unsigned short* st16 = reinterpret_cast<unsigned short*>(stage + buf * kStStride);
     bool late = false;
-    if (g.meets) {
-      late = !tc::mbar_wait(&full[grp][buf], (phase >> buf) & 1);
+    if (meets) {
+      late = !tc::mbar_wait_short(&full[grp][buf], (phase >> buf) & 1);
       phase ^= 1u << buf;
       if (gt == 0 && !late) pending &= ~(1u << buf);
     }
@@ -734,145 +841,126 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       aborted = true;
       break;
     }
-    // 1. the window at clamped coordinates
-    if (!g.meets) {
-      // entirely outside: every sample is an edge pixel of the frame
+    if (!meets) {
+      // the window misses the image: every sample is an edge pixel of the frame
       const long long v = t - src.t_first;
       const uint16_t* F = v < src.n_carry ? src.carry + (size_t)v * HW
                                           : src.batch + (size_t)(v - src.n_carry) * HW;
       for (int i = gt; i < kStRows * kStCols; i += kTmGroup) {
         const int r = i >> 6, c = i & 63;
-        const int rr = min(max(g.r0 + r, 0), H - 1), cc = min(max(g.c0e + c, 0), W - 1);
+        const int rr = min(max(r0 + r, 0), H - 1), cc = min(max(c0e + c, 0), W - 1);
         st16[i] = __ldg(F + (size_t)rr * W + cc);
       }
       group_bar(bar_id);
-    } else if (!g.inside) {
-      // rows / columns outside the image (zeros from the TMA) take the value at
-      // the clamped position, which lies inside the image and inside the window
-      for (int i = gt; i < kStRows * kStCols; i += kTmGroup) {
-        const int r = i >> 6, c = i & 63;
-        const int rr = min(max(g.r0 + r, 0), H - 1) - g.r0;
-        const int cc = min(max(g.c0e + c, 0), W - 1) - g.c0e;
-        if (rr != r || cc != c) st16[i] = st16[(rr << 6) + cc];
-      }
-      group_bar(bar_id);
     }
-    // 2. resample the tile + halo: thread = 2 columns x 7 rows; each source row
-    //    is read as two 32-bit words, lerped along x once and shared by the two
-    //    output rows it feeds (same formula and order as k_temporal)
-    if (gt < 224) {
-      const int p = gt % 28, kc = gt / 28;
-      const unsigned* sw =
-          reinterpret_cast<const unsigned*>(st16) + kc * 7 * (kStCols / 2) + ((2 * p + g.ox) >> 1);
-      const bool odd = g.ox & 1;
-      const unsigned sa = odd ? kSelHi : kSelLo, sb = odd ? kSelLo : kSelHi;
-      float* vo = vext + kc * 7 * kVS + 2 * p;
-      float ph0 = 0.f, ph1 = 0.f;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const unsigned w0 = sw[j * (kStCols / 2)], w1 = sw[j * (kStCols / 2) + 1];
-        const float va = u16f(w0, sa), vb = u16f(odd ? w1 : w0, sb), vc = u16f(w1, sa);
-        const float h0 = fmaf(g.fx, vb - va, va), h1 = fmaf(g.fx, vc - vb, vb);
-        if (j > 0)
-          *reinterpret_cast<float2*>(vo + (j - 1) * kVS) =
-              make_float2(fmaf(g.fy, h0 - ph0, ph0), fmaf(g.fy, h1 - ph1, ph1));
-        ph0 = h0;
-        ph1 = h1;
+    // 1. resample the tile + halo into vext: warp w takes the 7-row chunks w and
+    //    w + 4, lane p < 28 the columns 2p, 2p + 1
+    if (lane < 28) {
+#pragma unroll 1
+      for (int ch = wg; ch < 8; ch += 4) {
+        if (cols_in && !mirror_cols) {
+          if (rows_in)
+            resample_words<false>(st16, vext, ch, lane, ox, gf.x, gf.y, 0, kStRows);
+          else {
+            const int4 gb = geo_b[fi];
+            resample_words<true>(st16, vext, ch, lane, ox, gf.x, gf.y, gb.x, gb.y);
+          }
+        } else {
+          const int4 gb = geo_b[fi];
+          int sc[2][2];
+          sc[0][0] = min(max(cm0 + ox, gb.z), gb.w - 1);
+          sc[0][1] = min(max(cm0 + ox + 1, gb.z), gb.w - 1);
+          sc[1][0] = min(max(cm1 + ox, gb.z), gb.w - 1);
+          sc[1][1] = min(max(cm1 + ox + 1, gb.z), gb.w - 1);
+          if (rows_in)
+            resample_cols<false>(st16, vext, ch, lane, sc, gf.x, gf.y, 0, kStRows);
+          else
+            resample_cols<true>(st16, vext, ch, lane, sc, gf.x, gf.y, gb.x, gb.y);
+        }
       }
     }
     group_bar(bar_id);  // window consumed, tile resampled
-    if (gt == 0 && k + 2 < nmine) {
-      issue(fi + 4, buf);
-      if (win_geom(shs, fi + 4, ty0, tx0, H, W).meets) pending |= 1u << buf;
-    }
-    // 3. halo rows, then halo columns, outside the image: mirrored (Eq. 2's border)
-    if (mirror_rows) {
-      const int nt = max(0, kGaussMaxRadius - ty0), nb = max(0, ty0 + kTile + kGaussMaxRadius - H);
-      for (int i = gt; i < (nt + nb) * 64; i += kTmGroup) {
-        const int kk = i >> 6, rx = i & 63;
-        if (rx >= kExt) continue;
-        const int ry = kk < nt ? kk : kExt - nb + (kk - nt);
-        const int rs = mirror_idx(ty0 - kGaussMaxRadius + ry, H) - (ty0 - kGaussMaxRadius);
-        if (rs >= 0 && rs < kExt) vext[ry * kVS + rx] = vext[rs * kVS + rx];
-      }
-      group_bar(bar_id);
-    }
-    if (mirror_cols) {
-      const int nl = max(0, kGaussMaxRadius - tx0), nr = max(0, tx0 + kTile + kGaussMaxRadius - W);
-      for (int i = gt; i < (nl + nr) * 64; i += kTmGroup) {
-        const int kk = i >> 6, ry = i & 63;
-        if (ry >= kExt) continue;
-        const int rx = kk < nl ? kk : kExt - nr + (kk - nl);
-        const int cs = mirror_idx(tx0 - kGaussMaxRadius + rx, W) - (tx0 - kGaussMaxRadius);
-        if (cs >= 0 && cs < kExt) vext[ry * kVS + rx] = vext[ry * kVS + cs];
-      }
-      group_bar(bar_id);
-    }
-    float v[4];
+    if (gt == 0 && k + 2 < nmine && issue(fi + 2 * kTmGroups, buf)) pending |= 1u << buf;
+    float2 v2[4];  // V of the thread's 8 pixels
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      v[i] = vext[(kGaussMaxRadius + 4 * wg + i) * kVS + kGaussMaxRadius + lane];
-    // 4. row pass of the Gaussian: thread = one row x 8 output columns
-    if (gt < 224) {
-      const int r = gt >> 2, cg = gt & 3;
-      const float* in = vext + r * kVS + cg * 8;
-      float xv[32];
+      v2[i] = *reinterpret_cast<const float2*>(
+          vext + (kGaussMaxRadius + 4 * rg + i) * kVS + kGaussMaxRadius + 2 * cp);
+    // 2. row pass of the Gaussian: thread = one row x 16 output columns (halo
+    //    rows outside the image read their mirrored row); each output sums its
+    //    25 taps in order, as in k_temporal
+    if (gt < 2 * kExt) {
+      const int ch = gt & 1;
+      const float* in = vext + rp_src * kVS + ch * 16;
+      float xv[40];
 #pragma unroll
-      for (int i = 0; i < 32; i += 4) {
+      for (int i = 0; i < 40; i += 4) {
         const float4 q = *reinterpret_cast<const float4*>(in + i);
         xv[i] = q.x, xv[i + 1] = q.y, xv[i + 2] = q.z, xv[i + 3] = q.w;
       }
-      float o[8];
+      float o[16];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) o[j] = 0.f;
+      for (int j = 0; j < 16; ++j) o[j] = 0.f;
 #pragma unroll
       for (int m = 0; m < kTaps; ++m)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) o[j] = fmaf(w[m], xv[j + m], o[j]);
-      float* out = hbuf + r * kHS + cg * 8;
-      *reinterpret_cast<float4*>(out) = make_float4(o[0], o[1], o[2], o[3]);
-      *reinterpret_cast<float4*>(out + 4) = make_float4(o[4], o[5], o[6], o[7]);
+        for (int j = 0; j < 16; ++j) o[j] = fmaf(w[m], xv[j + m], o[j]);
+      float* out = hbuf + rp_row * kHS + ch * 16;
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(out + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
     }
     group_bar(bar_id);
-    // 5. column pass: four output rows of one column per thread, each in two
-    //    chains (even and odd taps) as in k_temporal
-    float col[kTaps + 3];
+    // 3. column pass: 4 output rows x 2 columns per thread, each output in two
+    //    chains (even and odd taps) as in k_temporal; the smoothed history
+    float2 c2[kTaps + 3];
 #pragma unroll
-    for (int kk = 0; kk < kTaps + 3; ++kk) col[kk] = hbuf[(4 * wg + kk) * kHS + lane];
-    float vb[4];
+    for (int kk = 0; kk < kTaps + 3; ++kk)
+      c2[kk] = *reinterpret_cast<const float2*>(hbuf + (4 * rg + kk) * kHS + 2 * cp);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      float be = 0.f, bo = 0.f;
+      float be0 = 0.f, bo0 = 0.f, be1 = 0.f, bo1 = 0.f;
 #pragma unroll
       for (int m = 0; m + 1 < kTaps; m += 2) {
-        be = fmaf(w[m], col[i + m], be);
-        bo = fmaf(w[m + 1], col[i + m + 1], bo);
+        be0 = fmaf(w[m], c2[i + m].x, be0);
+        be1 = fmaf(w[m], c2[i + m].y, be1);
+        bo0 = fmaf(w[m + 1], c2[i + m + 1].x, bo0);
+        bo1 = fmaf(w[m + 1], c2[i + m + 1].y, bo1);
       }
-      vb[i] = fmaf(w[kTaps - 1], col[i + kTaps - 1], be) + bo;
+      const float vb0 = fmaf(w[kTaps - 1], c2[i + kTaps - 1].x, be0) + bo0;
+      const float vb1 = fmaf(w[kTaps - 1], c2[i + kTaps - 1].y, be1) + bo1;
+      mx[2 * i] = fmaxf(mx[2 * i], vb0);
+      mx[2 * i + 1] = fmaxf(mx[2 * i + 1], vb1);
+      tc::tmem_st1(tlane + (uint32_t)(64 * (2 * i) + fi), vb0);
+      tc::tmem_st1(tlane + (uint32_t)(64 * (2 * i + 1) + fi), vb1);
     }
-    // 6. outputs of frames new to this call, traces, segment accumulators and
-    //    the smoothed history
+    // 4. outputs of frames new to this call, traces, segment sums
     const bool fresh = t >= src.t_new;
-    if (fresh && a.corrected && x < W) {
-      float* out = a.corrected + (size_t)(t - src.t_new) * HW + x;
+    if (fresh && obase) {
+      float* out = obase + (size_t)(t - src.t_new) * HW;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (yb + i < H) out[(size_t)(yb + i) * W] = v[i];
+      for (int i = 0; i < 4; ++i) {
+        if (yb + i >= H) continue;
+        if (xin1)
+          *reinterpret_cast<float2*>(out + (size_t)i * W) = v2[i];
+        else if (xin0)
+          out[(size_t)i * W] = v2[i].x;
+      }
     }
     if (roi_warp && fresh) {
-      unsigned long long m[4];
+      unsigned long long* racc = a.roi_acc + (size_t)(t - src.t_new) * a.n_rois;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        m[i] = (x < W && yb + i < H) ? __ldg(a.roi_members + (size_t)(yb + i) * W + x) : 0ull;
-      unsigned long long* acc = a.roi_acc + (size_t)(t - src.t_new) * a.n_rois;
-      roi_add(m[0], m[1], v[0], v[1], acc);
-      roi_add(m[2], m[3], v[2], v[3], acc);
+      for (int i = 0; i < 4; ++i) {
+        const bool yin = yb + i < H;
+        const unsigned long long* mrow = a.roi_members + (size_t)(yb + i) * W + xb;
+        roi_add(yin && xin0 ? __ldg(mrow) : 0ull, yin && xin1 ? __ldg(mrow + 1) : 0ull, v2[i].x,
+                v2[i].y, racc);
+      }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      sum[i] += v[i];
-      mx[i] = fmaxf(mx[i], vb[i]);
-      tc::tmem_st1(tlane + tcol0 + (uint32_t)(64 * i + fi), vb[i]);
+      sm[2 * i] += v2[i].x;
+      sm[2 * i + 1] += v2[i].y;
     }
     tc::tmem_wait_st();
   }
@@ -889,27 +977,30 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   __syncthreads();
   tc::tc_fence_after();
   if (complete && a.summary && !abort_any) {
-    // partial sums and maxima: each group publishes those of the two pixels the
-    // other group finishes (group 0's partial sum is always added first)
-    float* xs = fbase;  // [group][pixel 0..1][sum, max][256]
+    // each group's partial maxima and sums over its frames; group g finishes
+    // pixels 2 g and 2 g + 1 of every thread, adding the partial sums in group
+    // order
+    float* xs = fbase;  // [max | sum][group][pixel 0..7][128]
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int i = 2 * (1 - grp) + j;
-      xs[((grp * 2 + j) * 2 + 0) * kTmGroup + gt] = sum[i];
-      xs[((grp * 2 + j) * 2 + 1) * kTmGroup + gt] = mx[i];
+    for (int q = 0; q < 8; ++q) {
+      xs[((0 * kTmGroups + grp) * 8 + q) * kTmGroup + gt] = mx[q];
+      xs[((1 * kTmGroups + grp) * 8 + q) * kTmGroup + gt] = sm[q];
     }
     __syncthreads();
     float* S = a.summary + (size_t)slot * 2 * HW;
     float* T = S + HW;
     const float invL = 1.0f / (float)L;
-#pragma unroll 1
-    for (int j = 0; j < 2; ++j) {
-      const int i = 2 * grp + j, og = 1 - grp;
-      const float os = xs[((og * 2 + j) * 2 + 0) * kTmGroup + gt];
-      const float om = xs[((og * 2 + j) * 2 + 1) * kTmGroup + gt];
-      const float st = grp == 0 ? sum[i] + os : os + sum[i];
-      const float mt = fmaxf(mx[i], om);
-      const uint32_t ta = tlane + tcol0 + (uint32_t)(64 * i);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int q = 2 * grp + u, i = q >> 1, e = q & 1;
+      const int y = yb + i, xx = xb + e;
+      float mt = -FLT_MAX, st = 0.f;
+#pragma unroll
+      for (int g = 0; g < kTmGroups; ++g) {
+        mt = fmaxf(mt, xs[((0 * kTmGroups + g) * 8 + q) * kTmGroup + gt]);
+        st += xs[((1 * kTmGroups + g) * 8 + q) * kTmGroup + gt];
+      }
+      const uint32_t ta = tlane + (uint32_t)(64 * q);
       uint32_t r0[16], r1[16], r2[16], r3[2];
       tc::tmem_ld16_nowait(ta, r0);
       tc::tmem_ld16_nowait(ta + 16, r1);
@@ -918,18 +1009,17 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       tc::tmem_wait_ld();
       float h[50];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        h[q] = __uint_as_float(r0[q]);
-        h[16 + q] = __uint_as_float(r1[q]);
-        h[32 + q] = __uint_as_float(r2[q]);
+      for (int z = 0; z < 16; ++z) {
+        h[z] = __uint_as_float(r0[z]);
+        h[16 + z] = __uint_as_float(r1[z]);
+        h[32 + z] = __uint_as_float(r2[z]);
       }
       h[48] = __uint_as_float(r3[0]);
       h[49] = __uint_as_float(r3[1]);
       const float med = L == 50 ? median50_v(h) : median_any_v(h, L);
-      const int y = yb + i;
-      if (x < W && y < H) {
-        S[(size_t)y * W + x] = st * invL;
-        T[(size_t)y * W + x] = mt - med;
+      if (y < H && xx < W) {
+        S[(size_t)y * W + xx] = st * invL;
+        T[(size_t)y * W + xx] = mt - med;
       }
     }
   }
@@ -953,13 +1043,15 @@ static bool tm_frame_map(CUtensorMap* m, const uint16_t* base, int n, int H, int
 }
 
 // The tensor-memory kernel applies: no high-pass output, W a multiple of 8 (rows
-// on 16-byte boundaries), 16-byte aligned buffers, and not switched off.
+// on 16-byte boundaries), 16-byte aligned frame buffers, an 8-byte aligned
+// corrected output (pixel pairs are stored together), and not switched off.
 static bool tm_applies(const TemporalArgs& a) {
   const bool hp = a.out_hp && a.hp_w > 0 && a.corrected;
   const uintptr_t bb = reinterpret_cast<uintptr_t>(a.src.batch);
   const uintptr_t cb = reinterpret_cast<uintptr_t>(a.src.carry);
+  const uintptr_t ob = reinterpret_cast<uintptr_t>(a.corrected);
   return !a.smem_history && !hp && a.W % 8 == 0 && a.src.n_batch > 0 && bb && (bb & 15) == 0 &&
-         (a.src.n_carry == 0 || (cb && (cb & 15) == 0));
+         (a.src.n_carry == 0 || (cb && (cb & 15) == 0)) && (ob & 7) == 0;
 }
 
 // ---- voltage-trace ROIs ----------------------------------------------------------
