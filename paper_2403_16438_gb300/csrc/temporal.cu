@@ -78,7 +78,7 @@ __device__ __forceinline__ void sort_net(float* v) {
 
 // Median of 50 values: sort both halves, then the k-th smallest of two sorted
 // runs A, B is min_i max(A[i-1], B[k-1-i]).
-__device__ __forceinline__ float median50_v(const float (&h)[50]) {
+__device__ __forceinline__ float median50_v(const float (&h)[50], float* maxv = nullptr) {
   float a[32], b[32];
 #pragma unroll
   for (int i = 0; i < 25; ++i) {
@@ -93,22 +93,25 @@ __device__ __forceinline__ float median50_v(const float (&h)[50]) {
   float m26 = FLT_MAX;
 #pragma unroll
   for (int i = 1; i <= 25; ++i) m26 = fminf(m26, fmaxf(a[i - 1], b[25 - i]));
+  if (maxv) *maxv = fmaxf(a[24], b[24]);
   return 0.5f * (m25 + m26);
 }
 
 // Median of the first n <= 50 values (any n): pad to 64 with +inf, sort, pick.
-__device__ __forceinline__ float median_any_v(const float (&h)[50], int n) {
+__device__ __forceinline__ float median_any_v(const float (&h)[50], int n, float* maxv = nullptr) {
   float v[64];
 #pragma unroll
   for (int i = 0; i < 64; ++i) v[i] = (i < 50 && i < n) ? h[i] : FLT_MAX;
   sort_net<64, 64>(v);
-  float lo = 0.f, hi = 0.f;
+  float lo = 0.f, hi = 0.f, top = 0.f;
   const int il = (n - 1) / 2, ih = n / 2;
 #pragma unroll
   for (int i = 0; i < 64; ++i) {
     if (i == il) lo = v[i];
     if (i == ih) hi = v[i];
+    if (i == n - 1) top = v[i];
   }
+  if (maxv) *maxv = top;
   return 0.5f * (lo + hi);
 }
 
@@ -563,15 +566,16 @@ static size_t temporal_smem(int L) {
 //     window (the clamped coordinates of the resampling).
 // Work of a group per frame: its 4 warps resample (7 rows x 2 columns per thread
 // and chunk, two chunks), run the row pass (one row x 16 columns per thread) and
-// the column pass (4 rows x 2 columns per thread), keep the smoothed history,
-// store the corrected pixels and add the traces and segment sums.  Thread (w,
-// lane) owns the 8 pixels at rows 4 (2 w + lane / 16) + i and columns 2 (lane
-// mod 16) + e (i < 4, e < 2) -- the same pixels in every group.
+// the column pass (4 rows of one column per thread and job, two jobs), keep the
+// smoothed history, store the corrected pixels and add the traces and segment
+// sums.  Thread (w, lane) owns the 8 pixels at rows 4 w + i and 4 (w + 4) + i,
+// column lane (i < 4) -- the same pixels in every group.
 // Tensor memory: warp w (0..3) of a group reaches lanes 32 w .. +31; pixel q =
-// 2 i + e of a thread keeps its smoothed value of segment frame t at column
-// 64 q + t, whichever group smoothed that frame.  At the segment's end group g
-// takes pixels 2 g, 2 g + 1 of every thread for the median.
-constexpr int kTmGroups = 4, kTmGroup = 128, kTmThreads = kTmGroups * kTmGroup;
+// 4 j + i (job j) of a thread keeps its smoothed value of segment frame t at
+// column 64 q + t, whichever group smoothed that frame.  At the segment's end
+// the groups share out the 8 pixels of every thread for the median and the
+// maximum.
+constexpr int kTmGroups = 6, kTmGroup = 128, kTmThreads = kTmGroups * kTmGroup;
 constexpr int kStCols = 64, kStRows = kFstRows;       // source window of one frame (uint16)
 constexpr int kStBytes = kStCols * kStRows * 2;        // 7,296 B: one TMA box
 constexpr int kStStride = 7424;                        // stage buffer pitch (128-byte multiple)
@@ -584,12 +588,18 @@ constexpr size_t kTmSmemUsed = 2 * kTmGroups * (size_t)kStStride +
 // Shared memory requested per CTA: more than half of the SM's, so that one CTA
 // (which holds all of the SM's tensor memory) runs per SM.
 constexpr size_t kTmSmem = kTmSmemUsed > 120 * 1024 ? kTmSmemUsed : 120 * 1024;
-static_assert(2 * kTmGroups * 8 * kTmGroup * sizeof(float) <=
-                  kTmGroups * sizeof(float) * kExt * kVS,
+static_assert(kTmGroups * 8 * kTmGroup * sizeof(float) <= kTmGroups * sizeof(float) * kExt * kVS,
               "partial-sum exchange fits the resampled-tile buffers");
+static_assert(kTmSmemUsed <= 227 * 1024, "shared memory of the tensor-memory temporal kernel");
 
 struct TemporalMaps {
   CUtensorMap m[kMaxVideos][2];  // per job: [0] carry buffer, [1] caller's batch
+};
+
+// Gaussian taps shared by every job of a launch: a kernel parameter read at
+// fixed offsets, so the FMAs take them straight from the constant bank.
+struct TemporalTaps {
+  float w[2 * kGaussMaxRadius + 1];
 };
 
 __device__ __forceinline__ void group_bar(int id) {
@@ -718,7 +728,8 @@ __device__ __forceinline__ int mirror_local(int i, int o, int n) {
 }
 
 __global__ void __launch_bounds__(kTmThreads, 1)
-    k_temporal_tm(const __grid_constant__ TemporalBatch b, const __grid_constant__ TemporalMaps maps) {
+    k_temporal_tm(const __grid_constant__ TemporalBatch b, const __grid_constant__ TemporalMaps maps,
+                  const __grid_constant__ TemporalTaps taps) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t full[kTmGroups][2];
   __shared__ uint32_t tmem_slot;
@@ -771,21 +782,17 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tlane = tmem_slot + ((uint32_t)(32 * wg) << 16);
+  const float* w = taps.w;
 
-  float w[kTaps];
-#pragma unroll
-  for (int i = 0; i < kTaps; ++i) w[i] = a.gw[i];
-
-  // this thread's 8 pixels: rows yb + i, columns xb + e
-  const int cp = lane & 15, rg = 2 * wg + (lane >> 4);
-  const int xb = tx0 + 2 * cp, yb = ty0 + 4 * rg;
-  const bool xin0 = xb < W, xin1 = xb + 1 < W;
+  // this thread's 8 pixels: rows yb + 16 j + i (job j, i < 4), column x
+  const int x = tx0 + lane, yb = ty0 + 4 * wg;
+  const bool xin = x < W;
   bool myroi = false;
-  if (a.roi_acc)
-    for (int i = 0; i < 4; ++i)
-      for (int e = 0; e < 2; ++e)
-        if (yb + i < H && xb + e < W && __ldg(a.roi_members + (size_t)(yb + i) * W + xb + e))
-          myroi = true;
+  if (a.roi_acc && xin)
+    for (int q = 0; q < 8; ++q) {
+      const int y = yb + 16 * (q >> 2) + (q & 3);
+      if (y < H && __ldg(a.roi_members + (size_t)y * W + x)) myroi = true;
+    }
   const bool roi_warp = __any_sync(0xffffffffu, myroi);
   // the Gaussian's mirrored halo: the row pass reads mirrored rows, and the
   // resampling computes halo columns at their mirrored positions
@@ -816,11 +823,11 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   if (gt == 0)
     for (int k = 0; k < 2 && k < nmine; ++k)
       if (issue(grp + kTmGroups * k, k)) pending |= 1u << k;
-  float* const obase = a.corrected ? a.corrected + (size_t)yb * W + xb : nullptr;
+  float* const obase = a.corrected ? a.corrected + (size_t)yb * W + x : nullptr;
 
-  float mx[8], sm[8];  // running maxima of the smoothed values, sums of V
+  float sm[8];  // sums of V over this group's frames
 #pragma unroll
-  for (int q = 0; q < 8; ++q) mx[q] = -FLT_MAX, sm[q] = 0.f;
+  for (int q = 0; q < 8; ++q) sm[q] = 0.f;
   uint32_t phase = 0;  // bit k: parity of buffer k's next completion
   bool aborted = false;
   for (int k = 0; k < nmine; ++k) {
@@ -881,11 +888,10 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     }
     group_bar(bar_id);  // window consumed, tile resampled
     if (gt == 0 && k + 2 < nmine && issue(fi + 2 * kTmGroups, buf)) pending |= 1u << buf;
-    float2 v2[4];  // V of the thread's 8 pixels
+    float v[8];  // V of the thread's 8 pixels
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      v2[i] = *reinterpret_cast<const float2*>(
-          vext + (kGaussMaxRadius + 4 * rg + i) * kVS + kGaussMaxRadius + 2 * cp);
+    for (int q = 0; q < 8; ++q)
+      v[q] = vext[(kGaussMaxRadius + 4 * wg + 16 * (q >> 2) + (q & 3)) * kVS + kGaussMaxRadius + lane];
     // 2. row pass of the Gaussian: thread = one row x 16 output columns (halo
     //    rows outside the image read their mirrored row); each output sums its
     //    25 taps in order, as in k_temporal
@@ -911,57 +917,48 @@ __global__ void __launch_bounds__(kTmThreads, 1)
         *reinterpret_cast<float4*>(out + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
     }
     group_bar(bar_id);
-    // 3. column pass: 4 output rows x 2 columns per thread, each output in two
-    //    chains (even and odd taps) as in k_temporal; the smoothed history
-    float2 c2[kTaps + 3];
+    // 3. column pass: two jobs of 4 output rows of one column, each output in
+    //    two chains (even and odd taps) as in k_temporal; the smoothed history
 #pragma unroll
-    for (int kk = 0; kk < kTaps + 3; ++kk)
-      c2[kk] = *reinterpret_cast<const float2*>(hbuf + (4 * rg + kk) * kHS + 2 * cp);
+    for (int j = 0; j < 2; ++j) {
+      float col[kTaps + 3];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float be0 = 0.f, bo0 = 0.f, be1 = 0.f, bo1 = 0.f;
+      for (int kk = 0; kk < kTaps + 3; ++kk)
+        col[kk] = hbuf[(4 * wg + 16 * j + kk) * kHS + lane];
 #pragma unroll
-      for (int m = 0; m + 1 < kTaps; m += 2) {
-        be0 = fmaf(w[m], c2[i + m].x, be0);
-        be1 = fmaf(w[m], c2[i + m].y, be1);
-        bo0 = fmaf(w[m + 1], c2[i + m + 1].x, bo0);
-        bo1 = fmaf(w[m + 1], c2[i + m + 1].y, bo1);
+      for (int i = 0; i < 4; ++i) {
+        float be = 0.f, bo = 0.f;
+#pragma unroll
+        for (int m = 0; m + 1 < kTaps; m += 2) {
+          be = fmaf(w[m], col[i + m], be);
+          bo = fmaf(w[m + 1], col[i + m + 1], bo);
+        }
+        const float vb = fmaf(w[kTaps - 1], col[i + kTaps - 1], be) + bo;
+        tc::tmem_st1(tlane + (uint32_t)(64 * (4 * j + i) + fi), vb);
       }
-      const float vb0 = fmaf(w[kTaps - 1], c2[i + kTaps - 1].x, be0) + bo0;
-      const float vb1 = fmaf(w[kTaps - 1], c2[i + kTaps - 1].y, be1) + bo1;
-      mx[2 * i] = fmaxf(mx[2 * i], vb0);
-      mx[2 * i + 1] = fmaxf(mx[2 * i + 1], vb1);
-      tc::tmem_st1(tlane + (uint32_t)(64 * (2 * i) + fi), vb0);
-      tc::tmem_st1(tlane + (uint32_t)(64 * (2 * i + 1) + fi), vb1);
     }
     // 4. outputs of frames new to this call, traces, segment sums
     const bool fresh = t >= src.t_new;
-    if (fresh && obase) {
+    if (fresh && obase && xin) {
       float* out = obase + (size_t)(t - src.t_new) * HW;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (yb + i >= H) continue;
-        if (xin1)
-          *reinterpret_cast<float2*>(out + (size_t)i * W) = v2[i];
-        else if (xin0)
-          out[(size_t)i * W] = v2[i].x;
+      for (int q = 0; q < 8; ++q) {
+        const int dy = 16 * (q >> 2) + (q & 3);
+        if (yb + dy < H) out[(size_t)dy * W] = v[q];
       }
     }
     if (roi_warp && fresh) {
       unsigned long long* racc = a.roi_acc + (size_t)(t - src.t_new) * a.n_rois;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const bool yin = yb + i < H;
-        const unsigned long long* mrow = a.roi_members + (size_t)(yb + i) * W + xb;
-        roi_add(yin && xin0 ? __ldg(mrow) : 0ull, yin && xin1 ? __ldg(mrow + 1) : 0ull, v2[i].x,
-                v2[i].y, racc);
+      for (int q = 0; q < 8; q += 2) {
+        const int dy = 16 * (q >> 2) + (q & 3);
+        const unsigned long long* mrow = a.roi_members + (size_t)(yb + dy) * W + x;
+        roi_add(xin && yb + dy < H ? __ldg(mrow) : 0ull,
+                xin && yb + dy + 1 < H ? __ldg(mrow + W) : 0ull, v[q], v[q + 1], racc);
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      sm[2 * i] += v2[i].x;
-      sm[2 * i + 1] += v2[i].y;
-    }
+    for (int q = 0; q < 8; ++q) sm[q] += v[q];
     tc::tmem_wait_st();
   }
   if (aborted) {
@@ -977,29 +974,21 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   __syncthreads();
   tc::tc_fence_after();
   if (complete && a.summary && !abort_any) {
-    // each group's partial maxima and sums over its frames; group g finishes
-    // pixels 2 g and 2 g + 1 of every thread, adding the partial sums in group
-    // order
-    float* xs = fbase;  // [max | sum][group][pixel 0..7][128]
+    // each group's partial sums over its frames; the groups share out the 8
+    // pixels of every thread (pixel q goes to group q mod 6) and add the
+    // partial sums in group order; maximum and median come from the history
+    float* xs = fbase;  // [group][pixel 0..7][128]
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      xs[((0 * kTmGroups + grp) * 8 + q) * kTmGroup + gt] = mx[q];
-      xs[((1 * kTmGroups + grp) * 8 + q) * kTmGroup + gt] = sm[q];
-    }
+    for (int q = 0; q < 8; ++q) xs[(grp * 8 + q) * kTmGroup + gt] = sm[q];
     __syncthreads();
     float* S = a.summary + (size_t)slot * 2 * HW;
     float* T = S + HW;
     const float invL = 1.0f / (float)L;
+    for (int q = grp; q < 8; q += kTmGroups) {
+      const int y = yb + 16 * (q >> 2) + (q & 3);
+      float st = 0.f;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int q = 2 * grp + u, i = q >> 1, e = q & 1;
-      const int y = yb + i, xx = xb + e;
-      float mt = -FLT_MAX, st = 0.f;
-#pragma unroll
-      for (int g = 0; g < kTmGroups; ++g) {
-        mt = fmaxf(mt, xs[((0 * kTmGroups + g) * 8 + q) * kTmGroup + gt]);
-        st += xs[((1 * kTmGroups + g) * 8 + q) * kTmGroup + gt];
-      }
+      for (int g = 0; g < kTmGroups; ++g) st += xs[(g * 8 + q) * kTmGroup + gt];
       const uint32_t ta = tlane + (uint32_t)(64 * q);
       uint32_t r0[16], r1[16], r2[16], r3[2];
       tc::tmem_ld16_nowait(ta, r0);
@@ -1016,10 +1005,11 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       }
       h[48] = __uint_as_float(r3[0]);
       h[49] = __uint_as_float(r3[1]);
-      const float med = L == 50 ? median50_v(h) : median_any_v(h, L);
-      if (y < H && xx < W) {
-        S[(size_t)y * W + xx] = st * invL;
-        T[(size_t)y * W + xx] = mt - med;
+      float mt;
+      const float med = L == 50 ? median50_v(h, &mt) : median_any_v(h, L, &mt);
+      if (y < H && xin) {
+        S[(size_t)y * W + x] = st * invL;
+        T[(size_t)y * W + x] = mt - med;
       }
     }
   }
@@ -1288,15 +1278,17 @@ cudaError_t launch_temporal_multi(const TemporalBatch& b, cudaStream_t st) {
   bool tm = true;
   TemporalMaps maps;
   std::memset(&maps, 0, sizeof(maps));
+  TemporalTaps taps;
+  std::memcpy(taps.w, b.a[0].gw, sizeof(taps.w));
   for (int i = 0; i < b.n && tm; ++i) {
     const TemporalArgs& a = b.a[i];
-    tm = tm_applies(a) &&
+    tm = tm_applies(a) && std::memcmp(a.gw, taps.w, sizeof(taps.w)) == 0 &&
          tm_frame_map(&maps.m[i][0], a.src.n_carry > 0 ? a.src.carry : a.src.batch,
                       a.src.n_carry > 0 ? a.src.n_carry : a.src.n_batch, a.H, a.W) &&
          tm_frame_map(&maps.m[i][1], a.src.batch, a.src.n_batch, a.H, a.W);
   }
   if (tm) {
-    k_temporal_tm<<<blocks, kTmThreads, kTmSmem, st>>>(b, maps);
+    k_temporal_tm<<<blocks, kTmThreads, kTmSmem, st>>>(b, maps, taps);
     return cudaGetLastError();
   }
   int L = 1;
