@@ -1269,32 +1269,59 @@ cudaError_t temporal_init() {
   });
 }
 
+// The kernel is chosen per video, so that a video gets the same arithmetic
+// whether it runs alone or with others: the videos for which the tensor-memory
+// kernel applies go to launches of it (one per set of Gaussian taps, which that
+// kernel takes as one kernel parameter), the others to one launch of the
+// general kernel.
 cudaError_t launch_temporal_multi(const TemporalBatch& b, cudaStream_t st) {
-  const int blocks = b.begin[b.n];
-  if (blocks <= 0) return cudaSuccess;
+  if (b.begin[b.n] <= 0) return cudaSuccess;
   cudaError_t e = temporal_init();
   if (e != cudaSuccess) return e;
-  // the tensor-memory kernel when every job qualifies and its maps encode
-  bool tm = true;
-  TemporalMaps maps;
-  std::memset(&maps, 0, sizeof(maps));
-  TemporalTaps taps;
-  std::memcpy(taps.w, b.a[0].gw, sizeof(taps.w));
-  for (int i = 0; i < b.n && tm; ++i) {
+  bool tm[kMaxVideos], done[kMaxVideos];
+  TemporalBatch gb{};
+  for (int i = 0; i < b.n; ++i) {
+    CUtensorMap probe[2];
     const TemporalArgs& a = b.a[i];
-    tm = tm_applies(a) && std::memcmp(a.gw, taps.w, sizeof(taps.w)) == 0 &&
-         tm_frame_map(&maps.m[i][0], a.src.n_carry > 0 ? a.src.carry : a.src.batch,
-                      a.src.n_carry > 0 ? a.src.n_carry : a.src.n_batch, a.H, a.W) &&
-         tm_frame_map(&maps.m[i][1], a.src.batch, a.src.n_batch, a.H, a.W);
+    tm[i] = tm_applies(a) &&
+            tm_frame_map(&probe[0], a.src.n_carry > 0 ? a.src.carry : a.src.batch,
+                         a.src.n_carry > 0 ? a.src.n_carry : a.src.n_batch, a.H, a.W) &&
+            tm_frame_map(&probe[1], a.src.batch, a.src.n_batch, a.H, a.W);
+    done[i] = !tm[i];
+    if (!tm[i]) gb.a[gb.n++] = a;
   }
-  if (tm) {
-    k_temporal_tm<<<blocks, kTmThreads, kTmSmem, st>>>(b, maps, taps);
-    return cudaGetLastError();
+  for (int lead = 0; lead < b.n; ++lead) {
+    if (done[lead]) continue;
+    TemporalBatch tb{};
+    TemporalMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    TemporalTaps taps;
+    std::memcpy(taps.w, b.a[lead].gw, sizeof(taps.w));
+    for (int i = lead; i < b.n; ++i) {
+      const TemporalArgs& a = b.a[i];
+      if (done[i] || std::memcmp(a.gw, taps.w, sizeof(taps.w)) != 0) continue;
+      tm_frame_map(&maps.m[tb.n][0], a.src.n_carry > 0 ? a.src.carry : a.src.batch,
+                   a.src.n_carry > 0 ? a.src.n_carry : a.src.n_batch, a.H, a.W);
+      tm_frame_map(&maps.m[tb.n][1], a.src.batch, a.src.n_batch, a.H, a.W);
+      tb.a[tb.n++] = a;
+      done[i] = true;
+    }
+    if (!temporal_batch_finalize(tb)) return cudaErrorInvalidValue;
+    if (tb.begin[tb.n] > 0) {
+      k_temporal_tm<<<tb.begin[tb.n], kTmThreads, kTmSmem, st>>>(tb, maps, taps);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
-  int L = 1;
-  for (int i = 0; i < b.n; ++i) L = L > b.a[i].L ? L : b.a[i].L;
-  k_temporal<<<blocks, kTempThreads, temporal_smem(L), st>>>(b);
-  return cudaGetLastError();
+  if (gb.n > 0) {
+    if (!temporal_batch_finalize(gb)) return cudaErrorInvalidValue;
+    if (gb.begin[gb.n] > 0) {
+      int L = 1;
+      for (int i = 0; i < gb.n; ++i) L = L > gb.a[i].L ? L : gb.a[i].L;
+      k_temporal<<<gb.begin[gb.n], kTempThreads, temporal_smem(L), st>>>(gb);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_temporal(const TemporalArgs& a, cudaStream_t st) {
