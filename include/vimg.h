@@ -205,6 +205,21 @@ long long vimg_frames_seen(const vimg_handle* h);
  * keeps the template. */
 int vimg_reset(vimg_handle* h);
 
+/* Starts the stream at absolute frame index t_start, a multiple of the segment
+ * length L, as if the frames before it had been processed: segments then fall
+ * on the absolute ranges [iL, (i+1)L) (Sec. III-B), and the shifts, corrected
+ * (or high-passed) frames, segment summaries and traces of frames t >= t_start
+ * equal, bit for bit, those of one stream over the whole video from frame 0.
+ * This is how one video is cut into time shards that independent handles (on
+ * one GPU or several) process.  d_history: device uint16 [n_history][H][W], the
+ * frames t_start - n_history .. t_start - 1; the high-pass needs the last
+ * min(t_start, hp_window - 1) of them (their shifts are estimated; nothing is
+ * output for them, and the whole-video summary images start empty).  Resets
+ * the state first, like vimg_reset.  Enqueued on the handle's stream.  Returns
+ * VIMG_OK or an error (VIMG_ERR_ARG for t_start not a multiple of L or too
+ * short a history). */
+int vimg_seek(vimg_handle* h, long long t_start, const uint16_t* d_history, int n_history);
+
 /* Message for the last failure on h, or for the last failed vimg_create on
  * this host thread when h is NULL.  Never NULL. */
 const char* vimg_last_error(const vimg_handle* h);

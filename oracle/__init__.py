@@ -75,6 +75,8 @@ def lib():
         L.orc_create.restype = P
         L.orc_destroy.argtypes = [P]
         L.orc_set_template.argtypes = [P, P]
+        L.orc_seek.argtypes = [P, ctypes.c_longlong, P, i]
+        L.orc_seek.restype = i
         L.orc_frames_seen.argtypes = [P]
         L.orc_frames_seen.restype = ctypes.c_longlong
         L.orc_process.argtypes = [P, P, i, P, P, P, P, P, P, P, P]
@@ -230,6 +232,14 @@ class Oracle:
         T = _f64(T)
         assert T.shape == (self.H, self.W)
         lib().orc_set_template(self._h, _p(T))
+
+    def seek(self, t_start, history=None):
+        """Starts the stream at absolute frame t_start (a multiple of L) with the
+        frames before it, history [n][H][W], as high-pass history only."""
+        h = None if history is None else _u16(history)
+        n = 0 if h is None else h.shape[0]
+        if lib().orc_seek(self._h, int(t_start), _p(h), n):
+            raise ValueError("bad seek")
 
     def set_rois(self, masks):
         """ROI masks [n_rois][H][W] (nonzero = in the ROI) for the voltage traces."""

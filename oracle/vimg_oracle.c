@@ -358,6 +358,43 @@ int orc_set_rois(orc_t* o, const uint8_t* masks, int n_rois) {
   return 0;
 }
 
+int orc_estimate(const orc_t* o, const uint16_t* F, double* s, int* d, double* info,
+                 double* C_out);
+
+/* Places the stream at absolute frame t_start, a multiple of L (segments are
+ * the absolute ranges [iL, (i+1)L), Sec. III-B), with no open segment; the n
+ * frames before it ([n][H][W], frames t_start - n .. t_start - 1) only fill the
+ * high-pass history (their shifts are estimated, nothing is emitted).  With
+ * n >= min(t_start, hp_w - 1), every later output equals that of one stream
+ * from frame 0.  Returns 0 or -1. */
+int orc_seek(orc_t* o, long long t_start, const uint16_t* frames, int n) {
+  if (!o || t_start < 0 || t_start % o->L != 0 || n < 0 || n > t_start) return -1;
+  if (n > 0 && !o->have_T) return -1;
+  int H = o->H, W = o->W;
+  size_t hw = (size_t)H * W;
+  o->t = t_start - n;
+  o->seg_n = 0;
+  double* V = (double*)malloc(sizeof(double) * hw);
+  if (!V) return -1;
+  for (int i = 0; i < n; ++i) {
+    const uint16_t* F = frames + hw * i;
+    double s[2], inf[3];
+    int d[2];
+    if (orc_estimate(o, F, s, d, inf, NULL)) {
+      free(V);
+      return -1;
+    }
+    orc_resample(F, H, W, s[0], s[1], V);
+    if (o->hp_w > 0) {
+      if (o->t == 0) memcpy(o->first_V, V, sizeof(double) * hw);
+      memcpy(o->ring + hw * (size_t)(o->t % o->hp_w), V, sizeof(double) * hw);
+    }
+    o->t++;
+  }
+  free(V);
+  return 0;
+}
+
 /* Motion estimate of one frame over the full +-R window: shift, integer peak,
  * and {C(d*), second C, flags}.  C_out (optional) receives the (2R+1)^2
  * surface. */

@@ -351,6 +351,47 @@ extern "C" int vimg_reset(vimg_handle* h) {
   return VIMG_OK;
 }
 
+extern "C" int vimg_seek(vimg_handle* h, long long t_start, const uint16_t* d_history,
+                         int n_history) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  const int L = h->p.segment_len;
+  const long long need_ll =
+      std::min<long long>(t_start, h->p.hp_window > 0 ? h->p.hp_window - 1 : 0);
+  if (t_start < 0 || t_start % L != 0 || n_history < 0 || n_history > t_start ||
+      (n_history > 0 && !d_history) || n_history < need_ll)
+    return fail(h, VIMG_ERR_ARG,
+                "vimg_seek: t_start must be a non-negative multiple of the segment length and "
+                "the history must hold the min(t_start, hp_window - 1) frames before it");
+  const int need = (int)need_ll;
+  if (need > 0 && !h->have_template)
+    return fail(h, VIMG_ERR_NO_TEMPLATE, "vimg_set_template must come before vimg_seek");
+  if (need > 0 && (h->p.flags & VIMG_PROPOSAL_CNN) && !h->have_proposal)
+    return fail(h, VIMG_ERR_ARG, "vimg_load_proposal must come before vimg_seek");
+  h->frames_seen = 0;
+  h->carry_n = 0;
+  if (h->vs_acc) {
+    CK(cudaMemsetAsync(h->vs_acc, 0, sizeof(double) * 6 * h->H * h->W, h->st), "summary reset");
+    h->vs_frames = 0;
+  }
+  if (need == 0) {
+    h->frames_seen = t_start;
+    return VIMG_OK;
+  }
+  // the last `need` history frames: their shifts are estimated and they enter
+  // the carried high-pass history; nothing is output and the whole-video sums
+  // do not see them
+  h->frames_seen = t_start - need;
+  double* vs = h->vs_acc;
+  h->vs_acc = nullptr;
+  vimg_io io{};
+  const size_t HW = (size_t)h->H * h->W;
+  const int rc = vimg_process_io(h, d_history + HW * (size_t)(n_history - need), need, &io);
+  h->vs_acc = vs;
+  if (rc < 0) return rc;
+  return h->frames_seen == t_start ? VIMG_OK : fail(h, VIMG_ERR_ARG, "vimg_seek: stream position");
+}
+
 extern "C" int vimg_set_template(vimg_handle* h, const float* d_template) {
   if (!h || !d_template) return fail(h, VIMG_ERR_ARG, "null handle or template");
   if (h->sticky) return h->sticky;

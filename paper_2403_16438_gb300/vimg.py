@@ -62,7 +62,8 @@ class BatchOpts(ctypes.Structure):
 # Every symbol include/vimg.h declares (checked by the host-only tests).
 EXPORTS = [
     "vimg_default_params", "vimg_create", "vimg_destroy", "vimg_set_template", "vimg_process",
-    "vimg_process_io", "vimg_process_host", "vimg_frames_seen", "vimg_reset", "vimg_last_error",
+    "vimg_process_io", "vimg_process_host", "vimg_frames_seen", "vimg_reset", "vimg_seek",
+    "vimg_last_error",
     "vimg_version", "vimg_profile_enable", "vimg_profile_read", "vimg_motion_noalloc",
     "vimg_cnn_param_count", "vimg_cnn_workspace_floats", "vimg_cnn_prepare", "vimg_cnn_pack_bf16",
     "vimg_cnn_forward", "vimg_cnn_loss", "vimg_cnn_backward", "vimg_cnn_adam", "vimg_load_proposal",
@@ -90,6 +91,8 @@ def _load():
     L.vimg_destroy.restype = None
     L.vimg_set_template.argtypes = [vp, vp]
     L.vimg_set_template.restype = i
+    L.vimg_seek.argtypes = [vp, ctypes.c_longlong, vp, i]
+    L.vimg_seek.restype = i
     L.vimg_segmenter_create.argtypes = [i, i, i, vp]
     L.vimg_segmenter_create.restype = vp
     L.vimg_segmenter_destroy.argtypes = [vp]
@@ -244,6 +247,15 @@ class Handle:
         assert template.shape == (self.H, self.W) and template.is_contiguous()
         self._template = template
         self._check(lib.vimg_set_template(self._h, _ptr(template)))
+
+    def seek(self, t_start: int, history: torch.Tensor | None = None):
+        """Starts the stream at absolute frame t_start (a multiple of the segment
+        length); history: cuda uint16 [n, H, W], the frames just before it
+        (vimg_seek)."""
+        n = 0 if history is None else history.shape[0]
+        if history is not None:
+            assert history.is_cuda and history.dtype == torch.uint16 and history.is_contiguous()
+        self._check(lib.vimg_seek(self._h, int(t_start), _ptr(history), n))
 
     def reset(self):
         self._check(lib.vimg_reset(self._h))
