@@ -32,10 +32,32 @@ def test_every_declared_symbol_is_exported(vimg):
     assert sorted(vimg.EXPORTS) == names
 
 
-def test_struct_layouts_match_header(vimg):
-    # vimg_params: 8 ints/floats, a pointer, a long long, an int (+ padding)
-    assert ctypes.sizeof(vimg.Params) == 56
-    assert ctypes.sizeof(vimg.IO) == 8 * 8
+def test_struct_layouts_match_header(vimg, tmp_path):
+    """The binding's structs against the header itself: a C program built with
+    gcc from include/vimg.h prints the sizes and member offsets."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "layout.c"
+    fields = {"vimg_params": [f for f, _ in vimg.Params._fields_],
+              "vimg_io": [f for f, _ in vimg.IO._fields_],
+              "vimg_batch_opts": [f for f, _ in vimg.BatchOpts._fields_]}
+    body = "".join(
+        f'  printf("{t} %zu", sizeof({t}));' + "".join(
+            f' printf(" %zu", offsetof({t}, {f}));' for f in fs) + ' printf("\\n");\n'
+        for t, fs in fields.items())
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "vimg.h"\n'
+                   "int main(void) {\n" + body + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    for line, (cls, t) in zip(out, [(vimg.Params, "vimg_params"), (vimg.IO, "vimg_io"),
+                                    (vimg.BatchOpts, "vimg_batch_opts")]):
+        name, size, *offs = line.split()
+        assert name == t and int(size) == ctypes.sizeof(cls)
+        assert [int(o) for o in offs] == [getattr(cls, f).offset for f, _ in cls._fields_]
 
 
 def test_defaults(vimg):
