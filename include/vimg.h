@@ -352,6 +352,12 @@ int vimg_motion_noalloc(const float* d_template, const uint16_t* d_frames, int n
 /* Library version string. */
 const char* vimg_version(void);
 
+/* Measures the device's FP32 FMA rate (FLOP/s, 2 per FMA) with a kernel of
+ * independent FMA chains on every SM, timed on `stream` (NULL = default) after
+ * a warm-up run; synchronous.  The denominator of the FP32 correlation kernel's
+ * ALU roofline.  The paper has no counterpart.  Returns VIMG_OK or an error. */
+int vimg_fma_rate(void* stream, double* flops_per_s);
+
 /* ---- spiking-pixel U-Net (Sec. III-C) ---------------------------------------
  * A U-Net on 64x64 patches of a segment's summary pair (S_i, T_i) gives the
  * probability that spiking neurons lie at each pixel during the segment; the

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libvimg.so")
 SOURCES = ["abi.cu", "motion.cu", "temporal.cu", "noalloc.cu", "cnn.cu", "corr_bf16.cu", "unet.cu",
-           "segment.cu"]
+           "segment.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

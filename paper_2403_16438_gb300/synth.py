@@ -460,3 +460,34 @@ def disc_chain_maps() -> torch.Tensor:
         out[k % 2][disc(70, 10 + 6 * k, 4)] = 0.85
     out[0][disc(75, 500, 6)] = 0.85
     return out
+
+
+def make_video_range(cfg: VideoConfig, n_total: int, t0: int, t1: int, device="cpu",
+                     chunk: int = 256):
+    """Frames [t0, t1) of one n_total-frame video (for a time shard): the scene,
+    drift and activity of the whole video, rendered only over the range, with
+    the noise drawn for the range (generator seeded by the seed and t0), and
+    the video's template (independent of the range).  Returns (frames uint16
+    [t1 - t0, H, W], planted shifts float64 [t1 - t0, 2], template float32)."""
+    if not 0 <= t0 <= t1 <= n_total:
+        raise ValueError("bad frame range")
+    device = torch.device(device)
+    g_cpu = torch.Generator().manual_seed(cfg.seed)
+    scene = make_scene(cfg, g_cpu)
+    shifts = planted_shifts(cfg, n_total, g_cpu)
+    act = activity(scene, n_total, g_cpu)
+    g_dev = torch.Generator(device=device).manual_seed(cfg.seed + 7919 + 1000003 * t0)
+    frames = torch.empty((t1 - t0, cfg.H, cfg.W), dtype=torch.uint16, device=device)
+    for a in range(t0, t1, chunk):
+        b = min(t1, a + chunk)
+        exp_ = render(scene, shifts[a:b], act[a:b], device)
+        frames[a - t0:b - t0].copy_(add_noise(exp_, cfg.read_sigma, g_dev))
+    g_t = torch.Generator(device=device).manual_seed(cfg.seed + 104729)
+    nt = cfg.template_frames
+    act_t = activity(scene, nt, torch.Generator().manual_seed(cfg.seed + 1))
+    acc = torch.zeros((cfg.H, cfg.W), dtype=torch.float64, device=device)
+    for a in range(0, nt, chunk):
+        b = min(nt, a + chunk)
+        exp_ = render(scene, torch.zeros((b - a, 2), dtype=torch.float64), act_t[a:b], device)
+        acc += add_noise(exp_, cfg.read_sigma, g_t).to(torch.float64).sum(0)
+    return frames, shifts[t0:t1], (acc / nt).to(torch.float32)

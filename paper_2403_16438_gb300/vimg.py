@@ -72,7 +72,7 @@ EXPORTS = [
     "vimg_unet_last_error", "vimg_unet_load", "vimg_unet_run", "vimg_unet_synchronize",
     "vimg_unet_profile", "vimg_unet_profile_read", "vimg_attach_unet", "vimg_unet_activation",
     "vimg_video_summary", "vimg_segmenter_create", "vimg_segmenter_destroy",
-    "vimg_segmenter_last_error", "vimg_segment", "vimg_segment_status",
+    "vimg_segmenter_last_error", "vimg_segment", "vimg_segment_status", "vimg_fma_rate",
 ]
 NSTAGES = 7
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy", "downstream"]
@@ -93,6 +93,8 @@ def _load():
     L.vimg_set_template.restype = i
     L.vimg_seek.argtypes = [vp, ctypes.c_longlong, vp, i]
     L.vimg_seek.restype = i
+    L.vimg_fma_rate.argtypes = [vp, P(ctypes.c_double)]
+    L.vimg_fma_rate.restype = i
     L.vimg_segmenter_create.argtypes = [i, i, i, vp]
     L.vimg_segmenter_create.restype = vp
     L.vimg_segmenter_destroy.argtypes = [vp]
@@ -186,6 +188,17 @@ class VimgError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"vimg error {code}: {msg}")
         self.code = code
+
+
+def fma_rate(stream=None) -> float:
+    """Measured FP32 FMA rate of the current device, FLOP/s (vimg_fma_rate)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_double()
+    rc = lib.vimg_fma_rate(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out))
+    if rc < 0:
+        raise VimgError(rc, "vimg_fma_rate failed")
+    return out.value
 
 
 def default_params() -> Params:

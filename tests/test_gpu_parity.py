@@ -211,3 +211,13 @@ def test_host_buffer_entry_point(vimg, tiny):
     assert np.array_equal(sh.numpy(), g["shifts"])
     assert np.array_equal(sm.numpy(), g["summary"])
     h.close()
+
+
+def test_fma_rate_is_plausible(vimg):
+    """The measured FP32 FMA rate (the FP32 correlation's ALU roofline): below
+    the nominal 128 FMA lanes x 2 FLOP x the maximum clock of every SM, and far
+    above a small fraction of it."""
+    rate = vimg.fma_rate()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * 2 * 2.2e9
+    assert 0.3 * nominal < rate <= nominal, (rate, nominal)

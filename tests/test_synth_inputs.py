@@ -5,6 +5,7 @@ its planted shift; and the same seed gives the same video."""
 import math
 
 import numpy as np
+import pytest
 import torch
 
 from paper_2403_16438_gb300 import synth
@@ -129,3 +130,21 @@ def test_same_seed_same_video():
     assert torch.equal(t1, t2)
     f3, s3, _ = synth.make_video(synth.tiny_config(seed=7), 12)
     assert not torch.equal(f1.to(torch.int32), f3.to(torch.int32)) and not torch.equal(s1, s3)
+
+
+def test_frame_range_of_one_video():
+    """make_video_range: the planted drift of a range is that slice of the whole
+    video's drift, the template does not depend on the range, and frames of a
+    range follow the same content (mean counts close to the whole video's)."""
+    cfg = synth.tiny_config(seed=77)
+    n = 240
+    _, full_shifts, _ = synth.ground_truth(cfg, n)
+    f0, s0, T0 = synth.make_video_range(cfg, n, 0, 100)
+    f1, s1, T1 = synth.make_video_range(cfg, n, 100, 240)
+    assert torch.equal(s0, full_shifts[:100]) and torch.equal(s1, full_shifts[100:])
+    assert torch.equal(T0, T1)
+    ref, _, _ = synth.make_video(cfg, n)
+    m_ref = ref.double().mean().item()
+    assert abs(f1.double().mean().item() - m_ref) < 0.02 * m_ref
+    with pytest.raises(ValueError):
+        synth.make_video_range(cfg, n, 200, 100)
