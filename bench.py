@@ -166,6 +166,33 @@ def max_over_ranks(x, ws, device):
     return t.item()
 
 
+def gpu_local_cpus(index):
+    """Host CPUs local to GPU `index` (sysfs local_cpulist of its PCI device), or
+    None.  Pinned host buffers first touched from those CPUs live on the GPU's
+    NUMA node; from a remote node the host -> device copies run several times
+    slower."""
+    try:
+        bus = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist"
+        with open(path) as f:
+            return parse_cpulist(f.read()) or None
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None
+
+
+def parse_cpulist(spec):
+    """The set of CPUs of a sysfs cpulist such as '0-3,8,10-11'."""
+    cpus = set()
+    for part in spec.strip().split(","):
+        if part:
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -456,6 +483,14 @@ def run_vimg(args):
     # end to end through the public API with host buffers
     if not args.no_e2e:
         ke = max(1, min(args.steps, args.e2e_steps))
+        # host work of this leg on the GPU's own NUMA node (pinned buffers included)
+        prev_aff = os.sched_getaffinity(0)
+        local_cpus = gpu_local_cpus(local)
+        if local_cpus:
+            try:
+                os.sched_setaffinity(0, local_cpus & set(range(os.cpu_count() or 1)) or prev_aff)
+            except OSError:
+                local_cpus = None
         fh = torch.empty((n, H, W), dtype=torch.uint16, pin_memory=True)
         fh.copy_(frames.cpu())
         sh_h = torch.empty((n, 2), pin_memory=True)
@@ -480,9 +515,12 @@ def run_vimg(args):
                        "h2d_bytes_per_step": n * H * W * 2,
                        "d2h_bytes_per_step": n * 2 * 4 + k_max * 2 * H * W * 4,
                        "steps": ke, "h2d_GBs_measured": h2d_gbs,
+                       "host_cpus": (f"{min(local_cpus)}-{max(local_cpus)} ({len(local_cpus)} "
+                                     "CPUs local to the GPU)") if local_cpus else "not pinned",
                        "note": "vimg_process_host: pinned host frames in, shifts and summaries "
                                "out; corrected frames stay in device memory"}
-        del fh
+        del fh, sh_h, sm_h
+        os.sched_setaffinity(0, prev_aff)
     if not args.no_variants:
         line["variants"] = run_variants(args, frames, planted, T, shifts, corrected, summary, stream,
                                         dev, k_max, ws)

@@ -67,3 +67,10 @@ def test_committed_traffic_record_names_a_profile_summary():
         rec = json.load(f)["k_corr_f32"]
     assert rec["frames_per_launch"] == 200 and rec["dram_bytes_per_launch"] > 0
     assert os.path.exists(os.path.join(bench.ROOT, rec["from"].split(" ")[0]))
+
+
+def test_cpulist_parsing():
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("72-143") == set(range(72, 144))
+    assert bench.parse_cpulist("") == set()
