@@ -1139,6 +1139,9 @@ extern "C" int vimg_synchronize(vimg_handle* h) {
   int derr = 0;
   CK(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->st), "status copy");
   CK(cudaStreamSynchronize(h->st), "stream sync");
-  if (derr) return fail(h, VIMG_ERR_TIMEOUT, "a device-side wait gave up");
+  if (derr)
+    return fail(h, VIMG_ERR_TIMEOUT,
+                "a device-side wait gave up (flag " +
+                    std::to_string(derr) + ")");
   return VIMG_OK;
 }

@@ -585,12 +585,13 @@ constexpr int kTmCols = 512;
 constexpr size_t kTmSmemUsed = 2 * kTmGroups * (size_t)kStStride +
                                sizeof(float) * (kTmGroups * (size_t)kExt * (kVS + kHS) + 2 * kMaxL) +
                                (sizeof(float2) + 2 * sizeof(int4)) * kMaxL;
-// Shared memory requested per CTA: more than half of the SM's, so that one CTA
-// (which holds all of the SM's tensor memory) runs per SM.
-constexpr size_t kTmSmem = kTmSmemUsed > 120 * 1024 ? kTmSmemUsed : 120 * 1024;
+// Shared memory requested per CTA (the layout plus 128 bytes to align its start):
+// more than half of the SM's, so that one CTA (which holds all of the SM's
+// tensor memory) runs per SM.
+constexpr size_t kTmSmem = kTmSmemUsed + 128 > 120 * 1024 ? kTmSmemUsed + 128 : 120 * 1024;
 static_assert(kTmGroups * 8 * kTmGroup * sizeof(float) <= kTmGroups * sizeof(float) * kExt * kVS,
               "partial-sum exchange fits the resampled-tile buffers");
-static_assert(kTmSmemUsed <= 227 * 1024, "shared memory of the tensor-memory temporal kernel");
+static_assert(kTmSmemUsed + 128 <= 227 * 1024, "shared memory of the tensor-memory temporal kernel");
 
 struct TemporalMaps {
   CUtensorMap m[kMaxVideos][2];  // per job: [0] carry buffer, [1] caller's batch
@@ -730,10 +731,13 @@ __device__ __forceinline__ int mirror_local(int i, int o, int n) {
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_temporal_tm(const __grid_constant__ TemporalBatch b, const __grid_constant__ TemporalMaps maps,
                   const __grid_constant__ TemporalTaps taps) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kTmGroups][2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_any;
+  // TMA destinations start on 128-byte boundaries: the dynamic region is
+  // aligned here (the launch requests 128 bytes more than the layout needs)
+  unsigned char* smraw = smem_raw + ((128u - (tc::su32(smem_raw) & 127u)) & 127u);
   const int jb = job_of(b.begin, b.n, blockIdx.x);
   const TemporalArgs& a = b.a[jb];
   const int H = a.H, W = a.W, L = a.L, HW = H * W;
