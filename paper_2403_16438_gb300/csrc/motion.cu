@@ -309,9 +309,10 @@ cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid
 // windows use.  Twelve warps then each own one output-row pass:
 //   pass u < G:   lane = dy in 0..31, all lanes on patch u (template loads are
 //                 warp-uniform, frame rows distinct);
-//   pass G:       lane = u, dy = 32 (the 33rd displacement row, when 2R+1 = 33).
+//   pass G:       the 33rd displacement row (dy = 32, when 2R+1 = 33) of all G
+//                 patches, lane = (u, half of the columns), 17 columns per lane.
 // A lane streams the 21 frame rows it needs: per row 53 shared loads feed
-// 21 x 33 FMAs into 33 register accumulators.  Each finished row is normalised
+// 21 x 33 FMAs into 33 register accumulators (37 loads, 21 x 17 FMAs in pass G).  Each finished row is normalised
 // and added in 2^-40 fixed point to the item's int64 surface in shared memory,
 // which is finally added to the frame's global sums.
 //
@@ -326,6 +327,7 @@ constexpr int kIsfCols = (kGroup - 1) * kPatch + kMaxWin;           // 243
 constexpr int kGroupWarps = kGroup + 1;
 constexpr int kGroupThreads = kGroupWarps * 32;                     // 384
 constexpr int kCorrThreads = 2 * kGroupThreads;                     // 768
+constexpr int kHalfRow = 17;  // columns per lane in the 33rd-row pass (0..16 or 16..32)
 constexpr size_t kGroupSmem = sizeof(unsigned long long) * kCsEntries +
                               sizeof(float) * kMaxWin * kIsfCols +
                               sizeof(float) * kRegionRows * kRegionStride;
@@ -470,29 +472,47 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
     // One output-row pass per warp.
     const int n_pass = G + (w > 32 ? 1 : 0);
     for (int pass = gwarp; pass < n_pass; pass += kGroupWarps) {
-      int u, dy;
       if (pass < G) {
-        u = pass;
-        dy = lane;
-      } else {
-        u = lane;
-        dy = 32;
-      }
-      const bool active = u < G && dy < w;
-      const int uu = active ? u : 0, dd = active ? dy : 0;
-      float acc[NX];
-      corr_row<NX>(reg + dd * rs + uu * kPatch, rs, tc + (size_t)(p0 + uu) * kPatch * kTplStride,
-                   acc);
-      if (active) {
-        const float t2 = __ldg(tn2 + p0 + uu);
-        const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
-        const float* iv = ism + dd * scols + uu * kPatch;
-        unsigned long long* crow = cs + dd * w;
+        const int u = pass, dy = lane;
+        const bool active = dy < w;
+        const int dd = active ? dy : 0;
+        float acc[NX];
+        corr_row<NX>(reg + dd * rs + u * kPatch, rs, tc + (size_t)(p0 + u) * kPatch * kTplStride,
+                     acc);
+        if (active) {
+          const float t2 = __ldg(tn2 + p0 + u);
+          const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+          const float* iv = ism + dd * scols + u * kPatch;
+          unsigned long long* crow = cs + dd * w;
 #pragma unroll
-        for (int j = 0; j < NX; ++j) {
-          if (j < w) {
-            const float z = acc[j] * pscale * iv[j];
-            atomicAdd(crow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
+          for (int j = 0; j < NX; ++j) {
+            if (j < w) {
+              const float z = acc[j] * pscale * iv[j];
+              atomicAdd(crow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
+            }
+          }
+        }
+      } else {
+        // The 33rd displacement row (dy = 32; this pass exists only for 2R + 1 = 33)
+        // of all G patches: lane = (u = lane & 15, columns 0..16 or 16..32), 17
+        // accumulators each, column 16 kept by the first half.
+        const int u = lane & 15, half = lane >> 4, dx0 = 16 * half;
+        const bool active = u < G;
+        const int uu = active ? u : 0;
+        float acc[kHalfRow];
+        corr_row<kHalfRow>(reg + 32 * rs + uu * kPatch + dx0, rs,
+                           tc + (size_t)(p0 + uu) * kPatch * kTplStride, acc);
+        if (active) {
+          const float t2 = __ldg(tn2 + p0 + uu);
+          const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
+          const float* iv = ism + 32 * scols + uu * kPatch + dx0;
+          unsigned long long* crow = cs + 32 * w + dx0;
+#pragma unroll
+          for (int j = 0; j < kHalfRow; ++j) {
+            if (half == 0 || j > 0) {
+              const float z = acc[j] * pscale * iv[j];
+              atomicAdd(crow + j, (unsigned long long)__float2ll_rn(z * (float)kFix));
+            }
           }
         }
       }
