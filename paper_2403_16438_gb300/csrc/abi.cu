@@ -37,6 +37,8 @@ struct Prof {
 };
 }  // namespace
 
+constexpr int kRing = 3;  // frame stages of vimg_process_host
+
 struct vimg_handle {
   int H = 0, W = 0;
   vimg_params p{};
@@ -75,12 +77,16 @@ struct vimg_handle {
   int carry_cap = 0, carry_n = 0, carry_cur = 0;
   long long frames_seen = 0;
   // host-buffer path
-  uint16_t* stage[2] = {nullptr, nullptr};
-  float* stage_shift = nullptr;   // [max_chunk][2]
-  float* stage_summary = nullptr; // [max segments per batch][2][H][W]
-  cudaStream_t copy_st = nullptr;
-  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-  cudaEvent_t ev_used[2] = {nullptr, nullptr};
+  // vimg_process_host: a ring of kRing frame stages (uploads run up to kRing - 1
+  // batches ahead of the compute), two output stages downloaded on their own stream
+  uint16_t* stage[kRing] = {};
+  float* stage_shift[2] = {};    // [max_chunk][2]
+  float* stage_summary[2] = {};  // [max segments per batch][2][H][W]
+  cudaStream_t copy_st = nullptr, dl_st = nullptr;
+  cudaEvent_t ev_copied[kRing] = {};
+  cudaEvent_t ev_used[kRing] = {};
+  cudaEvent_t ev_out[2] = {};   // a batch's outputs are complete in the output stage
+  cudaEvent_t ev_dl[2] = {};    // the output stage has been downloaded
   Prof prof;
   int sticky = 0;
   std::string err;
@@ -174,17 +180,23 @@ static bool grid_for(int H, int W, int R, PatchGrid* g) {
 static void free_all(vimg_handle* h) {
   void* ptrs[] = {h->td.tc, h->td.tn2, h->td.coff, h->inv, h->csum, h->shift_tmp,
                   h->carry[0], h->carry[1], h->carry_shift[0], h->carry_shift[1],
-                  h->stage[0], h->stage[1], h->stage_shift, h->stage_summary, h->tmpl,
+                  h->stage[0], h->stage[1], h->stage[2], h->stage_shift[0], h->stage_shift[1],
+                  h->stage_summary[0], h->stage_summary[1], h->tmpl,
                   h->cnn_p, h->cnn_b, h->cnn_acts, h->prop, h->csum_n, h->fb_list, h->fb_n,
                   h->fb_total, h->tround, h->as, h->bgc, h->fc, h->dev_err, h->num,
                   h->roi_members, h->roi_count, h->roi_acc, h->roi_flag, h->vs_acc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kRing; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
   }
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+    if (h->ev_dl[i]) cudaEventDestroy(h->ev_dl[i]);
+  }
   if (h->copy_st) cudaStreamDestroy(h->copy_st);
+  if (h->dl_st) cudaStreamDestroy(h->dl_st);
   for (auto& ge : h->graphs)
     if (ge.exec) cudaGraphExecDestroy(ge.exec);
   h->graphs.clear();
@@ -328,6 +340,7 @@ extern "C" void vimg_destroy(vimg_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   if (h->copy_st) cudaStreamSynchronize(h->copy_st);
+  if (h->dl_st) cudaStreamSynchronize(h->dl_st);
   free_all(h);
   delete h;
 }
@@ -968,18 +981,29 @@ extern "C" int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n
   const int L = h->p.segment_len, maxc = h->p.max_chunk;
   const int max_seg = (L - 1 + maxc) / L;
   if (!h->stage[0]) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kRing; ++i) {
       CK(cudaMalloc((void**)&h->stage[i], sizeof(uint16_t) * HW * maxc), "stage alloc");
       CK(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming), "event");
       CK(cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming), "event");
       CK(cudaEventRecord(h->ev_used[i], h->st), "event record");
     }
-    CK(cudaMalloc((void**)&h->stage_shift, sizeof(float) * 2 * maxc), "stage alloc");
-    CK(cudaMalloc((void**)&h->stage_summary, sizeof(float) * 2 * HW * std::max(1, max_seg)),
-       "stage alloc");
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaMalloc((void**)&h->stage_shift[i], sizeof(float) * 2 * maxc), "stage alloc");
+      CK(cudaMalloc((void**)&h->stage_summary[i],
+                    sizeof(float) * 2 * HW * std::max(1, max_seg)),
+         "stage alloc");
+      CK(cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming), "event");
+      CK(cudaEventCreateWithFlags(&h->ev_dl[i], cudaEventDisableTiming), "event");
+      CK(cudaEventRecord(h->ev_dl[i], h->st), "event record");
+    }
     CK(cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking), "copy stream");
+    CK(cudaStreamCreateWithFlags(&h->dl_st, cudaStreamNonBlocking), "download stream");
   }
-  int done = 0, k_total = 0, buf = 0;
+  // Three streams: uploads (copy_st) into a ring of kRing frame stages, compute
+  // (st), downloads (dl_st) from two output stages.  Only events order them, so
+  // a slow copy in either direction stalls the compute only when the ring (or
+  // the output pair) is exhausted.
+  int done = 0, k_total = 0, buf = 0, ob = 0;
   while (done < n) {
     int m = std::min(n - done, maxc);
     if (m < n - done) {
@@ -993,25 +1017,33 @@ extern "C" int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n
        "frames upload");
     CK(cudaEventRecord(h->ev_copied[buf], h->copy_st), "event record");
     CK(cudaStreamWaitEvent(h->st, h->ev_copied[buf], 0), "wait");
+    // the output stage ob is free once its previous download has finished
+    CK(cudaStreamWaitEvent(h->st, h->ev_dl[ob], 0), "wait");
     vimg_io io{};
-    io.shifts = h->stage_shift;
+    io.shifts = h->stage_shift[ob];
     io.corrected = d_corrected_out ? d_corrected_out + HW * done : nullptr;
-    io.summary = h_summary_out ? h->stage_summary : nullptr;
+    io.summary = h_summary_out ? h->stage_summary[ob] : nullptr;
     int k = vimg_process_io(h, h->stage[buf], m, &io);
     if (k < 0) return k;
     CK(cudaEventRecord(h->ev_used[buf], h->st), "event record");
+    CK(cudaEventRecord(h->ev_out[ob], h->st), "event record");
+    CK(cudaStreamWaitEvent(h->dl_st, h->ev_out[ob], 0), "wait");
     if (h_shifts_out)
-      CK(cudaMemcpyAsync(h_shifts_out + 2 * (size_t)done, h->stage_shift, sizeof(float) * 2 * m,
-                         cudaMemcpyDeviceToHost, h->st),
+      CK(cudaMemcpyAsync(h_shifts_out + 2 * (size_t)done, h->stage_shift[ob],
+                         sizeof(float) * 2 * m, cudaMemcpyDeviceToHost, h->dl_st),
          "shifts download");
     if (h_summary_out && k > 0)
-      CK(cudaMemcpyAsync(h_summary_out + 2 * HW * (size_t)k_total, h->stage_summary,
-                         sizeof(float) * 2 * HW * k, cudaMemcpyDeviceToHost, h->st),
+      CK(cudaMemcpyAsync(h_summary_out + 2 * HW * (size_t)k_total, h->stage_summary[ob],
+                         sizeof(float) * 2 * HW * k, cudaMemcpyDeviceToHost, h->dl_st),
          "summary download");
+    CK(cudaEventRecord(h->ev_dl[ob], h->dl_st), "event record");
     k_total += k;
     done += m;
-    buf ^= 1;
+    buf = (buf + 1) % kRing;
+    ob ^= 1;
   }
+  // the caller's next work on the handle's stream sees the downloads complete
+  CK(cudaStreamWaitEvent(h->st, h->ev_dl[ob ^ 1], 0), "wait");
   CK(cudaStreamSynchronize(h->st), "stream sync");
   return k_total;
 }

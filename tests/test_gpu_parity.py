@@ -197,15 +197,25 @@ def test_edge_cases(vimg):
         vimg.Handle(40, 40, search_radius=16)  # 40 < 2R + 21
 
 
-def test_host_buffer_entry_point(vimg, tiny):
+@pytest.mark.parametrize("max_chunk,split", [(40, None), (10, None), (10, 70)])
+def test_host_buffer_entry_point(vimg, tiny, max_chunk, split):
+    """vimg_process_host against the device-buffer path, bit for bit: batches of
+    max_chunk frames through the ring of upload stages and the pair of download
+    stages (max_chunk = 10 wraps both several times), and the stream split
+    over two calls at frame `split` (the second call's uploads and downloads
+    follow the first's)."""
     frames, _, T = tiny
     n, H, W = frames.shape
-    h = vimg.Handle(H, W, max_chunk=40)
+    h = vimg.Handle(H, W, max_chunk=max_chunk)
     h.set_template(T.to(DEV))
     fh = frames.pin_memory()
     sh = torch.zeros((n, 2)).pin_memory()
     sm = torch.zeros((n // 50, 2, H, W)).pin_memory()
-    k = h.process_host(fh, shifts_host=sh, summary_host=sm)
+    if split is None:
+        k = h.process_host(fh, shifts_host=sh, summary_host=sm)
+    else:
+        k1 = h.process_host(fh[:split], shifts_host=sh[:split], summary_host=sm)
+        k = k1 + h.process_host(fh[split:], shifts_host=sh[split:], summary_host=sm[k1:])
     assert k == 2
     g = run_gpu(vimg, frames, T)
     assert np.array_equal(sh.numpy(), g["shifts"])
