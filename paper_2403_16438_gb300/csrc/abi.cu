@@ -520,7 +520,8 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
        "narrow peak launch");
     prof_end(h, ps);
     ps = prof_begin(h, 0);
-    CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st, h->fb_list, h->fb_n),
+    CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st, h->fb_list, h->fb_n,
+                    h->dev_err),
        "fallback window statistics launch");
     prof_end(h, ps);
     ps = prof_begin(h, 1);
@@ -539,7 +540,8 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
   // One launch per stage for the whole batch: thousands of CTAs, so the last
   // partial wave costs little.
   int ps = prof_begin(h, 0);
-  CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st),
+  CK(launch_stats(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->st, nullptr, nullptr,
+                  h->dev_err),
      "window statistics launch");
   prof_end(h, ps);
   ps = prof_begin(h, 1);
@@ -784,7 +786,7 @@ static int batch_body(const BatchCall& c, cudaStream_t st, std::vector<int>& seg
         J.frames = fr[i], J.nf = m[v], J.H = hv->H, J.W = hv->W, J.g = hv->g;
         J.R = hv->p.search_radius;
         J.tc = hv->td.tc, J.tn2 = hv->td.tn2, J.coff = hv->td.coff;
-        J.isf = hv->inv, J.csum = hv->csum, J.shifts = sh_out[i];
+        J.isf = hv->inv, J.csum = hv->csum, J.shifts = sh_out[i], J.err = hv->dev_err;
         CK(cudaMemsetAsync(hv->csum, 0, sizeof(unsigned long long) * (size_t)m[v] * hv->nwin, st),
            "surface reset");
       }

@@ -14,7 +14,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstdio>
+#include <cstring>
 
+#include "tc_ptx.h"
 #include "vimg_internal.h"
 
 namespace vimg {
@@ -121,8 +123,10 @@ template <typename Acc2>
 __device__ __forceinline__ void box_sums(const int* __restrict__ in, int* __restrict__ rs1,
                                          Acc2* __restrict__ rs2, int c, int by, int bx, int sh,
                                          int sw, float* __restrict__ out) {
+  // job = (column chunk, row) with the row fastest: the lanes of a warp take
+  // consecutive rows, whose strides (53 and 33 words) put them in distinct banks
   for (int job = threadIdx.x; job < kBoxIR * 3; job += kBoxThreads) {
-    const int r = job / 3, c0 = (job - 3 * r) * kBoxChunk;
+    const int q = job / kBoxIR, r = job - q * kBoxIR, c0 = q * kBoxChunk;
     const int n = min(kBoxChunk, kBoxCols - c0);
     const int* row = in + r * kBoxInStride + c0;
     int s1 = 0;
@@ -244,6 +248,129 @@ __global__ void __launch_bounds__(kBoxThreads, 4)
   }
 }
 
+// The same statistics with each block's 76 x 52 input tile staged by one 3-D TMA
+// box (64 columns from the block's first input column rounded down to a multiple
+// of 8, so the copy's x coordinate is 16-byte aligned) instead of 16 indexed
+// 16-bit loads per thread: one pass then copies the tile into the odd-stride
+// integer layout of box_sums and takes the range of the pixels that in-map
+// windows read.  Coordinates outside the image read zeros (in-map windows never
+// reach them).  The tile shares its space with the squared row sums, which are
+// written only after the copy pass.  Outputs are those of k_boxstats bit for bit
+// (exact integer sums, same SF and rsqrtf).
+struct StatsMaps {
+  CUtensorMap m[kMaxVideos];  // per job: the frames [nf][H][W] (uint16), boxes 64 x 76 x 1
+};
+constexpr int kBoxTmaW = 64;
+constexpr int kBoxTmaBytes = kBoxTmaW * kBoxIR * 2;
+constexpr size_t kBoxRs2Bytes = ((size_t)kBoxIR * kBoxRsStride * 8 + 127) & ~(size_t)127;
+constexpr size_t kBoxTmaSmem = kBoxRs2Bytes + sizeof(int) * kBoxIR * kBoxInStride +
+                               sizeof(int) * kBoxIR * kBoxRsStride + 128;
+static_assert(kBoxTmaBytes <= (int)kBoxRs2Bytes, "the staged tile fits the squared row sums");
+static_assert(kBoxIC + 7 <= kBoxTmaW, "the box covers the tile after the alignment shift");
+static_assert(kBoxTmaSmem <= 48 * 1024, "no shared-memory attribute needed");
+
+__global__ void __launch_bounds__(kBoxThreads, 4)
+    k_boxstats_tma(const __grid_constant__ MotionBatch b, const __grid_constant__ StatsMaps maps,
+                   const int* __restrict__ list, const int* __restrict__ list_n) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full;
+  __shared__ unsigned wmin[kBoxThreads / 32], wmax[kBoxThreads / 32];
+  // TMA destinations start on 128-byte boundaries: the dynamic region is
+  // aligned here (the launch requests 128 bytes more than the layout needs)
+  unsigned char* sm = smem_raw + ((128u - (tc::su32(smem_raw) & 127u)) & 127u);
+  long long* rs2 = reinterpret_cast<long long*>(sm);
+  const unsigned short* tin = reinterpret_cast<const unsigned short*>(sm);  // [76][64]
+  int* in = reinterpret_cast<int*>(sm + kBoxRs2Bytes);
+  int* rs1 = in + kBoxIR * kBoxInStride;
+  int n_items = b.stats_begin[b.n];
+  if (list) {
+    const MotionJob& J0 = b.j[0];
+    n_items = min(J0.nf, *list_n) * stats_tiles(J0.g, J0.R);
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int jb = list ? 0 : job_of(b.stats_begin, b.n, item);
+    const MotionJob& J = b.j[jb];
+    int oy, ox, sh, sw;
+    stats_map_dims(J.g, J.R, &oy, &ox, &sh, &sw);
+    const int ntx = (sw + kBoxCols - 1) / kBoxCols, per = ntx * ((sh + kBoxRows - 1) / kBoxRows);
+    const int local = item - (list ? 0 : b.stats_begin[jb]);
+    const int fi = local / per, rem = local - fi * per;
+    const int f = list ? list[fi] : fi;
+    const int by = (rem / ntx) * kBoxRows, bx = (rem % ntx) * kBoxCols;
+    const int x = ox + bx, x0 = x & ~7, oxs = x - x0;  // ox >= 0
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last item's reads
+      tc::mbar_expect_tx(&full, kBoxTmaBytes);
+      tc::tma_load_3d(sm, &maps.m[jb], x0, oy + by, f, &full);
+    }
+    const bool late = !tc::mbar_wait(&full, phase);
+    if (__syncthreads_or(late)) {  // give up on the whole block, report, drain the copy
+      if (threadIdx.x == 0) {
+        if (J.err) atomicExch(J.err, 1);
+        tc::mbar_wait(&full, phase);
+      }
+      return;
+    }
+    phase ^= 1u;
+    // tile -> odd-stride integers; range of the pixels in-map windows read
+    const int ir = min(kBoxIR, sh - by + kPatch - 1), ic = min(kBoxIC, sw - bx + kPatch - 1);
+    unsigned mn = 0xffffu, mx = 0u;
+    {
+      const int cc = threadIdx.x & 63;
+      for (int r = threadIdx.x >> 6; r < kBoxIR; r += kBoxThreads / 64) {
+        if (cc < kBoxIC) {
+          const unsigned v = tin[r * kBoxTmaW + oxs + cc];
+          in[r * kBoxInStride + cc] = (int)v;
+          if (r < ir && cc < ic) {
+            mn = min(mn, v);
+            mx = max(mx, v);
+          }
+        }
+      }
+    }
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) {
+      wmin[threadIdx.x >> 5] = mn;
+      wmax[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    mn = wmin[0], mx = wmax[0];
+#pragma unroll
+    for (int w = 1; w < kBoxThreads / 32; ++w) {
+      mn = min(mn, wmin[w]);
+      mx = max(mx, wmax[w]);
+    }
+    const int c = (int)((mn + mx) >> 1);
+    float* out = J.isf + (size_t)f * sh * sw;
+    if ((int)mx - c <= kBoxDev32)
+      box_sums<unsigned>(in, rs1, reinterpret_cast<unsigned*>(rs2), c, by, bx, sh, sw, out);
+    else
+      box_sums<long long>(in, rs1, rs2, c, by, bx, sh, sw, out);
+    __syncthreads();  // the tile space and the shared buffers are reused by the next item
+  }
+}
+
+// 3-D TMA map of a uint16 frame buffer [n][H][W], boxes box_w x box_h x 1.
+static bool frames_map_3d(CUtensorMap* m, const uint16_t* base, int n, int H, int W, int box_w,
+                          int box_h) {
+  tc::EncodeTiledFn fn = tc::encode_fn();
+  if (!fn || !base || n < 1) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+  cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)H * W * 2};
+  cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 size_t stats_map_floats(PatchGrid g, int R) {
   int oy, ox, sh, sw;
   stats_map_dims(g, R, &oy, &ox, &sh, &sw);
@@ -285,17 +412,33 @@ cudaError_t launch_stats_multi(const MotionBatch& b, cudaStream_t st, const int*
     if (e != cudaSuccess) return e;
     blocks = std::min(blocks, 4 * sm_count());
   }
-  k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b, list, list_n);
+  // the TMA-staged kernel when every job can report a wait that gave up and
+  // its frames allow 16-byte aligned boxes
+  StatsMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  bool tma = true;
+  for (int i = 0; i < b.n && tma; ++i) {
+    const MotionJob& J = b.j[i];
+    if (J.nf == 0) continue;
+    tma = J.err != nullptr && J.W % 8 == 0 &&
+          (reinterpret_cast<uintptr_t>(J.frames) & 15) == 0 &&
+          frames_map_3d(&maps.m[i], J.frames, J.nf, J.H, J.W, kBoxTmaW, kBoxIR);
+  }
+  if (tma)
+    k_boxstats_tma<<<blocks, kBoxThreads, kBoxTmaSmem, st>>>(b, maps, list, list_n);
+  else
+    k_boxstats<<<blocks, kBoxThreads, 0, st>>>(b, list, list_n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                          const TemplateDev& td, float* isf, cudaStream_t st, const int* list,
-                         const int* list_n) {
+                         const int* list_n, int* err) {
   if (nf <= 0) return cudaSuccess;
   MotionBatch b{};
   b.n = 1;
   b.j[0] = one_job(frames, nf, H, W, g, R, td, isf, nullptr);
+  b.j[0].err = err;
   if (!motion_batch_finalize(b)) return cudaErrorInvalidValue;
   return launch_stats_multi(b, st, list, list_n);
 }

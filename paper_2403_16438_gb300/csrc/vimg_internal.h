@@ -82,6 +82,7 @@ struct MotionJob {
   float* shifts;              // [nf][2] or null
   float* info;                // [nf][4] or null
   double* surface;            // [nf][w*w] or null
+  int* err;                   // sticky device error flag of bounded waits, or null
   PatchGrid g;
   int nf, H, W, R;
 };
@@ -155,9 +156,12 @@ cudaError_t launch_template_prep(const float* T, int H, int W, PatchGrid g, Temp
                                  cudaStream_t st);
 size_t stats_map_floats(PatchGrid g, int R);  // per frame
 // list/list_n (device): only the listed frames (count read on the device).
+// err (device, may be null): the flag a bounded wait that gave up sets; without
+// it the statistics run on the kernel that stages with plain loads.
 cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                          const TemplateDev& td, float* isf, cudaStream_t st,
-                         const int* list = nullptr, const int* list_n = nullptr);
+                         const int* list = nullptr, const int* list_n = nullptr,
+                         int* err = nullptr);
 // Only the isf entries of the narrow windows around the proposals.
 cudaError_t launch_stats_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                                 const float* prop, float* isf, cudaStream_t st);
