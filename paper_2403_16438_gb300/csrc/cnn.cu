@@ -116,18 +116,37 @@ __global__ void __launch_bounds__(kThreads)
   float2 acc[NC / 2];
 #pragma unroll
   for (int c = 0; c < NC / 2; ++c) acc[c] = make_float2(bias[g * NC + 2 * c], bias[g * NC + 2 * c + 1]);
+  // the nine taps of the next input channel are loaded before the current
+  // channel's FMAs (taps outside the image are skipped, as before)
+  bool vy[3], vx[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int iy = oy * S + k - 1, ix = ox * S + k - 1;
+    vy[k] = iy >= 0 && iy < HI;
+    vx[k] = ix >= 0 && ix < HI;
+  }
+  const float* ip0 = in + (size_t)b * CIN * HI * HI + (oy * S - 1) * HI + (ox * S - 1);
+  auto load_taps = [&](int ci, float (&v)[9]) {
+    const float* ip = ip0 + (size_t)ci * HI * HI;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+        v[ky * 3 + kx] = vy[ky] && vx[kx] ? __ldg(ip + ky * HI + kx) : 0.f;
+  };
+  float vin[9];
+  load_taps(0, vin);
+#pragma unroll 2
   for (int ci = 0; ci < CIN; ++ci) {
-    const float* ip = in + ((size_t)b * CIN + ci) * HI * HI;
+    float vnext[9];
+    if (ci + 1 < CIN) load_taps(ci + 1, vnext);
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky) {
-      const int iy = oy * S + ky - 1;
-      if (iy < 0 || iy >= HI) continue;
+      if (!vy[ky]) continue;
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx) {
-        const int ix = ox * S + kx - 1;
-        if (ix < 0 || ix >= HI) continue;
-        const float v = __ldg(ip + iy * HI + ix);
-        const float2 vv = make_float2(v, v);
+        if (!vx[kx]) continue;
+        const float2 vv = make_float2(vin[ky * 3 + kx], vin[ky * 3 + kx]);
         const float4* wr = reinterpret_cast<const float4*>(&ws[ci * 9 + ky * 3 + kx][g * NC]);
 #pragma unroll
         for (int q = 0; q < NC / 4; ++q) {
@@ -137,6 +156,8 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
     }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vin[k] = vnext[k];
   }
   float* op = out + ((size_t)b * kC + g * NC) * HO * HO + oy * HO + ox;
 #pragma unroll
@@ -146,28 +167,106 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// ---- global average pool + linear ------------------------------------------------
-__global__ void k_gap_lin_fwd(const float* __restrict__ a6, const float* __restrict__ lw,
-                              const float* __restrict__ lb, float* __restrict__ gap,
-                              float* __restrict__ out, int n) {
-  const int b = blockIdx.x * blockDim.y + threadIdx.y;
-  const int c = threadIdx.x;  // 32 lanes = channels
-  if (b >= n) return;
-  const float* p = a6 + ((size_t)b * kC + c) * 16;
-  float s = 0.f;
+// ---- fused tail: conv4, conv5, conv6 (+ ReLU), global average pool, linear ---------
+// One CTA per sample.  The layers' inputs stay in shared memory (the 16x16x32
+// output of conv3 is read once); every output channel is the FMA chain of
+// k_conv_fwd (bias, then input channels, rows, columns in order, taps outside
+// the image skipped), the pool sums the 16 positions in order and scales by
+// 1/16, and the linear layer sums its 32 products by a fixed butterfly.  The
+// activations the backward pass reads (a4, a5, a6, the pooled vector) are
+// written as well.
+constexpr int kTailIn = kC * 16 * 16;  // conv4 input
+constexpr size_t kTailSmem =
+    sizeof(float) * ((size_t)kTailIn + kC * 9 * kC + kC * 8 * 8 + 2 * kC * 4 * 4);
+
+template <int HI, int S>
+__device__ __forceinline__ void tail_conv(const float* __restrict__ x, const float (*ws)[kC],
+                                          const float* __restrict__ bias, float* __restrict__ y,
+                                          float* __restrict__ yg) {
+  constexpr int HO = HI / S, NPIX = HO * HO, NC = kC * NPIX / kThreads;  // channels per thread
+  const int pix = threadIdx.x % NPIX, g = threadIdx.x / NPIX;
+  const int oy = pix / HO, ox = pix - oy * HO;
+  float acc[NC];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) s += p[i];
-  s *= (1.0f / 16.0f);
-  gap[(size_t)b * kC + c] = s;
-  float o0 = lw[c] * s, o1 = lw[kC + c] * s;
+  for (int c = 0; c < NC; ++c) acc[c] = bias[g * NC + c];
+  for (int ci = 0; ci < kC; ++ci) {
+    const float* ip = x + ci * HI * HI;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    o0 += __shfl_xor_sync(0xffffffffu, o0, off);
-    o1 += __shfl_xor_sync(0xffffffffu, o1, off);
+    for (int ky = 0; ky < 3; ++ky) {
+      const int iy = oy * S + ky - 1;
+      if (iy < 0 || iy >= HI) continue;
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int ix = ox * S + kx - 1;
+        if (ix < 0 || ix >= HI) continue;
+        const float v = ip[iy * HI + ix];
+        const float* wr = &ws[ci * 9 + ky * 3 + kx][g * NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fmaf(wr[c], v, acc[c]);
+      }
+    }
   }
-  if (c == 0) {
-    out[2 * b] = o0 + lb[0];
-    out[2 * b + 1] = o1 + lb[1];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const float r = fmaxf(acc[c], 0.f);
+    y[(g * NC + c) * NPIX + pix] = r;
+    yg[(g * NC + c) * NPIX + pix] = r;
+  }
+}
+
+__device__ __forceinline__ void tail_weights(const __nv_bfloat16* __restrict__ w, float (*ws)[kC]) {
+  for (int i = threadIdx.x; i < kC * 9 * kC; i += kThreads) {
+    const int co = i / (kC * 9), r = i - co * (kC * 9);
+    ws[r][co] = __bfloat162float(w[i]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_cnn_tail(const float* __restrict__ a3, const float* __restrict__ params,
+               const __nv_bfloat16* __restrict__ wb, float* __restrict__ a4,
+               float* __restrict__ a5, float* __restrict__ a6, float* __restrict__ gap,
+               float* __restrict__ out) {
+  extern __shared__ __align__(16) float tsm[];
+  float* x = tsm;                                                  // [32][16][16]
+  float(*ws)[kC] = reinterpret_cast<float(*)[kC]>(x + kTailIn);    // [288][32]
+  float* y4 = x + kTailIn + kC * 9 * kC;                           // [32][8][8]
+  float* y5 = y4 + kC * 8 * 8;                                     // [32][4][4]
+  float* y6 = y5 + kC * 4 * 4;                                     // [32][4][4]
+  const int b = blockIdx.x;
+  const float4* src = reinterpret_cast<const float4*>(a3 + (size_t)b * kTailIn);
+  for (int i = threadIdx.x; i < kTailIn / 4; i += kThreads)
+    reinterpret_cast<float4*>(x)[i] = __ldg(src + i);
+  tail_weights(wb + w_off(3), ws);
+  __syncthreads();
+  tail_conv<16, 2>(x, ws, params + w_off(3) + w_count(3), y4, a4 + (size_t)b * kC * 64);
+  __syncthreads();
+  tail_weights(wb + w_off(4), ws);
+  __syncthreads();
+  tail_conv<8, 2>(y4, ws, params + w_off(4) + w_count(4), y5, a5 + (size_t)b * kC * 16);
+  __syncthreads();
+  tail_weights(wb + w_off(5), ws);
+  __syncthreads();
+  tail_conv<4, 1>(y5, ws, params + w_off(5) + w_count(5), y6, a6 + (size_t)b * kC * 16);
+  __syncthreads();
+  if (threadIdx.x < 32) {  // pool and linear: lane = channel
+    const int c = threadIdx.x;
+    const float* lw = params + kLinOff;
+    const float* pp = y6 + c * 16;
+    float sv = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sv += pp[i];
+    sv *= (1.0f / 16.0f);
+    gap[(size_t)b * kC + c] = sv;
+    float o0 = lw[c] * sv, o1 = lw[kC + c] * sv;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      o0 += __shfl_xor_sync(0xffffffffu, o0, off);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, off);
+    }
+    if (c == 0) {
+      out[2 * b] = o0 + params[kLinOff + 2 * kC];
+      out[2 * b + 1] = o1 + params[kLinOff + 2 * kC + 1];
+    }
   }
 }
 
@@ -373,8 +472,9 @@ size_t cnn_act_floats(int n) { return act_off(kLayers + 1, n) + (size_t)(kC + 2)
 // of cnn_act_floats(n) floats whose first part holds the input; out [n][2].
 cudaError_t cnn_forward(const float* params, const __nv_bfloat16* wb, float* acts, int n,
                         float* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+  for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
     const float* in = acts + act_off(l, n);
     float* o = acts + act_off(l + 1, n);
     const __nv_bfloat16* w = wb + w_off(l);
@@ -383,16 +483,19 @@ cudaError_t cnn_forward(const float* params, const __nv_bfloat16* wb, float* act
     // output channel groups per layer: more threads where there are few pixels
     if (l == 0) e = conv_fwd<2, 2, 1>(in, w, b, o, n, HI, HO, st);
     else if (l == 1) e = conv_fwd<32, 2, 1>(in, w, b, o, n, HI, HO, st);
-    else if (l == 2) e = conv_fwd<32, 2, 2>(in, w, b, o, n, HI, HO, st);
-    else if (l == 3) e = conv_fwd<32, 2, 4>(in, w, b, o, n, HI, HO, st);
-    else if (l == 4) e = conv_fwd<32, 2, 8>(in, w, b, o, n, HI, HO, st);
-    else e = conv_fwd<32, 1, 8>(in, w, b, o, n, HI, HO, st);
+    else e = conv_fwd<32, 2, 2>(in, w, b, o, n, HI, HO, st);
   }
   if (e != cudaSuccess) return e;
-  float* gap = acts + act_off(kLayers + 1, n);
-  dim3 blk(32, 8);
-  k_gap_lin_fwd<<<(n + 7) / 8, blk, 0, st>>>(acts + act_off(kLayers, n), params + kLinOff,
-                                              params + kLinOff + 2 * kC, gap, out, n);
+  // conv4..conv6, pool and linear in one kernel per sample
+  static unsigned char attr[kMaxDevices] = {};
+  e = once_per_device(attr, [](int) {
+    return cudaFuncSetAttribute(k_cnn_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTailSmem);
+  });
+  if (e != cudaSuccess) return e;
+  k_cnn_tail<<<n, kThreads, kTailSmem, st>>>(
+      acts + act_off(3, n), params, wb, acts + act_off(4, n), acts + act_off(5, n),
+      acts + act_off(6, n), acts + act_off(kLayers + 1, n), out);
   return cudaGetLastError();
 }
 
