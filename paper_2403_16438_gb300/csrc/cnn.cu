@@ -94,77 +94,102 @@ __global__ void k_cnn_input(const uint16_t* __restrict__ frames, int H, int W,
 
 // ---- conv 3x3 forward + ReLU: thread per (output pixel, group of kC / COG channels)
 // The deep layers have few pixels, so they split the output channels over COG
-// threads to keep enough warps in flight.  Pairs of channels accumulate with the
-// packed FP32 FMA (two independent round-to-nearest FMAs, the same results as
-// scalar fmaf).
-template <int CIN, int S, int COG>
-__global__ void __launch_bounds__(kThreads)
+// threads to keep enough warps in flight; the large layers give a thread PX
+// adjacent output pixels of a row, which share each tap's weight loads.  Pairs
+// of channels accumulate with the packed FP32 FMA (two independent
+// round-to-nearest FMAs, the same results as scalar fmaf); every output sums
+// its taps in the same order (input channels, rows, columns; taps outside the
+// image skipped) whatever COG and PX.
+template <int CIN, int S, int COG, int PX>
+__global__ void __launch_bounds__(kThreads, 2)
     k_conv_fwd(const float* __restrict__ in, const __nv_bfloat16* __restrict__ w,
                const float* __restrict__ bias, float* __restrict__ out, int n, int HI, int HO) {
-  constexpr int NC = kC / COG;  // output channels per thread (multiple of 4)
+  constexpr int NC = kC / COG;          // output channels per thread (multiple of 4)
+  constexpr int NXC = S * (PX - 1) + 3;  // input columns the PX pixels' taps read
   __shared__ __align__(16) float ws[CIN * 9][kC];
   for (int i = threadIdx.x; i < CIN * 9 * kC; i += kThreads) {
     const int co = i / (CIN * 9), r = i - co * (CIN * 9);
     ws[r][co] = __bfloat162float(w[i]);
   }
   __syncthreads();
-  const int npix = n * HO * HO;
+  const int hox = HO / PX;  // pixel groups per output row
+  const int npg = n * HO * hox;
   const int t = blockIdx.x * kThreads + threadIdx.x;
-  if (t >= npix * COG) return;
-  const int g = t / npix, pix = t - g * npix;
-  const int b = pix / (HO * HO), rem = pix - b * HO * HO, oy = rem / HO, ox = rem - oy * HO;
-  float2 acc[NC / 2];
+  if (t >= npg * COG) return;
+  const int g = t / npg, pg = t - g * npg;
+  const int b = pg / (HO * hox), rem = pg - b * HO * hox, oy = rem / hox;
+  const int ox0 = (rem - oy * hox) * PX;
+  float2 acc[PX][NC / 2];
 #pragma unroll
-  for (int c = 0; c < NC / 2; ++c) acc[c] = make_float2(bias[g * NC + 2 * c], bias[g * NC + 2 * c + 1]);
-  // the nine taps of the next input channel are loaded before the current
-  // channel's FMAs (taps outside the image are skipped, as before)
-  bool vy[3], vx[3];
+  for (int k = 0; k < PX; ++k)
+#pragma unroll
+    for (int c = 0; c < NC / 2; ++c)
+      acc[k][c] = make_float2(bias[g * NC + 2 * c], bias[g * NC + 2 * c + 1]);
+  // the taps of the next input channel are loaded before the current channel's FMAs
+  bool vy[3], vx[NXC];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int iy = oy * S + k - 1, ix = ox * S + k - 1;
+    const int iy = oy * S + k - 1;
     vy[k] = iy >= 0 && iy < HI;
-    vx[k] = ix >= 0 && ix < HI;
   }
-  const float* ip0 = in + (size_t)b * CIN * HI * HI + (oy * S - 1) * HI + (ox * S - 1);
-  auto load_taps = [&](int ci, float (&v)[9]) {
+#pragma unroll
+  for (int j = 0; j < NXC; ++j) {
+    const int ix = ox0 * S + j - 1;
+    vx[j] = ix >= 0 && ix < HI;
+  }
+  const float* ip0 = in + (size_t)b * CIN * HI * HI + (oy * S - 1) * HI + (ox0 * S - 1);
+  auto load_taps = [&](int ci, float (&v)[3][NXC]) {
     const float* ip = ip0 + (size_t)ci * HI * HI;
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-      for (int kx = 0; kx < 3; ++kx)
-        v[ky * 3 + kx] = vy[ky] && vx[kx] ? __ldg(ip + ky * HI + kx) : 0.f;
+      for (int j = 0; j < NXC; ++j) v[ky][j] = vy[ky] && vx[j] ? __ldg(ip + ky * HI + j) : 0.f;
   };
-  float vin[9];
+  // (one pixel per thread: the next channel's taps are loaded ahead; several
+  // pixels per thread give the FMAs enough independent work without it)
+  constexpr bool kAhead = PX == 1;
+  float vin[3][NXC];
   load_taps(0, vin);
-#pragma unroll 2
+#pragma unroll(kAhead ? 2 : 1)
   for (int ci = 0; ci < CIN; ++ci) {
-    float vnext[9];
-    if (ci + 1 < CIN) load_taps(ci + 1, vnext);
+    float vnext[3][NXC];
+    if (!kAhead && ci > 0) load_taps(ci, vin);
+    if (kAhead && ci + 1 < CIN) load_taps(ci + 1, vnext);
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky) {
       if (!vy[ky]) continue;
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx) {
-        if (!vx[kx]) continue;
-        const float2 vv = make_float2(vin[ky * 3 + kx], vin[ky * 3 + kx]);
         const float4* wr = reinterpret_cast<const float4*>(&ws[ci * 9 + ky * 3 + kx][g * NC]);
 #pragma unroll
         for (int q = 0; q < NC / 4; ++q) {
           const float4 wv = wr[q];
-          acc[2 * q] = __ffma2_rn(make_float2(wv.x, wv.y), vv, acc[2 * q]);
-          acc[2 * q + 1] = __ffma2_rn(make_float2(wv.z, wv.w), vv, acc[2 * q + 1]);
+#pragma unroll
+          for (int k = 0; k < PX; ++k) {
+            const int j = kx + S * k;
+            if (!vx[j]) continue;
+            const float2 vv = make_float2(vin[ky][j], vin[ky][j]);
+            acc[k][2 * q] = __ffma2_rn(make_float2(wv.x, wv.y), vv, acc[k][2 * q]);
+            acc[k][2 * q + 1] = __ffma2_rn(make_float2(wv.z, wv.w), vv, acc[k][2 * q + 1]);
+          }
         }
       }
     }
+    if (kAhead) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) vin[k] = vnext[k];
-  }
-  float* op = out + ((size_t)b * kC + g * NC) * HO * HO + oy * HO + ox;
+      for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-  for (int c = 0; c < NC / 2; ++c) {
-    op[(size_t)(2 * c) * HO * HO] = fmaxf(acc[c].x, 0.f);
-    op[(size_t)(2 * c + 1) * HO * HO] = fmaxf(acc[c].y, 0.f);
+        for (int j = 0; j < NXC; ++j) vin[ky][j] = vnext[ky][j];
+    }
   }
+  float* op = out + ((size_t)b * kC + g * NC) * HO * HO + oy * HO + ox0;
+#pragma unroll
+  for (int c = 0; c < NC / 2; ++c)
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      op[(size_t)(2 * c) * HO * HO + k] = fmaxf(acc[k][c].x, 0.f);
+      op[(size_t)(2 * c + 1) * HO * HO + k] = fmaxf(acc[k][c].y, 0.f);
+    }
 }
 
 // ---- fused tail: conv4, conv5, conv6 (+ ReLU), global average pool, linear ---------
@@ -454,11 +479,11 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
 
 inline int blocks(size_t count) { return (int)((count + kThreads - 1) / kThreads); }
 
-template <int CIN, int S, int COG>
+template <int CIN, int S, int COG, int PX>
 cudaError_t conv_fwd(const float* in, const __nv_bfloat16* w, const float* b, float* out, int n,
                      int HI, int HO, cudaStream_t st) {
-  k_conv_fwd<CIN, S, COG><<<blocks((size_t)n * HO * HO * COG), kThreads, 0, st>>>(in, w, b, out, n,
-                                                                                 HI, HO);
+  k_conv_fwd<CIN, S, COG, PX><<<blocks((size_t)n * HO * (HO / PX) * COG), kThreads, 0, st>>>(
+      in, w, b, out, n, HI, HO);
   return cudaGetLastError();
 }
 
@@ -481,9 +506,9 @@ cudaError_t cnn_forward(const float* params, const __nv_bfloat16* wb, float* act
     const float* b = params + w_off(l) + w_count(l);
     const int HI = kSide[l], HO = kSide[l + 1];
     // output channel groups per layer: more threads where there are few pixels
-    if (l == 0) e = conv_fwd<2, 2, 1>(in, w, b, o, n, HI, HO, st);
-    else if (l == 1) e = conv_fwd<32, 2, 1>(in, w, b, o, n, HI, HO, st);
-    else e = conv_fwd<32, 2, 2>(in, w, b, o, n, HI, HO, st);
+    if (l == 0) e = conv_fwd<2, 2, 1, 1>(in, w, b, o, n, HI, HO, st);
+    else if (l == 1) e = conv_fwd<32, 2, 1, 2>(in, w, b, o, n, HI, HO, st);
+    else e = conv_fwd<32, 2, 2, 2>(in, w, b, o, n, HI, HO, st);
   }
   if (e != cudaSuccess) return e;
   // conv4..conv6, pool and linear in one kernel per sample
