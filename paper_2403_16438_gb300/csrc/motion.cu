@@ -848,7 +848,11 @@ cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, f
 // read-only cache.  Same normalisation and fixed-point sums as the full window.
 constexpr int kNarrow = kNarrowWin;  // 7
 constexpr int kNarrowGroup = 24;     // patches per CTA (one patch row, or part of it)
-constexpr int kNarrowStride = kNarrowGroup * kPatch + kNarrow;  // staged row stride (floats)
+// staged row stride (floats): at least 24 x 21 + 6, and = 4 (mod 32) so that the
+// 32 lanes of a warp (4 patches 21 words apart x 8 rows) read distinct banks
+constexpr int kNarrowStride = ((kNarrowGroup * kPatch + kNarrow - 1 - 4 + 31) & ~31) + 4;
+static_assert(kNarrowStride % 32 == 4 && kNarrowStride >= kNarrowGroup * kPatch + kNarrow - 1,
+              "narrow region stride");
 
 __device__ __forceinline__ void narrow_center(const float* prop, int f, int R, int& cy, int& cx) {
   // prop holds the network output (shift / kShiftScale)
