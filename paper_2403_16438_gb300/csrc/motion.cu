@@ -843,9 +843,10 @@ cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, f
 // ---------------------------------------------------------------------------
 // Narrow window around a proposed shift p_t (learned proposal): the 7x7
 // displacements centred on c_t = round(p_t) (clamped so the window stays in
-// [-R, R]^2), i.e. +-2 px plus a one-pixel ring for the refinement.  CTA = 16
-// patches x 8 lanes (lane = displacement row), the frame read through the
-// read-only cache.  Same normalisation and fixed-point sums as the full window.
+// [-R, R]^2), i.e. +-2 px plus a one-pixel ring for the refinement.  CTA = 24
+// patches x 8 lanes (lane = displacement row), the union of the group's 27-row
+// regions staged in shared memory.  Same normalisation and fixed-point sums as
+// the full window.
 constexpr int kNarrow = kNarrowWin;  // 7
 constexpr int kNarrowGroup = 24;     // patches per CTA (one patch row, or part of it)
 // staged row stride (floats): at least 24 x 21 + 6, and = 4 (mod 32) so that the
