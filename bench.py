@@ -823,7 +823,11 @@ def run_batched(args, stream, dev, ws):
     total = sum(f.shape[0] for f in frames)
     px = sum(f.numel() for f in frames)
     maxc = 512
-    hs = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=maxc) for f in frames]
+    # tile shape: the correlation's patch group per video, timed on a probe
+    groups, group_table = autotune.tune_groups(frames, [T for _, T in vids], probe_frames=200,
+                                               stream=stream)
+    hs = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=maxc, corr_group=g)
+          for f, g in zip(frames, groups)]
     for h, (_, T) in zip(hs, vids):
         h.set_template(T)
     shifts = [torch.empty((f.shape[0], 2), device=dev) for f in frames]
@@ -861,25 +865,32 @@ def run_batched(args, stream, dev, ws):
     ref_shifts = [x.clone() for x in shifts]
     for h in hs:
         h.close()
-    # the plain per-video path: each video on its own, 500-frame calls, same rings
-    plain = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=args.chunk)
-             for f in frames]
-    for h, (_, T) in zip(plain, vids):
-        h.set_template(T)
+    # the plain per-video path: each video on its own, 500-frame calls, same rings;
+    # with the default patch group (the path as a user runs it) and with the
+    # batched form's groups (the same arithmetic: shifts identical)
+    def sequential_run(group_of):
+        plain = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=args.chunk,
+                             corr_group=group_of(i)) for i, f in enumerate(frames)]
+        for h, (_, T) in zip(plain, vids):
+            h.set_template(T)
 
-    def sequential():
-        for h, f, sh, r, m in zip(plain, frames, shifts, rings, summ):
-            h.reset()
-            k = 0
-            for i, t in enumerate(range(0, f.shape[0], 500)):
-                c = f[t:t + 500]
-                k += h.process(c, shifts=sh[t:t + 500], corrected=r[(i % 2) * 500:],
-                               summary=m[k:])
+        def sequential():
+            for h, f, sh, r, m in zip(plain, frames, shifts, rings, summ):
+                h.reset()
+                k = 0
+                for i, t in enumerate(range(0, f.shape[0], 500)):
+                    c = f[t:t + 500]
+                    k += h.process(c, shifts=sh[t:t + 500], corrected=r[(i % 2) * 500:],
+                                   summary=m[k:])
 
-    ms_p = timed(sequential, steps, 1)
+        ms = timed(sequential, steps, 1)
+        for h in plain:
+            h.close()
+        return ms
+
+    ms_pt = sequential_run(lambda i: groups[i])
     same = all(torch.equal(a, b) for a, b in zip(ref_shifts, shifts))
-    for h in plain:
-        h.close()
+    ms_p = sequential_run(lambda i: 0)
     value = total / (ms_b / 1000.0)
     del vids, frames, rings, summ
     torch.cuda.empty_cache()
@@ -891,8 +902,13 @@ def run_batched(args, stream, dev, ws):
         "plain_per_video_value": total / (ms_p / 1000.0),
         "plain_per_video_ms_per_step": ms_p,
         "speedup_vs_plain": ms_p / ms_b,
-        "shifts_identical_to_plain": same,
-        "autotune": {"choice": {"chunk": chunk, "use_graph": graph},
+        "plain_same_groups_value": total / (ms_pt / 1000.0),
+        "speedup_vs_plain_same_groups": ms_pt / ms_b,
+        "shifts_identical_to_plain_same_groups": same,
+        "autotune": {"choice": {"chunk": chunk, "use_graph": graph, "corr_group": groups},
+                     "corr_group_seconds_on_200_frames": {
+                         f"{BATCH_VIDEOS[i][0]}x{BATCH_VIDEOS[i][1]}": {str(g): t for g, t in tg.items()}
+                         for i, tg in group_table.items()},
                      "probe_frames_per_video": probe,
                      "seconds": {f"{c}/{'graph' if g else 'direct'}": t
                                  for (c, g), t in table.items()}},

@@ -90,11 +90,15 @@ typedef struct {
   void* stream;             /* cudaStream_t for all work; NULL = default stream  */
   long long timeout_spins;  /* cap on any device-side wait loop                  */
   int max_chunk;            /* frames per internal batch (workspace sizing)      */
+  int corr_group;           /* patches per work item of the FP32 correlation:
+                               0 = 11 (fills 22-patch rows, 512 px); 7, 8, 10
+                               or 11 (e.g. 7 for 35-patch rows, 768 px).  Only
+                               the rounding of the FP32 sums depends on it      */
 } vimg_params;
 
 /* Fills *p with the defaults above (R = 16, patch 21, L = 50, sigma 3,
  * high-pass off, no flags, fallback 0.5, narrow radius 2, default stream,
- * max_chunk 200). */
+ * max_chunk 200, corr_group 0 = 11). */
 void vimg_default_params(vimg_params* p);
 
 /* Creates a handle for H x W frames on the current CUDA device and allocates

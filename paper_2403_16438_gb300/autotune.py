@@ -5,10 +5,18 @@ The batched call (vimg_process_batch) advances all videos together in steps of
 per window-statistics, correlation, peak and temporal launch), so it sets how
 full the GPU is at the end of each launch, how much of a step's frames are
 still in L2 when the temporal pass re-reads them, and how many launches the
-whole call makes.  The spatial tiles of the kernels are fixed by their
-shared-memory budgets.  Candidates are the chunk sizes {64, 128, 256, 512}
+whole call makes.  Candidates are the chunk sizes {64, 128, 256, 512}
 (shortened by the library to end on segment boundaries), each with and
 without CUDA-graph replay.
+
+The one spatial tile shape with a choice is the FP32 correlation's patch group
+(vimg_params.corr_group: patches per work item, 11, 10, 8 or 7): a row of nx
+patches takes ceil(nx / g) items, so the best g depends on the frame width (22
+patches per row fill groups of 11, 35 fill groups of 7), while smaller groups
+spend more of each item on its shared region and its 33rd-row warp.
+`tune_groups` times the correlation stage of every video with every group size
+on a probe and picks the fastest per video; the other kernels' tiles are fixed
+by their shared-memory and tensor-memory budgets.
 
 `tune` is the pure selection (any `run(candidate) -> seconds`); `tune_batch`
 times candidates on the device with CUDA events on a probe prefix of the
@@ -20,6 +28,7 @@ import json
 import os
 
 CHUNKS = (64, 128, 256, 512)
+GROUPS = (11, 10, 8, 7)
 
 
 def candidates(max_chunk: int, chunks=CHUNKS, graphs=(False, True)):
@@ -119,3 +128,46 @@ def tune_batch(handles, frames, probe_frames: int = 500, reps: int = 2, chunks=C
     if cache_path:
         store(cache_path, key, choice, table)
     return choice, table
+
+
+def pick_group(timings: dict) -> int:
+    """Fastest group size; ties go to the larger group."""
+    if not timings:
+        raise ValueError("no timings")
+    return min(timings, key=lambda g: (timings[g], -g))
+
+
+def tune_groups(frames, templates, probe_frames: int = 200, groups=GROUPS, reps: int = 2,
+                stream=None):
+    """Per video, the correlation group size whose correlation stage (CUDA
+    events around its launches, vimg_profile_*) is fastest on the first
+    `probe_frames` frames.  frames: list of cuda uint16 [n, H, W]; templates:
+    list of cuda float32 [H, W].  Returns (groups per video, {video: {g: s}})."""
+    import torch
+
+    from . import vimg
+
+    chosen, table = [], {}
+    for i, (f, T) in enumerate(zip(frames, templates)):
+        probe = f[:min(probe_frames, f.shape[0])]
+        times = {}
+        for g in groups:
+            h = vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=probe.shape[0],
+                            corr_group=g)
+            h.set_template(T)
+            h.process(probe)  # warm-up
+            h.profile(True)
+            best = None
+            for _ in range(reps):
+                h.profile_read(reset=True)
+                h.reset()
+                h.process(probe)
+                ms = h.profile_read(reset=True)["corr"][0]
+                best = ms if best is None else min(best, ms)
+            h.profile(False)
+            torch.cuda.synchronize()
+            h.close()
+            times[g] = best / 1000.0
+        chosen.append(pick_group(times))
+        table[i] = times
+    return chosen, table

@@ -243,6 +243,10 @@ extern "C" vimg_handle* vimg_create(int H, int W, const vimg_params* pin) {
     fail(nullptr, VIMG_ERR_ARG, "max_chunk must be in 1..4096");
     return nullptr;
   }
+  if (!corr_group_valid(p.corr_group)) {
+    fail(nullptr, VIMG_ERR_ARG, "corr_group must be 0, 7, 8, 10 or 11");
+    return nullptr;
+  }
   if (p.flags & ~(VIMG_CORR_BF16 | VIMG_PROPOSAL_CNN | VIMG_OUT_HIGHPASS | VIMG_VIDEO_SUMMARY |
                   VIMG_TEMPORAL_SMEM)) {
     fail(nullptr, VIMG_ERR_ARG, "unknown flag bits");
@@ -526,7 +530,7 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
     prof_end(h, ps);
     ps = prof_begin(h, 1);
     CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st, h->fb_list,
-                       h->fb_n),
+                       h->fb_n, h->p.corr_group),
        "fallback correlation launch");
     prof_end(h, ps);
     ps = prof_begin(h, 2);
@@ -552,7 +556,8 @@ static int estimate(vimg_handle* h, const uint16_t* frames, int nf, float* shift
                         h->dev_err, h->st),
        "tensor-core correlation launch");
   } else {
-    CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st),
+    CK(launch_corr_f32(frames, nf, h->H, h->W, h->g, R, h->td, h->inv, h->csum, h->st, nullptr,
+                       nullptr, h->p.corr_group),
        "correlation launch");
   }
   prof_end(h, ps);
@@ -787,6 +792,7 @@ static int batch_body(const BatchCall& c, cudaStream_t st, std::vector<int>& seg
         J.R = hv->p.search_radius;
         J.tc = hv->td.tc, J.tn2 = hv->td.tn2, J.coff = hv->td.coff;
         J.isf = hv->inv, J.csum = hv->csum, J.shifts = sh_out[i], J.err = hv->dev_err;
+        J.cg = hv->p.corr_group;
         CK(cudaMemsetAsync(hv->csum, 0, sizeof(unsigned long long) * (size_t)m[v] * hv->nwin, st),
            "surface reset");
       }

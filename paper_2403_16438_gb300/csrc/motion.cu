@@ -463,24 +463,36 @@ cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid
 // each with its own shared buffers.  Group 1 starts once group 0 has staged its
 // first item, so from then on one group's staging (global-memory latency) runs
 // while the other group computes, and the SM's FMA pipes stay busy.
+//
+// The group size GP (patches per work item, 11 by default) is a template
+// parameter: a CTA holds two groups of GP + 1 warps.  A row of nx patches takes
+// ceil(nx / GP) items, so GP = 11 fills every group on 22-patch rows (512 px)
+// while 7 or 8 fit 35- or 47-patch rows (768 or 1,024 px) better; the per-item
+// arithmetic does not depend on GP except through the offset c of the item's
+// first patch (F - c is exact, so only the rounding of the FP32 sums moves).
 constexpr int kCsEntries = kMaxWin * kMaxWin + 1;  // keeps what follows 16-byte aligned
 constexpr int kRegionRows = kPatch + 2 * kMaxR;                     // 53
-constexpr int kRegionStride = (kGroup * kPatch + 2 * kMaxR) | 1;    // 263
-constexpr int kIsfCols = (kGroup - 1) * kPatch + kMaxWin;           // 243
-constexpr int kGroupWarps = kGroup + 1;
-constexpr int kGroupThreads = kGroupWarps * 32;                     // 384
-constexpr int kCorrThreads = 2 * kGroupThreads;                     // 768
 constexpr int kHalfRow = 17;  // columns per lane in the 33rd-row pass (0..16 or 16..32)
-constexpr size_t kGroupSmem = sizeof(unsigned long long) * kCsEntries +
-                              sizeof(float) * kMaxWin * kIsfCols +
-                              sizeof(float) * kRegionRows * kRegionStride;
+template <int GP>
+struct CorrGeom {
+  static_assert(GP >= 2 && GP <= 16, "the 33rd-row pass maps 16 patches x 2 column halves");
+  static constexpr int kWarps = GP + 1;                            // per group
+  static constexpr int kThreads = 32 * kWarps;                     // per group
+  static constexpr int kCta = 2 * kThreads;                        // two groups
+  static constexpr int kStride = (GP * kPatch + 2 * kMaxR) | 1;    // region row stride
+  static constexpr int kIsf = (GP - 1) * kPatch + kMaxWin;         // isf columns
+  static constexpr size_t kSmem =                                  // per group, 16-byte multiple
+      (sizeof(unsigned long long) * kCsEntries + sizeof(float) * kMaxWin * kIsf +
+       sizeof(float) * kRegionRows * kStride + 15) & ~(size_t)15;
+};
 
 // floor(i / d) as a multiply-high by m = ceil(2^32 / d): exact for i < 2^32 / d,
 // far above any index here (d <= 263, i < 14,000).
 __device__ __forceinline__ unsigned fast_div(unsigned i, unsigned m) { return __umulhi(i, m); }
 
+template <int N>
 __device__ __forceinline__ void group_sync(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kGroupThreads) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(N) : "memory");
 }
 
 template <int NX>
@@ -508,26 +520,27 @@ __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
   }
 }
 
-template <int NX>
-__global__ void __launch_bounds__(kCorrThreads, 1)
+template <int NX, int GP>
+__global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
     k_corr_f32(const __grid_constant__ MotionBatch b, const int* __restrict__ list,
                const int* __restrict__ list_n) {
+  using C = CorrGeom<GP>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int grp = threadIdx.x / kGroupThreads, gtid = threadIdx.x - grp * kGroupThreads;
+  const int grp = threadIdx.x / C::kThreads, gtid = threadIdx.x - grp * C::kThreads;
   const int lane = gtid & 31, gwarp = gtid >> 5;
-  unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem + grp * kGroupSmem);
+  unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem + grp * C::kSmem);
   float* ism = reinterpret_cast<float*>(cs + kCsEntries);  // [w][scols]
-  float* reg = ism + kMaxWin * kIsfCols;                   // [rows][rs]
+  float* reg = ism + kMaxWin * C::kIsf;                   // [rows][rs]
   // With a frame list (fallback frames of the learned proposal; one job) only the
   // listed frames are processed; their count is read from device memory.
   int n_items = b.corr_begin[b.n];
   if (list) {
     const PatchGrid g0 = b.j[0].g;
-    n_items = min(b.j[0].nf, *list_n) * g0.ny * ((g0.nx + kGroup - 1) / kGroup);
+    n_items = min(b.j[0].nf, *list_n) * g0.ny * ((g0.nx + GP - 1) / GP);
   }
   const int bar = 1 + grp;  // named barrier of this group (0 is __syncthreads)
 
-  if (grp == 1) asm volatile("bar.sync 3, %0;" ::"r"(kCorrThreads) : "memory");
+  if (grp == 1) asm volatile("bar.sync 3, %0;" ::"r"(C::kCta) : "memory");
   bool released = false;
   for (int k = grp;; k += 2) {
     const int item = blockIdx.x + k * gridDim.x;
@@ -537,7 +550,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
     const PatchGrid g = J.g;
     const int R = J.R, H = J.H, W = J.W;
     const int w = 2 * R + 1, rows = kPatch + 2 * R;
-    const int groups_per_row = (g.nx + kGroup - 1) / kGroup;
+    const int groups_per_row = (g.nx + GP - 1) / GP;
     const int items_per_frame = g.ny * groups_per_row;
     int oy, ox, sh, sw;
     stats_map_dims(g, R, &oy, &ox, &sh, &sw);
@@ -550,11 +563,11 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
     const float* __restrict__ isf = J.isf;
     unsigned long long* __restrict__ csum = J.csum;
     const int py = rem / groups_per_row, gx = rem - py * groups_per_row;
-    const int px0 = gx * kGroup, G = min(kGroup, g.nx - px0);
+    const int px0 = gx * GP, G = min(GP, g.nx - px0);
     const int cols = G * kPatch + 2 * R;
     // Rows are allocated for the widest window (a lane always reads 53 values) and
     // given an odd stride so that lanes on different rows hit distinct banks.
-    const int rs = (G * kPatch + 2 * kMaxR) | 1;  // <= kRegionStride
+    const int rs = (G * kPatch + 2 * kMaxR) | 1;  // <= C::kStride
     const int scols = (G - 1) * kPatch + w;       // isf columns this item uses
     const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
     const int p0 = py * g.nx + px0;
@@ -562,11 +575,11 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
 
     // Stage: every thread first issues its global loads (one round trip per
     // batch), then converts and stores.
-    for (int i = gtid; i < w * w; i += kGroupThreads) cs[i] = 0ull;
+    for (int i = gtid; i < w * w; i += C::kThreads) cs[i] = 0ull;
     const float* isf_f = isf + (size_t)f * sh * sw + (size_t)(ry - oy) * sw + (rx - ox);
     const uint16_t* F = frames + (size_t)f * H * W + (size_t)ry * W + rx;
     {
-      constexpr int kRegLoads = (kRegionRows * kRegionStride + kGroupThreads - 1) / kGroupThreads;
+      constexpr int kRegLoads = (kRegionRows * C::kStride + C::kThreads - 1) / C::kThreads;
       constexpr int kBatches = 3;  // batches of loads keep the registers in budget
       constexpr int kHalf = (kRegLoads + kBatches - 1) / kBatches;
       const unsigned m = 0xffffffffu / (unsigned)rs + 1u;
@@ -575,20 +588,20 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
         unsigned short v[kHalf];
 #pragma unroll
         for (int q = 0; q < kHalf; ++q) {
-          const int i = gtid + (b * kHalf + q) * kGroupThreads;
+          const int i = gtid + (b * kHalf + q) * C::kThreads;
           const int r = (int)fast_div((unsigned)i, m), x = i - r * rs;
           v[q] = (i < rows * rs && x < cols) ? __ldg(F + (size_t)r * W + x) : (unsigned short)0;
         }
 #pragma unroll
         for (int q = 0; q < kHalf; ++q) {
-          const int i = gtid + (b * kHalf + q) * kGroupThreads;
+          const int i = gtid + (b * kHalf + q) * C::kThreads;
           const int x = i - (int)fast_div((unsigned)i, m) * rs;
           if (i < rows * rs) reg[i] = x < cols ? (float)v[q] - c : 0.f;
         }
       }
     }
     {
-      constexpr int kIsfLoads = (kMaxWin * kIsfCols + kGroupThreads - 1) / kGroupThreads;
+      constexpr int kIsfLoads = (kMaxWin * C::kIsf + C::kThreads - 1) / C::kThreads;
       constexpr int kIsfHalf = (kIsfLoads + 1) / 2;
       const unsigned m = 0xffffffffu / (unsigned)scols + 1u;
 #pragma unroll 1
@@ -596,25 +609,25 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
         float v[kIsfHalf];
 #pragma unroll
         for (int q = 0; q < kIsfHalf; ++q) {
-          const int i = gtid + (b * kIsfHalf + q) * kGroupThreads;
+          const int i = gtid + (b * kIsfHalf + q) * C::kThreads;
           const int r = (int)fast_div((unsigned)i, m), x = i - r * scols;
           v[q] = i < w * scols ? __ldg(isf_f + (size_t)r * sw + x) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < kIsfHalf; ++q) {
-          const int i = gtid + (b * kIsfHalf + q) * kGroupThreads;
+          const int i = gtid + (b * kIsfHalf + q) * C::kThreads;
           if (i < w * scols) ism[i] = v[q];
         }
       }
     }
-    group_sync(bar);
+    group_sync<C::kThreads>(bar);
     if (grp == 0 && !released) {  // let group 1 start staging now
-      asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
+      asm volatile("bar.arrive 3, %0;" ::"r"(C::kCta) : "memory");
       released = true;
     }
     // One output-row pass per warp.
     const int n_pass = G + (w > 32 ? 1 : 0);
-    for (int pass = gwarp; pass < n_pass; pass += kGroupWarps) {
+    for (int pass = gwarp; pass < n_pass; pass += C::kWarps) {
       if (pass < G) {
         const int u = pass, dy = lane;
         const bool active = dy < w;
@@ -660,12 +673,12 @@ __global__ void __launch_bounds__(kCorrThreads, 1)
         }
       }
     }
-    group_sync(bar);
+    group_sync<C::kThreads>(bar);
     unsigned long long* out = csum + (size_t)f * w * w;
-    for (int i = gtid; i < w * w; i += kGroupThreads) atomicAdd(out + i, cs[i]);
-    group_sync(bar);
+    for (int i = gtid; i < w * w; i += C::kThreads) atomicAdd(out + i, cs[i]);
+    group_sync<C::kThreads>(bar);
   }
-  if (grp == 0 && !released) asm volatile("bar.arrive 3, %0;" ::"r"(kCorrThreads) : "memory");
+  if (grp == 0 && !released) asm volatile("bar.arrive 3, %0;" ::"r"(C::kCta) : "memory");
 }
 
 static int g_sms[kMaxDevices] = {};
@@ -683,36 +696,71 @@ int sm_count() {
   return e == cudaSuccess && dev >= 0 ? g_sms[dev] : 0;
 }
 
+template <int GP>
+static cudaError_t corr_attr() {
+  return cudaFuncSetAttribute(k_corr_f32<kMaxWin, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * CorrGeom<GP>::kSmem));
+}
+
 cudaError_t kernels_init() {
   return once_per_device(g_kernels_done, [](int) {
     if (sm_count() <= 0) return cudaErrorInvalidDevice;
-    cudaError_t e = cudaFuncSetAttribute(k_corr_f32<kMaxWin>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * kGroupSmem));
+    cudaError_t e = corr_attr<11>();
+    if (e == cudaSuccess) e = corr_attr<10>();
+    if (e == cudaSuccess) e = corr_attr<8>();
+    if (e == cudaSuccess) e = corr_attr<7>();
     if (e == cudaSuccess) e = temporal_init();
     return e;
   });
+}
+
+bool corr_group_valid(int cg) { return cg == 0 || cg == 7 || cg == 8 || cg == 10 || cg == 11; }
+
+// The jobs of b whose group size is GP, with their work items counted in
+// groups of GP patches, in one launch.
+template <int GP>
+static cudaError_t launch_corr_group(const MotionBatch& b, cudaStream_t st, const int* list,
+                                     const int* list_n) {
+  MotionBatch s{};
+  long long c = 0;
+  for (int i = 0; i < b.n; ++i) {
+    const MotionJob& J = b.j[i];
+    if ((J.cg ? J.cg : kGroup) != GP) continue;
+    s.j[s.n] = J;
+    c += (long long)J.nf * J.g.ny * ((J.g.nx + GP - 1) / GP);
+    if (c > INT_MAX) return cudaErrorInvalidValue;
+    s.corr_begin[++s.n] = (int)c;
+  }
+  if (s.n == 0 || c == 0) return cudaSuccess;
+  const int grid = std::min(sm_count(), (int)((c + 1) / 2));
+  k_corr_f32<kMaxWin, GP><<<grid, CorrGeom<GP>::kCta, 2 * CorrGeom<GP>::kSmem, st>>>(s, list,
+                                                                                      list_n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st, const int* list,
                                   const int* list_n) {
   const int items = b.corr_begin[b.n];
   if (items <= 0) return cudaSuccess;
+  for (int i = 0; i < b.n; ++i)
+    if (!corr_group_valid(b.j[i].cg)) return cudaErrorInvalidValue;
   cudaError_t e = kernels_init();
-  if (e != cudaSuccess) return e;
-  const int grid = std::min(sm_count(), (items + 1) / 2);
-  k_corr_f32<kMaxWin><<<grid, kCorrThreads, 2 * kGroupSmem, st>>>(b, list, list_n);
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = launch_corr_group<11>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<10>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<8>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<7>(b, st, list, list_n);
+  return e;
 }
 
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
                             unsigned long long* csum, cudaStream_t st, const int* list,
-                            const int* list_n) {
+                            const int* list_n, int cg) {
   if (nf <= 0) return cudaSuccess;
   MotionBatch b{};
   b.n = 1;
   b.j[0] = one_job(frames, nf, H, W, g, R, td, const_cast<float*>(isf), csum);
+  b.j[0].cg = cg;
   if (!motion_batch_finalize(b)) return cudaErrorInvalidValue;
   return launch_corr_f32_multi(b, st, list, list_n);
 }

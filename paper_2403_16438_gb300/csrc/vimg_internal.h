@@ -85,6 +85,7 @@ struct MotionJob {
   int* err;                   // sticky device error flag of bounded waits, or null
   PatchGrid g;
   int nf, H, W, R;
+  int cg;                     // patches per FP32 correlation item (0 = 11; 7, 8, 10, 11)
 };
 
 struct MotionBatch {
@@ -166,10 +167,13 @@ cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid
 cudaError_t launch_stats_narrow(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                                 const float* prop, float* isf, cudaStream_t st);
 // list/list_n (device): process only the listed frames (count read on the device).
+// cg: patches per work item of the FP32 correlation (0 = the default 11; 7, 8,
+// 10 or 11; corr_group_valid).
+bool corr_group_valid(int cg);
 cudaError_t launch_corr_f32(const uint16_t* frames, int nf, int H, int W, PatchGrid g, int R,
                             const TemplateDev& td, const float* isf,
                             unsigned long long* csum, cudaStream_t st,
-                            const int* list = nullptr, const int* list_n = nullptr);
+                            const int* list = nullptr, const int* list_n = nullptr, int cg = 0);
 cudaError_t launch_peak(const unsigned long long* csum, int nf, int R, int np, float* shifts,
                         float* peak_info, double* surface, cudaStream_t st,
                         const int* list = nullptr, const int* list_n = nullptr);

@@ -33,6 +33,7 @@ class Params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("timeout_spins", ctypes.c_longlong),
         ("max_chunk", ctypes.c_int),
+        ("corr_group", ctypes.c_int),
     ]
 
 

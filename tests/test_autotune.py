@@ -1,5 +1,7 @@
 """Host logic of the batched path's autotuner (no GPU): candidate set,
 selection, timing loop and the on-disk choice cache."""
+import pytest
+
 from paper_2403_16438_gb300 import autotune as at
 
 
@@ -39,3 +41,15 @@ def test_cache_roundtrip(tmp_path):
     assert at.load(p, k1) == (256, True)
     assert at.load(p, k2) == (128, False)
     assert at.load(p, "other") is None
+
+
+def test_pick_group_fastest_then_larger():
+    assert at.pick_group({11: 2.0, 10: 1.5, 8: 1.7, 7: 1.5}) == 10
+    assert at.pick_group({11: 1.0, 7: 1.0}) == 11
+    with pytest.raises(ValueError):
+        at.pick_group({})
+
+
+def test_group_candidates_are_the_library_sizes():
+    # the sizes the C ABI accepts for vimg_params.corr_group (besides 0 = 11)
+    assert set(at.GROUPS) == {11, 10, 8, 7}
