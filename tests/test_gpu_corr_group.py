@@ -101,3 +101,27 @@ def test_batch_with_mixed_group_sizes(vimg):
         assert torch.equal(sh, bsh.cpu()) and torch.equal(sm, bsm.cpu())
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("cg", [7, 11])
+def test_group_sizes_at_a_smaller_radius(vimg, cg):
+    """R = 8 (17 x 17 window, no 33rd-row pass; 20 patches per row: groups of 7
+    give 7, 7, 6) against the oracle, on a width whose statistics take the TMA
+    tiles."""
+    cfg = synth.scaled_config(80, 448, 10, seed=91)
+    frames, _, T = synth.make_video(cfg, 10)
+    o = oracle.Oracle(80, 448, R=8)
+    o.set_template(T.double().numpy())
+    ref = o.process(frames.numpy(), want_surface=True)
+    n, H, W = frames.shape
+    h = vimg.Handle(H, W, corr_group=cg, search_radius=8)
+    h.set_template(T.to(DEV))
+    sh = torch.zeros((n, 2), device=DEV)
+    info = torch.zeros((n, 4), device=DEV)
+    surf = torch.zeros((n, 17, 17), device=DEV, dtype=torch.float64)
+    h.process(frames.to(DEV), shifts=sh, peak_info=info, surface=surf)
+    torch.cuda.synchronize()
+    h.close()
+    assert np.abs(surf.cpu().numpy() - ref["surface"]).max() < 2e-6
+    near, _ = compare_shifts(sh.cpu().numpy(), info.cpu().numpy(), ref)
+    assert len(near) == 0
