@@ -186,8 +186,9 @@ int vimg_video_summary(vimg_handle* h, float* d_average, float* d_correlation);
 int vimg_process_io(vimg_handle* h, const uint16_t* d_frames, int n, const vimg_io* io);
 
 /* End-to-end variant with HOST buffers: h_frames host uint16 [n][H][W] is
- * streamed to the device in batches of max_chunk frames (uploads run up to two
- * batches ahead of the compute, into a ring of three device stages), and the
+ * streamed to the device in batches of max_chunk frames, the first a quarter of
+ * that (uploads run up to two batches ahead of the compute, into a ring of
+ * three device stages; only the first batch's upload is not overlapped), and the
  * shifts (host float32 [n][2]) and the summaries (host float32 [k][2][H][W])
  * are copied back on a stream of their own.  Host buffers should be pinned for
  * the copies to overlap the compute.  Either output

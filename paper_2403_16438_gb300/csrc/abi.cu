@@ -1012,8 +1012,11 @@ extern "C" int vimg_process_host(vimg_handle* h, const uint16_t* h_frames, int n
   // a slow copy in either direction stalls the compute only when the ring (or
   // the output pair) is exhausted.
   int done = 0, k_total = 0, buf = 0, ob = 0;
+  // the first batch is a quarter of max_chunk (whole segments): its upload is
+  // the only one no compute hides, and the next, full batch uploads behind it
+  const int first = std::max(L, (maxc / 4) / L * L);
   while (done < n) {
-    int m = std::min(n - done, maxc);
+    int m = std::min(n - done, done == 0 ? std::min(first, maxc) : maxc);
     if (m < n - done) {
       const int cut = (int)((h->frames_seen + m) % L);
       if (m - cut > 0) m -= cut;
