@@ -510,17 +510,24 @@ def run_vimg(args):
         torch.cuda.synchronize()
         h2d_gbs = fh.numel() * 2 / (time.perf_counter() - tc0) / 1e9
         barrier()
+        eclk = Clocks(local)
+        eclk.start()
+        step_ms = []
         t0 = time.perf_counter()
         for _ in range(ke):
+            ts = time.perf_counter()
             h.reset()
             h.process_host(fh, shifts_host=sh_h, summary_host=sm_h, corrected=corrected)
+            step_ms.append((time.perf_counter() - ts) * 1000.0)  # the call synchronises
         torch.cuda.synchronize()
         barrier()
         te = max_over_ranks(time.perf_counter() - t0, ws, dev)
+        e2e_clocks = eclk.stop()
         line["e2e"] = {"value": n * ke * ws / te, "unit": UNIT,
                        "h2d_bytes_per_step": n * H * W * 2,
                        "d2h_bytes_per_step": n * 2 * 4 + k_max * 2 * H * W * 4,
-                       "steps": ke, "h2d_GBs_measured": h2d_gbs,
+                       "steps": ke, "step_ms": step_ms, "clocks": e2e_clocks,
+                       "h2d_GBs_measured": h2d_gbs,
                        "host_cpus": (f"{min(local_cpus)}-{max(local_cpus)} ({len(local_cpus)} "
                                      "CPUs local to the GPU)") if local_cpus else "not pinned",
                        "note": "vimg_process_host: pinned host frames in, shifts and summaries "
