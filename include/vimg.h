@@ -227,6 +227,24 @@ int vimg_reset(vimg_handle* h);
  * short a history). */
 int vimg_seek(vimg_handle* h, long long t_start, const uint16_t* d_history, int n_history);
 
+/* Stream-state checkpoint and restore.  What carries over from one call to the
+ * next is the stream position, the frames of the open segment with their
+ * shifts (which also hold the high-pass history; Sec. III-B segments span
+ * calls), the whole-video summary sums (VIMG_VIDEO_SUMMARY) and the proposal
+ * counters.  vimg_state_bytes: size in bytes of the current state (it grows
+ * with the frames held for the open segment), or a negative VIMG_ERR_* code.
+ * vimg_get_state: waits for the handle's streams and writes the state to host
+ * memory `host` of `bytes` bytes (>= vimg_state_bytes; VIMG_ERR_ARG if
+ * smaller).  vimg_set_state: replaces the handle's state by one that
+ * vimg_get_state wrote on a handle of the same H, W, segment length,
+ * high-pass window, search radius and flags (VIMG_ERR_ARG otherwise, state
+ * unchanged); the template, proposal weights and ROIs are not part of it.
+ * After a restore the stream continues bit for bit as the checkpointed one
+ * would have.  Both return VIMG_OK or an error. */
+long long vimg_state_bytes(const vimg_handle* h);
+int vimg_get_state(vimg_handle* h, void* host, long long bytes);
+int vimg_set_state(vimg_handle* h, const void* host, long long bytes);
+
 /* Message for the last failure on h, or for the last failed vimg_create on
  * this host thread when h is NULL.  Never NULL. */
 const char* vimg_last_error(const vimg_handle* h);

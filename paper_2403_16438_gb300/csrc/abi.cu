@@ -356,6 +356,106 @@ extern "C" const char* vimg_last_error(const vimg_handle* h) {
 
 extern "C" long long vimg_frames_seen(const vimg_handle* h) { return h ? h->frames_seen : -1; }
 
+// Stream-state blob: this header, then the open segment's frames [carry_n][H][W]
+// (uint16) and shifts [carry_n][2] (float), then the whole-video sums [6][H][W]
+// (double) when the handle keeps them.
+struct StateHeader {
+  uint32_t magic, version;
+  int H, W, segment_len, hp_window, search_radius, flags;
+  long long frames_seen, vs_frames, prop_frames, fb_total;
+  int carry_n, has_vs;
+};
+constexpr uint32_t kStateMagic = 0x534d4956u;  // "VIMS"
+
+static long long state_size(const vimg_handle* h, int carry_n) {
+  const long long HW = (long long)h->H * h->W;
+  return (long long)sizeof(StateHeader) + carry_n * HW * 2 + carry_n * 2LL * 4 +
+         (h->vs_acc ? 6 * HW * 8 : 0);
+}
+
+extern "C" long long vimg_state_bytes(const vimg_handle* h) {
+  if (!h) return VIMG_ERR_ARG;
+  return state_size(h, h->carry_n);
+}
+
+extern "C" int vimg_get_state(vimg_handle* h, void* host, long long bytes) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  if (!host || bytes < state_size(h, h->carry_n))
+    return fail(h, VIMG_ERR_ARG, "vimg_get_state: buffer smaller than vimg_state_bytes");
+  CK(cudaStreamSynchronize(h->st), "stream sync");
+  if (h->copy_st) CK(cudaStreamSynchronize(h->copy_st), "stream sync");
+  if (h->dl_st) CK(cudaStreamSynchronize(h->dl_st), "stream sync");
+  StateHeader hd{};
+  hd.magic = kStateMagic, hd.version = 1;
+  hd.H = h->H, hd.W = h->W, hd.segment_len = h->p.segment_len, hd.hp_window = h->p.hp_window;
+  hd.search_radius = h->p.search_radius, hd.flags = h->p.flags;
+  hd.frames_seen = h->frames_seen, hd.vs_frames = h->vs_frames, hd.prop_frames = h->prop_frames;
+  hd.carry_n = h->carry_n, hd.has_vs = h->vs_acc ? 1 : 0;
+  if (h->fb_total)
+    CK(cudaMemcpy(&hd.fb_total, h->fb_total, sizeof(long long), cudaMemcpyDeviceToHost),
+       "state copy");
+  unsigned char* o = static_cast<unsigned char*>(host);
+  std::memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  const size_t HW = (size_t)h->H * h->W;
+  if (h->carry_n > 0) {
+    CK(cudaMemcpy(o, h->carry[h->carry_cur], sizeof(uint16_t) * HW * h->carry_n,
+                  cudaMemcpyDeviceToHost),
+       "state copy");
+    o += sizeof(uint16_t) * HW * h->carry_n;
+    CK(cudaMemcpy(o, h->carry_shift[h->carry_cur], sizeof(float) * 2 * h->carry_n,
+                  cudaMemcpyDeviceToHost),
+       "state copy");
+    o += sizeof(float) * 2 * h->carry_n;
+  }
+  if (h->vs_acc)
+    CK(cudaMemcpy(o, h->vs_acc, sizeof(double) * 6 * HW, cudaMemcpyDeviceToHost), "state copy");
+  return VIMG_OK;
+}
+
+extern "C" int vimg_set_state(vimg_handle* h, const void* host, long long bytes) {
+  if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
+  if (h->sticky) return h->sticky;
+  StateHeader hd{};
+  if (!host || bytes < (long long)sizeof(hd))
+    return fail(h, VIMG_ERR_ARG, "vimg_set_state: no state header");
+  std::memcpy(&hd, host, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != 1)
+    return fail(h, VIMG_ERR_ARG, "vimg_set_state: not a state written by vimg_get_state");
+  if (hd.H != h->H || hd.W != h->W || hd.segment_len != h->p.segment_len ||
+      hd.hp_window != h->p.hp_window || hd.search_radius != h->p.search_radius ||
+      hd.flags != h->p.flags || hd.has_vs != (h->vs_acc ? 1 : 0))
+    return fail(h, VIMG_ERR_ARG, "vimg_set_state: state of a handle with other parameters");
+  if (hd.carry_n < 0 || hd.carry_n > h->carry_cap || hd.frames_seen < hd.carry_n ||
+      bytes < state_size(h, hd.carry_n))
+    return fail(h, VIMG_ERR_ARG, "vimg_set_state: inconsistent or truncated state");
+  CK(cudaStreamSynchronize(h->st), "stream sync");
+  if (h->copy_st) CK(cudaStreamSynchronize(h->copy_st), "stream sync");
+  if (h->dl_st) CK(cudaStreamSynchronize(h->dl_st), "stream sync");
+  const unsigned char* in = static_cast<const unsigned char*>(host) + sizeof(hd);
+  const size_t HW = (size_t)h->H * h->W;
+  if (hd.carry_n > 0) {
+    CK(cudaMemcpy(h->carry[0], in, sizeof(uint16_t) * HW * hd.carry_n, cudaMemcpyHostToDevice),
+       "state copy");
+    in += sizeof(uint16_t) * HW * hd.carry_n;
+    CK(cudaMemcpy(h->carry_shift[0], in, sizeof(float) * 2 * hd.carry_n, cudaMemcpyHostToDevice),
+       "state copy");
+    in += sizeof(float) * 2 * hd.carry_n;
+  }
+  if (h->vs_acc)
+    CK(cudaMemcpy(h->vs_acc, in, sizeof(double) * 6 * HW, cudaMemcpyHostToDevice), "state copy");
+  if (h->fb_total)
+    CK(cudaMemcpy(h->fb_total, &hd.fb_total, sizeof(long long), cudaMemcpyHostToDevice),
+       "state copy");
+  h->carry_cur = 0;
+  h->carry_n = hd.carry_n;
+  h->frames_seen = hd.frames_seen;
+  h->vs_frames = hd.vs_frames;
+  h->prop_frames = hd.prop_frames;
+  return VIMG_OK;
+}
+
 extern "C" int vimg_reset(vimg_handle* h) {
   if (!h) return fail(h, VIMG_ERR_ARG, "null handle");
   if (h->sticky) return h->sticky;

@@ -74,6 +74,7 @@ EXPORTS = [
     "vimg_unet_profile", "vimg_unet_profile_read", "vimg_attach_unet", "vimg_unet_activation",
     "vimg_video_summary", "vimg_segmenter_create", "vimg_segmenter_destroy",
     "vimg_segmenter_last_error", "vimg_segment", "vimg_segment_status", "vimg_fma_rate",
+    "vimg_state_bytes", "vimg_get_state", "vimg_set_state",
 ]
 NSTAGES = 7
 STAGES = ["stats", "corr", "peak", "temporal", "proposal", "carry_copy", "downstream"]
@@ -96,6 +97,12 @@ def _load():
     L.vimg_seek.restype = i
     L.vimg_fma_rate.argtypes = [vp, P(ctypes.c_double)]
     L.vimg_fma_rate.restype = i
+    L.vimg_state_bytes.argtypes = [vp]
+    L.vimg_state_bytes.restype = ctypes.c_longlong
+    L.vimg_get_state.argtypes = [vp, vp, ctypes.c_longlong]
+    L.vimg_get_state.restype = i
+    L.vimg_set_state.argtypes = [vp, vp, ctypes.c_longlong]
+    L.vimg_set_state.restype = i
     L.vimg_segmenter_create.argtypes = [i, i, i, vp]
     L.vimg_segmenter_create.restype = vp
     L.vimg_segmenter_destroy.argtypes = [vp]
@@ -261,6 +268,21 @@ class Handle:
         assert template.shape == (self.H, self.W) and template.is_contiguous()
         self._template = template
         self._check(lib.vimg_set_template(self._h, _ptr(template)))
+
+    def get_state(self) -> bytes:
+        """The stream state (vimg_get_state) as bytes: position, open segment,
+        high-pass history, whole-video sums, proposal counters."""
+        n = lib.vimg_state_bytes(self._h)
+        if n < 0:
+            self._check(int(n))
+        buf = ctypes.create_string_buffer(int(n))
+        self._check(lib.vimg_get_state(self._h, buf, n))
+        return buf.raw
+
+    def set_state(self, state: bytes):
+        """Restores a state from get_state of a handle with the same parameters."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        self._check(lib.vimg_set_state(self._h, buf, len(state)))
 
     def seek(self, t_start: int, history: torch.Tensor | None = None):
         """Starts the stream at absolute frame t_start (a multiple of the segment

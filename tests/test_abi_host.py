@@ -88,6 +88,9 @@ def test_null_handle_calls(vimg):
     assert L.vimg_set_template(None, None) == vimg.ERR_ARG
     assert L.vimg_reset(None) == vimg.ERR_ARG
     assert L.vimg_frames_seen(None) == -1
+    assert L.vimg_state_bytes(None) == vimg.ERR_ARG
+    assert L.vimg_get_state(None, None, 0) == vimg.ERR_ARG
+    assert L.vimg_set_state(None, None, 0) == vimg.ERR_ARG
     assert b"sm_103a" in L.vimg_version()
 
 
