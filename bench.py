@@ -807,6 +807,7 @@ def run_variants(args, frames, planted, T, ref_shifts, corrected, summary, strea
 
 
 # Six concurrent videos of uneven size (H, W, frames): 44.6 GB of uint16 frames.
+SERVE_CHUNK = 64  # frames per video per step in the serving-granularity comparison
 BATCH_VIDEOS = [(256, 256, 20000), (384, 512, 15000), (512, 512, 12000), (512, 1024, 10000),
                 (768, 768, 7500), (1024, 1024, 5000)]
 
@@ -898,6 +899,52 @@ def run_batched(args, stream, dev, ws):
     ms_pt = sequential_run(lambda i: groups[i])
     same = all(torch.equal(a, b) for a, b in zip(ref_shifts, shifts))
     ms_p = sequential_run(lambda i: 0)
+
+    # serving granularity: every video advances by SERVE_CHUNK frames per step
+    # (the smallest streaming chunk of the load); batched = one call per step
+    # for all videos, plain = one call per video per step, round robin
+    serve = SERVE_CHUNK
+    hs = [vimg.Handle(f.shape[1], f.shape[2], stream=stream, max_chunk=maxc, corr_group=g)
+          for f, g in zip(frames, groups)]
+    for h, (_, T) in zip(hs, vids):
+        h.set_template(T)
+    n_min = min(f.shape[0] for f in frames)
+    n_serve = (n_min // serve) * serve  # frames per video in the serving comparison
+    s_rings = [torch.empty((2 * serve, f.shape[1], f.shape[2]), device=dev) for f in frames]
+
+    def serving_batched():
+        for h in hs:
+            h.reset()
+        ks = [0] * len(hs)
+        for t in range(0, n_serve, serve):
+            segs = vimg.process_batch(hs, [f[t:t + serve] for f in frames],
+                                      shifts=[sh[t:t + serve] for sh in shifts],
+                                      corrected=s_rings,
+                                      summary=[m[k:] for m, k in zip(summ, ks)], chunk=serve)
+            ks = [k + g for k, g in zip(ks, segs)]
+
+    def serving_plain():
+        for h in hs:
+            h.reset()
+        ks = [0] * len(hs)
+        for t in range(0, n_serve, serve):
+            for v, (h, f) in enumerate(zip(hs, frames)):
+                ks[v] += h.process(f[t:t + serve], shifts=shifts[v][t:t + serve],
+                                   corrected=s_rings[v], summary=summ[v][ks[v]:])
+
+    ms_sb = timed(serving_batched, 1, 1)
+    sb_shifts = [sh[:n_serve].clone() for sh in shifts]
+    ms_sp = timed(serving_plain, 1, 1)
+    s_same = all(torch.equal(a, b[:n_serve]) for a, b in zip(sb_shifts, shifts))
+    for h in hs:
+        h.close()
+    serving = {"frames_per_video_per_step": serve, "frames": n_serve * len(frames),
+               "batched_value": n_serve * len(frames) / (ms_sb / 1000.0),
+               "plain_per_video_value": n_serve * len(frames) / (ms_sp / 1000.0),
+               "speedup_vs_plain": ms_sp / ms_sb, "shifts_identical": s_same,
+               "note": "the first n frames of every video (n = the shortest video's length, "
+                       "whole chunks), same handles and groups, direct launches for both (each "
+                       "step's call differs, so there is no graph to replay)"}
     value = total / (ms_b / 1000.0)
     del vids, frames, rings, summ
     torch.cuda.empty_cache()
@@ -912,6 +959,7 @@ def run_batched(args, stream, dev, ws):
         "plain_same_groups_value": total / (ms_pt / 1000.0),
         "speedup_vs_plain_same_groups": ms_pt / ms_b,
         "shifts_identical_to_plain_same_groups": same,
+        "serving": serving,
         "autotune": {"choice": {"chunk": chunk, "use_graph": graph, "corr_group": groups},
                      "corr_group_seconds_on_200_frames": {
                          f"{BATCH_VIDEOS[i][0]}x{BATCH_VIDEOS[i][1]}": {str(g): t for g, t in tg.items()}
