@@ -506,7 +506,7 @@ cudaError_t cnn_forward(const float* params, const __nv_bfloat16* wb, float* act
     const float* b = params + w_off(l) + w_count(l);
     const int HI = kSide[l], HO = kSide[l + 1];
     // output channel groups per layer: more threads where there are few pixels
-    if (l == 0) e = conv_fwd<2, 2, 1, 1>(in, w, b, o, n, HI, HO, st);
+    if (l == 0) e = conv_fwd<2, 2, 1, 2>(in, w, b, o, n, HI, HO, st);
     else if (l == 1) e = conv_fwd<32, 2, 1, 2>(in, w, b, o, n, HI, HO, st);
     else e = conv_fwd<32, 2, 1, 2>(in, w, b, o, n, HI, HO, st);
   }
