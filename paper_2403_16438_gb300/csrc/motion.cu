@@ -920,9 +920,11 @@ __global__ void __launch_bounds__(kNarrowGroup * 8, 4)
                   unsigned long long* __restrict__ csum) {
   extern __shared__ __align__(16) float nreg[];  // [27][nrs] frame region - c
   __shared__ unsigned long long cs[kNarrow * kNarrow];
-  const int f = blockIdx.y;
+  // frames vary fastest over the grid, so the CTAs resident on an SM at a time
+  // mostly share one patch group, whose template rows then stay in L1
+  const int f = blockIdx.x;
   const int gpr = (g.nx + kNarrowGroup - 1) / kNarrowGroup;
-  const int py = blockIdx.x / gpr, px0 = (blockIdx.x % gpr) * kNarrowGroup;
+  const int py = blockIdx.y / gpr, px0 = (blockIdx.y % gpr) * kNarrowGroup;
   const int G = min(kNarrowGroup, g.nx - px0);
   const int u = threadIdx.x >> 3, dy = threadIdx.x & 7;
   int cy, cx;
@@ -1127,7 +1129,7 @@ cudaError_t launch_corr_narrow(const uint16_t* frames, int nf, int H, int W, Pat
   });
   if (e != cudaSuccess) return e;
   const int groups = g.ny * ((g.nx + kNarrowGroup - 1) / kNarrowGroup);
-  k_corr_narrow<<<dim3(groups, nf), kNarrowGroup * 8, smem, st>>>(frames, H, W, g, R, td.tc, td.tn2,
+  k_corr_narrow<<<dim3(nf, groups), kNarrowGroup * 8, smem, st>>>(frames, H, W, g, R, td.tc, td.tn2,
                                                                    isf, prop, csum);
   return cudaGetLastError();
 }
