@@ -89,6 +89,16 @@ __host__ __device__ __forceinline__ int dperm(int dyi, int dxi) {
   return base + (a < 4 ? a * 8 + i : 32);
 }
 
+// D (+)= A * B, kind::f16 BF16 operands, FP32 accumulator in TMEM at d;
+// accumulate = 0 overwrites D.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
 // Last frame row of dy block a (rows beyond 52 only feed displacements past 32).
 __host__ __device__ __forceinline__ int last_row(int a) { return min(8 * a + 27, kRows - 1); }
 
@@ -185,32 +195,37 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == kEpiWarps + 1) {
     // ---------------- MMA issuer ----------------
+    // One thread issues every MMA; at N = 128 an MMA occupies the tensor pipe
+    // for about 64 cycles, so the per-row bookkeeping is kept to a few integer
+    // operations: slot state in bit masks (no local arrays), the abort flag read
+    // once per work unit, descriptors advanced by constants.
     if (lane == 0) {
-      int it = 0, u = 0;
-      int slot_use[kSlots] = {0, 0, 0, 0};
-      bool issued = false;
-      for (int wk = blockIdx.x; wk < n_work && !abort_flag; wk += gridDim.x, ++u) {
+      uint32_t it = 0, u = 0;
+      uint32_t used = 0, par = 0;  // bit s: slot s used before / parity of its next release
+      bool issued = false, fail = false;
+      for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x, ++u) {
+        if (abort_flag) break;
         const int grp = wk / np;
         const int rem = nf - grp * kNF;
         const int n_cols = rem >= kNF ? kNF : ((rem + 15) & ~15);
         const uint32_t idesc = idesc_for(n_cols);
-        const int buf = u & 1;
+        const uint32_t buf = u & 1;
         if (!mbar_wait(&a_full[buf], (u >> 1) & 1)) {
-          atomicExch(err, 1);
-          abort_flag = 1;
+          fail = true;
           break;
         }
         // Descriptors change only in their start-address field (bits 0-13, in
         // 16-byte units): build the constant parts once, add offsets per MMA.
         const uint64_t a_desc0 = desc(su32(sA + buf * kABytes), kASlice, kAXl);
         const uint64_t b_desc0 = desc(su32(sB), kNF * 16, 128);
-        for (int b = 0; b < kPasses && !abort_flag; ++b) {
-          const int pass = u * kPasses + b;
-          for (int y = 0; y < kRows; ++y, ++it) {
-            const int s = it % kStages;
+        for (int b = 0; b < kPasses && !fail; ++b) {
+          const uint32_t pass = u * kPasses + b;
+          // A rows start at q0 = 27 - (y - 8 a): one 16-byte row less per frame row
+          uint64_t ad_row = a_desc0 + 27;
+          for (int y = 0; y < kRows; ++y, ++it, --ad_row) {
+            const uint32_t s = it % kStages;
             if (!mbar_wait(&full[s], (it / kStages) & 1)) {
-              atomicExch(err, 1);
-              abort_flag = 1;
+              fail = true;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -218,39 +233,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             // dy blocks fed by row y: a with 8a <= y <= last_row(a)
             const int a_lo = y < 27 ? 0 : (y - 27 + 7) >> 3, a_hi = min(kDyBlk - 1, y >> 3);
             for (int a = a_lo; a <= a_hi; ++a) {
-              const int slot = (a + pass) & (kSlots - 1);
+              const uint32_t slot = (a + pass) & (kSlots - 1);
+              const uint32_t d = tmem + slot * kNF;
+              const uint64_t ad0 = ad_row + (uint64_t)(8 * a);
               if (y == 8 * a) {
-                const int k = slot_use[slot]++;
-                if (k > 0) {
-                  if (!mbar_wait(&acc_free[slot], (k - 1) & 1)) {
-                    atomicExch(err, 1);
-                    abort_flag = 1;
+                const uint32_t bit = 1u << slot;
+                if (used & bit) {
+                  if (!mbar_wait(&acc_free[slot], (par >> slot) & 1)) {
+                    fail = true;
                     break;
                   }
+                  par ^= bit;
                   asm volatile("tcgen05.fence::after_thread_sync;");
                 }
+                used |= bit;
+                mma_bf16(d, ad0, bd0, idesc, 0u);  // the block's first product overwrites
+              } else {
+                mma_bf16(d, ad0, bd0, idesc, 1u);
               }
-              const uint64_t ad0 = a_desc0 + (uint64_t)(27 - (y - 8 * a));  // q0 rows of 16 B
-              const uint32_t d = tmem + (uint32_t)(slot * kNF);
-#pragma unroll
-              for (int qk = 0; qk < kKq; ++qk) {
-                const uint64_t ad = ad0 + (uint64_t)(qk * (2 * kASlice >> 4));
-                const uint64_t bd = bd0 + (uint64_t)(qk * (2 * kNF * 16 >> 4));
-                const uint32_t acc = (y == 8 * a && qk == 0) ? 0u : 1u;
-                asm volatile(
-                    "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              }
-              issued = true;
+              mma_bf16(d, ad0 + (2 * kASlice >> 4), bd0 + (2 * kNF * 16 >> 4), idesc, 1u);
+              mma_bf16(d, ad0 + 2 * (2 * kASlice >> 4), bd0 + 2 * (2 * kNF * 16 >> 4), idesc, 1u);
               if (y == last_row(a)) mma_commit(&acc_full[slot]);
             }
-            if (abort_flag) break;
+            if (fail) break;
+            issued = true;
             if (s % kGroupRows == kGroupRows - 1) mma_commit(&grp_empty[s / kGroupRows]);
           }
         }
-        if (abort_flag) break;
+        if (fail) break;
         mma_commit(&a_empty[buf]);
+      }
+      if (fail) {
+        atomicExch(err, 1);
+        abort_flag = 1;
       }
       // every MMA issued by this thread has completed before the CTA frees TMEM
       if (issued) {
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int m = quad * 32 + lane, xl = m >> 3, i = m & 7;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     int u = 0;
-    int slot_use[kSlots] = {0, 0, 0, 0};
+    uint32_t epar = 0;  // bit s: parity of the next completion of slot s
     for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x, ++u) {
       const int grp = wk / np, p = wk - grp * np;
       const int nvalid = min(kNF, nf - grp * kNF);
@@ -276,12 +291,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int dxi = 16 * b + xl;
         for (int a = 0; a < kDyBlk; ++a) {
           const int slot = (a + pass) & (kSlots - 1);
-          const int k = slot_use[slot]++;
+          const uint32_t k = (epar >> slot) & 1;
+          epar ^= 1u << slot;
           const int dyi = 8 * a + i;
           const bool valid = dyi < kWin && dxi < kWin;
           const float bgv = valid ? __ldg(bg + dyi * kWin + dxi) : 0.f;
           const int dp = valid ? dperm(dyi, dxi) : 0;
-          if (!mbar_wait(&acc_full[slot], k & 1)) {
+          if (!mbar_wait(&acc_full[slot], k)) {
             atomicExch(err, 1);
             abort_flag = 1;
             stop = true;
