@@ -90,12 +90,13 @@ __host__ __device__ __forceinline__ int dperm(int dyi, int dxi) {
 }
 
 // D (+)= A * B, kind::f16 BF16 operands, FP32 accumulator in TMEM at d;
-// accumulate = 0 overwrites D.
+// accumulate = 0 overwrites D.  Called by a whole converged warp; one elected
+// lane issues the MMA.
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
-      "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
+      "{\n.reg .pred pe, pa;\nelect.sync _|pe, 0xffffffff;\nsetp.ne.b32 pa, %4, 0;\n"
+      "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
       "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
 }
 
@@ -195,22 +196,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == kEpiWarps + 1) {
     // ---------------- MMA issuer ----------------
-    // One thread issues every MMA; at N = 128 an MMA occupies the tensor pipe
-    // for about 64 cycles, so the per-row bookkeeping is kept to a few integer
-    // operations: slot state in bit masks (no local arrays), the abort flag read
-    // once per work unit, descriptors advanced by constants.
-    if (lane == 0) {
+    // The whole warp runs the loop in step and one elected lane issues each MMA
+    // and commit, so the descriptor arithmetic stays warp-uniform.  At N = 128
+    // an MMA occupies the tensor pipe for about 64 cycles; the per-row
+    // bookkeeping is kept to a few integer operations: slot state in bit masks
+    // (no local arrays), the abort flag read once per work unit, descriptors
+    // advanced by constants.
+    {
       uint32_t it = 0, u = 0;
       uint32_t used = 0, par = 0;  // bit s: slot s used before / parity of its next release
       bool issued = false, fail = false;
       for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x, ++u) {
-        if (abort_flag) break;
+        if (__shfl_sync(0xffffffffu, abort_flag, 0)) break;
         const int grp = wk / np;
         const int rem = nf - grp * kNF;
         const int n_cols = rem >= kNF ? kNF : ((rem + 15) & ~15);
         const uint32_t idesc = idesc_for(n_cols);
         const uint32_t buf = u & 1;
-        if (!mbar_wait(&a_full[buf], (u >> 1) & 1)) {
+        if (!mbar_wait_warp(&a_full[buf], (u >> 1) & 1)) {
           fail = true;
           break;
         }
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint64_t ad_row = a_desc0 + 27;
           for (int y = 0; y < kRows; ++y, ++it, --ad_row) {
             const uint32_t s = it % kStages;
-            if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+            if (!mbar_wait_warp(&full[s], (it / kStages) & 1)) {
               fail = true;
               break;
             }
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (y == 8 * a) {
                 const uint32_t bit = 1u << slot;
                 if (used & bit) {
-                  if (!mbar_wait(&acc_free[slot], (par >> slot) & 1)) {
+                  if (!mbar_wait_warp(&acc_free[slot], (par >> slot) & 1)) {
                     fail = true;
                     break;
                   }
@@ -253,24 +256,24 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               mma_bf16(d, ad0 + (2 * kASlice >> 4), bd0 + (2 * kNF * 16 >> 4), idesc, 1u);
               mma_bf16(d, ad0 + 2 * (2 * kASlice >> 4), bd0 + 2 * (2 * kNF * 16 >> 4), idesc, 1u);
-              if (y == last_row(a)) mma_commit(&acc_full[slot]);
+              if (y == last_row(a)) mma_commit_elect(&acc_full[slot]);
             }
             if (fail) break;
             issued = true;
-            if (s % kGroupRows == kGroupRows - 1) mma_commit(&grp_empty[s / kGroupRows]);
+            if (s % kGroupRows == kGroupRows - 1) mma_commit_elect(&grp_empty[s / kGroupRows]);
           }
         }
         if (fail) break;
-        mma_commit(&a_empty[buf]);
+        mma_commit_elect(&a_empty[buf]);
       }
-      if (fail) {
+      if (fail && lane == 0) {
         atomicExch(err, 1);
         abort_flag = 1;
       }
-      // every MMA issued by this thread has completed before the CTA frees TMEM
+      // every MMA issued by this warp has completed before the CTA frees TMEM
       if (issued) {
-        mma_commit(&mma_done);
-        mbar_wait(&mma_done, 0);
+        mma_commit_elect(&mma_done);
+        mbar_wait_warp(&mma_done, 0);
       }
     }
   } else {

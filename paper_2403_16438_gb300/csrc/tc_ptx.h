@@ -58,6 +58,23 @@ __device__ __forceinline__ bool mbar_wait_short(uint64_t* bar, uint32_t parity,
   return done != 0;
 }
 
+// Warp-wide form of mbar_wait: every lane polls and lane 0's answer is taken by
+// all, so the warp leaves the loop together and the code after it stays
+// warp-uniform (descriptor arithmetic then runs on the uniform datapath).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity,
+                                               long long spins = kTcSpin) {
+  uint32_t done = 0;
+  for (long long s = 0; s < spins && !done; ++s) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    done = __shfl_sync(0xffffffffu, done, 0);
+  }
+  return done != 0;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }
@@ -76,6 +93,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    su32(bar))
                : "memory");
+}
+
+// mma_commit issued by one elected lane of a converged warp.
+__device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
+  asm volatile(
+      "{\n.reg .pred pe;\nelect.sync _|pe, 0xffffffff;\n"
+      "@pe tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+          su32(bar))
+      : "memory");
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane.
