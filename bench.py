@@ -994,8 +994,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="seconds of host work for the reference arm's warm-up and timed steps")
-    ap.add_argument("--bf16-chunk", type=int, default=250,
-                    help="frames per internal batch of the tensor-core path (two 128-frame groups)")
+    ap.add_argument("--bf16-chunk", type=int, default=1000,
+                    help="frames per internal batch of the tensor-core path (eight 128-frame groups, so the (group, patch) work units leave a small last wave)")
     ap.add_argument("--corr", choices=["f32", "bf16", "proposal"], default="f32",
                     help="correlation path of the main line (f32 = the full-window FP32 method)")
     ap.add_argument("--train-frames", type=int, default=200000,

@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                     // [2][kABytes]
   unsigned char* sB = smem + 2 * kABytes;       // [kStages][kBStage]
-  __shared__ __align__(8) uint64_t full[kStages], grp_empty[kStages / kGroupRows];
+  // full[q]: the kGroupRows frame rows of ring group q have landed (one wait per group);
+  // grp_empty[q]: the MMAs reading them have completed
+  __shared__ __align__(8) uint64_t full[kStages / kGroupRows], grp_empty[kStages / kGroupRows];
   __shared__ __align__(8) uint64_t a_full[2], a_empty[2];
   __shared__ __align__(8) uint64_t acc_full[kSlots], acc_free[kSlots], mma_done;
   __shared__ uint32_t tmem_base;
@@ -127,8 +129,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
-    for (int q = 0; q < kStages / kGroupRows; ++q) mbar_init(&grp_empty[q], 1);
+    for (int q = 0; q < kStages / kGroupRows; ++q) {
+      mbar_init(&full[q], kGroupRows);
+      mbar_init(&grp_empty[q], 1);
+    }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&a_full[i], 1);
       mbar_init(&a_empty[i], 1);
@@ -178,20 +182,23 @@ __global__ void __launch_bounds__(kThreads, 1)
               abort_flag = 1;
               break;
             }
-            mbar_expect_tx(&full[s], kBStage);
+            uint64_t* fb = &full[s / kGroupRows];
+            mbar_expect_tx(fb, kBStage);  // one of the group's kGroupRows arrivals
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
                     su32(sB + s * kBStage)),
                 "l"(&tmap), "r"(0), "r"(grp * (kNF / 16)), "r"(cb0 + 2 * b), "r"(ty - kMaxR + y),
-                "r"(su32(&full[s]))
+                "r"(su32(fb))
                 : "memory");
           }
       }
-      // wait (bounded) for the copies this thread issued: the last use of every stage
-      for (int s = 0; s < kStages && s < it; ++s) {
-        const int last_use = (it - 1 - s) / kStages;
-        mbar_wait(&full[s], last_use & 1);
-      }
+      // a last, partial ring group completes with plain arrivals in place of its
+      // missing rows
+      if (it % kGroupRows)
+        for (int r = it % kGroupRows; r < kGroupRows; ++r) mbar_arrive(&full[(it % kStages) / kGroupRows]);
+      // wait (bounded) for the copies this thread issued: the last use of every group
+      const int n_grp = (it + kGroupRows - 1) / kGroupRows, ring = kStages / kGroupRows;
+      for (int q = 0; q < ring && q < n_grp; ++q) mbar_wait(&full[q], ((n_grp - 1 - q) / ring) & 1);
       for (int i = 0; i < 2 && i < na; ++i) mbar_wait(&a_full[i], ((na - 1 - i) >> 1) & 1);
     }
   } else if (warp == kEpiWarps + 1) {
@@ -227,11 +234,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint64_t ad_row = a_desc0 + 27;
           for (int y = 0; y < kRows; ++y, ++it, --ad_row) {
             const uint32_t s = it % kStages;
-            if (!mbar_wait_warp(&full[s], (it / kStages) & 1)) {
-              fail = true;
-              break;
+            if (s % kGroupRows == 0) {  // the first row of a ring group: all its rows have landed
+              if (!mbar_wait_warp(&full[s / kGroupRows], (it / kStages) & 1)) {
+                fail = true;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
             const uint64_t bd0 = b_desc0 + (uint64_t)(s * (kBStage >> 4));
             // dy blocks fed by row y: a with 8a <= y <= last_row(a)
             const int a_lo = y < 27 ? 0 : (y - 27 + 7) >> 3, a_hi = min(kDyBlk - 1, y >> 3);
