@@ -103,6 +103,65 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, u
 // Last frame row of dy block a (rows beyond 52 only feed displacements past 32).
 __host__ __device__ __forceinline__ int last_row(int a) { return min(8 * a + 27, kRows - 1); }
 
+// State of the MMA-issuing warp carried from row to row.
+struct IssueState {
+  uint32_t it;    // frame rows consumed (position in the ring)
+  uint32_t used;  // bit s: accumulator slot s has been used before
+  uint32_t par;   // bit s: parity of slot s's next release by the epilogue
+};
+
+struct IssueCtx {
+  uint64_t* full;
+  uint64_t* grp_empty;
+  uint64_t* acc_full;
+  uint64_t* acc_free;
+  uint32_t tmem, idesc;
+  uint64_t b_desc0;
+};
+
+// MMAs of frame rows [y0, y1) of one pass, rows that feed exactly the dy blocks
+// A0..A1: with the block set fixed at compile time each row's MMAs are
+// straight-line code.  Per block and row, three K chunks of 16 columns; the
+// block's first row overwrites its accumulator slot (after the epilogue has
+// released it) and its last row commits it to the epilogue.  False when a wait
+// gave up.
+template <int A0, int A1>
+__device__ __forceinline__ bool issue_rows(int y0, int y1, uint32_t pass, uint64_t& ad_row,
+                                           IssueState& st, const IssueCtx& c) {
+  static_assert(kRows == 53 && kDyBlk == 5, "row segments assume a 53-row region, 5 dy blocks");
+  for (int y = y0; y < y1; ++y, ++st.it, --ad_row) {
+    const uint32_t s = st.it % kStages;
+    if (s % kGroupRows == 0) {  // the first row of a ring group: all its rows have landed
+      if (!mbar_wait_warp(&c.full[s / kGroupRows], (st.it / kStages) & 1)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    const uint64_t bd0 = c.b_desc0 + (uint64_t)(s * (kBStage >> 4));
+#pragma unroll
+    for (int a = A0; a <= A1; ++a) {
+      const uint32_t slot = (a + pass) & (kSlots - 1);
+      const uint32_t d = c.tmem + slot * kNF;
+      const uint64_t ad0 = ad_row + (uint64_t)(8 * a);
+      if (y == 8 * a) {
+        const uint32_t bit = 1u << slot;
+        if (st.used & bit) {
+          if (!mbar_wait_warp(&c.acc_free[slot], (st.par >> slot) & 1)) return false;
+          st.par ^= bit;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        st.used |= bit;
+        mma_bf16(d, ad0, bd0, c.idesc, 0u);
+      } else {
+        mma_bf16(d, ad0, bd0, c.idesc, 1u);
+      }
+      mma_bf16(d, ad0 + (2 * kASlice >> 4), bd0 + (2 * kNF * 16 >> 4), c.idesc, 1u);
+      mma_bf16(d, ad0 + 2 * (2 * kASlice >> 4), bd0 + 2 * (2 * kNF * 16 >> 4), c.idesc, 1u);
+      if (y == last_row(a)) mma_commit_elect(&c.acc_full[slot]);
+    }
+    if (s % kGroupRows == kGroupRows - 1) mma_commit_elect(&c.grp_empty[s / kGroupRows]);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_corr_bf16(const __grid_constant__ CUtensorMap tmap, int nf, PatchGrid g,
                 const __nv_bfloat16* __restrict__ astore, const float* __restrict__ bgc,
@@ -205,13 +264,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer ----------------
     // The whole warp runs the loop in step and one elected lane issues each MMA
     // and commit, so the descriptor arithmetic stays warp-uniform.  At N = 128
-    // an MMA occupies the tensor pipe for about 64 cycles; the per-row
-    // bookkeeping is kept to a few integer operations: slot state in bit masks
-    // (no local arrays), the abort flag read once per work unit, descriptors
-    // advanced by constants.
+    // an MMA occupies the tensor pipe for about 64 cycles, and a single warp's
+    // dependent integer work easily costs more, so the bookkeeping is kept
+    // small: slot state in bit masks (no local arrays), the abort flag read once
+    // per work unit, one wait per ring group, descriptors advanced by constants,
+    // and the dy blocks of each row segment fixed at compile time.
     {
-      uint32_t it = 0, u = 0;
-      uint32_t used = 0, par = 0;  // bit s: slot s used before / parity of its next release
+      uint32_t u = 0;
+      IssueState st{0, 0, 0};
       bool issued = false, fail = false;
       for (int wk = blockIdx.x; wk < n_work; wk += gridDim.x, ++u) {
         if (__shfl_sync(0xffffffffu, abort_flag, 0)) break;
@@ -228,49 +288,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         // 16-byte units): build the constant parts once, add offsets per MMA.
         const uint64_t a_desc0 = desc(su32(sA + buf * kABytes), kASlice, kAXl);
         const uint64_t b_desc0 = desc(su32(sB), kNF * 16, 128);
+        const IssueCtx c{full, grp_empty, acc_full, acc_free, tmem, idesc, b_desc0};
         for (int b = 0; b < kPasses && !fail; ++b) {
-          const uint32_t pass = u * kPasses + b;
+          issued = true;
           // A rows start at q0 = 27 - (y - 8 a): one 16-byte row less per frame row
           uint64_t ad_row = a_desc0 + 27;
-          for (int y = 0; y < kRows; ++y, ++it, --ad_row) {
-            const uint32_t s = it % kStages;
-            if (s % kGroupRows == 0) {  // the first row of a ring group: all its rows have landed
-              if (!mbar_wait_warp(&full[s / kGroupRows], (it / kStages) & 1)) {
-                fail = true;
-                break;
-              }
-              asm volatile("tcgen05.fence::after_thread_sync;");
-            }
-            const uint64_t bd0 = b_desc0 + (uint64_t)(s * (kBStage >> 4));
-            // dy blocks fed by row y: a with 8a <= y <= last_row(a)
-            const int a_lo = y < 27 ? 0 : (y - 27 + 7) >> 3, a_hi = min(kDyBlk - 1, y >> 3);
-            for (int a = a_lo; a <= a_hi; ++a) {
-              const uint32_t slot = (a + pass) & (kSlots - 1);
-              const uint32_t d = tmem + slot * kNF;
-              const uint64_t ad0 = ad_row + (uint64_t)(8 * a);
-              if (y == 8 * a) {
-                const uint32_t bit = 1u << slot;
-                if (used & bit) {
-                  if (!mbar_wait_warp(&acc_free[slot], (par >> slot) & 1)) {
-                    fail = true;
-                    break;
-                  }
-                  par ^= bit;
-                  asm volatile("tcgen05.fence::after_thread_sync;");
-                }
-                used |= bit;
-                mma_bf16(d, ad0, bd0, idesc, 0u);  // the block's first product overwrites
-              } else {
-                mma_bf16(d, ad0, bd0, idesc, 1u);
-              }
-              mma_bf16(d, ad0 + (2 * kASlice >> 4), bd0 + (2 * kNF * 16 >> 4), idesc, 1u);
-              mma_bf16(d, ad0 + 2 * (2 * kASlice >> 4), bd0 + 2 * (2 * kNF * 16 >> 4), idesc, 1u);
-              if (y == last_row(a)) mma_commit_elect(&acc_full[slot]);
-            }
-            if (fail) break;
-            issued = true;
-            if (s % kGroupRows == kGroupRows - 1) mma_commit_elect(&grp_empty[s / kGroupRows]);
-          }
+          const uint32_t pass = u * kPasses + b;
+          // row segments with a fixed set of dy blocks (a with 8a <= y <= last_row(a))
+          fail = !(issue_rows<0, 0>(0, 8, pass, ad_row, st, c) &&
+                   issue_rows<0, 1>(8, 16, pass, ad_row, st, c) &&
+                   issue_rows<0, 2>(16, 24, pass, ad_row, st, c) &&
+                   issue_rows<0, 3>(24, 28, pass, ad_row, st, c) &&
+                   issue_rows<1, 3>(28, 32, pass, ad_row, st, c) &&
+                   issue_rows<1, 4>(32, 36, pass, ad_row, st, c) &&
+                   issue_rows<2, 4>(36, 44, pass, ad_row, st, c) &&
+                   issue_rows<3, 4>(44, 52, pass, ad_row, st, c) &&
+                   issue_rows<4, 4>(52, 53, pass, ad_row, st, c));
         }
         if (fail) break;
         mma_commit_elect(&a_empty[buf]);
