@@ -89,15 +89,22 @@ __host__ __device__ __forceinline__ int dperm(int dyi, int dxi) {
   return base + (a < 4 ? a * 8 + i : 32);
 }
 
-// D (+)= A * B, kind::f16 BF16 operands, FP32 accumulator in TMEM at d;
-// accumulate = 0 overwrites D.  Called by a whole converged warp; one elected
-// lane issues the MMA.
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                         uint32_t accumulate) {
+// The three K chunks of one dy block and frame row, kind::f16 with BF16
+// operands and the FP32 accumulator in TMEM at d: D (+)= sum_q A_q * B_q
+// (accumulate_first = 0: the first product overwrites D, the others add).
+// Called by a whole converged warp; one elected lane issues all three.
+__device__ __forceinline__ void mma_bf16_x3(uint32_t d, uint64_t a0, uint64_t b0, uint32_t idesc,
+                                            uint32_t accumulate_first) {
+  static_assert(kKq == 3, "three K chunks of 16 columns per frame row");
+  constexpr uint64_t kDa = 2 * kASlice >> 4, kDb = 2 * kNF * 16 >> 4;  // per K chunk, 16-B units
   asm volatile(
-      "{\n.reg .pred pe, pa;\nelect.sync _|pe, 0xffffffff;\nsetp.ne.b32 pa, %4, 0;\n"
-      "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+      "{\n.reg .pred pe, pa, pt;\nelect.sync _|pe, 0xffffffff;\n"
+      "setp.ne.b32 pa, %7, 0;\nsetp.eq.b32 pt, %7, %7;\n"
+      "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %8, pa;\n"
+      "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %5, %8, pt;\n"
+      "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %6, %8, pt;\n}\n" ::"r"(d),
+      "l"(a0), "l"(a0 + kDa), "l"(a0 + 2 * kDa), "l"(b0), "l"(b0 + kDb), "l"(b0 + 2 * kDb),
+      "r"(accumulate_first), "r"(idesc));
 }
 
 // Last frame row of dy block a (rows beyond 52 only feed displacements past 32).
@@ -149,12 +156,10 @@ __device__ __forceinline__ bool issue_rows(int y0, int y1, uint32_t pass, uint64
           asm volatile("tcgen05.fence::after_thread_sync;");
         }
         st.used |= bit;
-        mma_bf16(d, ad0, bd0, c.idesc, 0u);
+        mma_bf16_x3(d, ad0, bd0, c.idesc, 0u);
       } else {
-        mma_bf16(d, ad0, bd0, c.idesc, 1u);
+        mma_bf16_x3(d, ad0, bd0, c.idesc, 1u);
       }
-      mma_bf16(d, ad0 + (2 * kASlice >> 4), bd0 + (2 * kNF * 16 >> 4), c.idesc, 1u);
-      mma_bf16(d, ad0 + 2 * (2 * kASlice >> 4), bd0 + 2 * (2 * kNF * 16 >> 4), c.idesc, 1u);
       if (y == last_row(a)) mma_commit_elect(&c.acc_full[slot]);
     }
     if (s % kGroupRows == kGroupRows - 1) mma_commit_elect(&c.grp_empty[s / kGroupRows]);
