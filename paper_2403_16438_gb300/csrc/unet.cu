@@ -274,9 +274,11 @@ __global__ void __launch_bounds__(kUThreads, 1)
     }
   } else if (warp == kUEpiWarps + 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    // The whole warp runs the loop in step and one elected lane issues each MMA
+    // and commit, so the descriptor arithmetic stays warp-uniform.
+    {
       int it = 0, tl = 0;
-      bool issued = false;
+      bool issued = false, fail = false;
       const uint32_t idesc = idesc_for(p.ntile);
       const uint32_t a_lbo = p.lin ? p.plane_bytes : 2048u;
       // descriptor steps in 16-byte units
@@ -287,16 +289,13 @@ __global__ void __launch_bounds__(kUThreads, 1)
       for (int t = 0; t < TQ; ++t)
         a_t[t] = TQ == 9 ? (uint64_t)(p.hoff + (t / 3 - 1) * p.sp_in + (t % 3 - 1)) : 0;
       const int kk = p.kc / 16, R = p.R;
-      if (p.bres && !mbar_wait(&bres_full, 0)) {
-        atomicExch(p.err, 1);
-        abort_flag = 1;
-      }
-      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++tl) {
+      if (p.bres && !mbar_wait_warp(&bres_full, 0)) fail = true;
+      for (int tile = blockIdx.x; tile < n_tiles && !fail; tile += gridDim.x, ++tl) {
+        if (__shfl_sync(0xffffffffu, abort_flag, 0)) break;
         const int buf = tl & 1, use = tl >> 1;
         if (use > 0) {
-          if (!mbar_wait(&acc_empty[buf], (use - 1) & 1)) {
-            atomicExch(p.err, 1);
-            abort_flag = 1;
+          if (!mbar_wait_warp(&acc_empty[buf], (use - 1) & 1)) {
+            fail = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
@@ -304,9 +303,8 @@ __global__ void __launch_bounds__(kUThreads, 1)
         const uint32_t dbase = tmem + (uint32_t)(buf * acc_cols);
         for (int q = 0; q < nq; ++q, ++it) {
           const int s = it % S;
-          if (!mbar_wait(&full[s], (it / S) & 1)) {
-            atomicExch(p.err, 1);
-            abort_flag = 1;
+          if (!mbar_wait_warp(&full[s], (it / S) & 1)) {
+            fail = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
@@ -325,23 +323,27 @@ __global__ void __launch_bounds__(kUThreads, 1)
               for (int r = 0; r < 4; ++r) {
                 if (r < R)
                   asm volatile(
-                      "{\n.reg .pred pa;\nsetp.ne.b32 pa, %4, 0;\n"
-                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(
+                      "{\n.reg .pred pe, pa;\nelect.sync _|pe, 0xffffffff;\nsetp.ne.b32 pa, %4, 0;\n"
+                      "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(
                           dbase + (uint32_t)(r * p.ntile)),
                       "l"(ad + (uint64_t)(128 * r)), "l"(bd), "r"(idesc), "r"(acc));
               }
             }
           }
           issued = true;
-          mma_commit(&empty[s]);
+          mma_commit_elect(&empty[s]);
         }
-        if (abort_flag) break;
-        mma_commit(&acc_full[buf]);
+        if (fail) break;
+        mma_commit_elect(&acc_full[buf]);
       }
-      // every MMA issued by this thread has completed before the CTA frees TMEM
+      if (fail && lane == 0) {
+        atomicExch(p.err, 1);
+        abort_flag = 1;
+      }
+      // every MMA issued by this warp has completed before the CTA frees TMEM
       if (issued) {
-        mma_commit(&mma_done);
-        mbar_wait(&mma_done, 0);
+        mma_commit_elect(&mma_done);
+        mbar_wait_warp(&mma_done, 0);
       }
     }
   } else {
