@@ -526,7 +526,9 @@ def run_vimg(args):
         line["e2e"] = {"value": n * ke * ws / te, "unit": UNIT,
                        "h2d_bytes_per_step": n * H * W * 2,
                        "d2h_bytes_per_step": n * 2 * 4 + k_max * 2 * H * W * 4,
-                       "steps": ke, "step_ms": step_ms, "clocks": e2e_clocks,
+                       "steps": ke, "step_ms": step_ms,
+                       "step_ms_median": sorted(step_ms)[len(step_ms) // 2],
+                       "clocks": e2e_clocks,
                        "h2d_GBs_measured": h2d_gbs,
                        "host_cpus": (f"{min(local_cpus)}-{max(local_cpus)} ({len(local_cpus)} "
                                      "CPUs local to the GPU)") if local_cpus else "not pinned",
@@ -986,7 +988,8 @@ def main():
     ap.add_argument("--frames", type=int, default=10000)
     ap.add_argument("--chunk", type=int, default=1000,
                     help="frames per internal batch (one launch per stage)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10,
+                    help="timed end-to-end steps (at most --steps); ~0.13 s each at the default size")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
