@@ -401,30 +401,39 @@ __device__ __forceinline__ void dperm_inv(int t, int& dyi, int& dxi) {
 
 // ZNCC of every (frame, displacement) summed over the patches in patch order:
 //   C(d) = sum_p num_p(d) * 21 / |Tc_p| * isf(window_p(d)),  stored in 2^-40 fixed point.
-// Thread = storage position t (contiguous numerator reads); the patch loop is
-// unrolled so that several patches' loads are in flight.
+// Thread = storage position t of two consecutive frames (contiguous numerator
+// reads; the patch scale is computed once for both and twice the loads are in
+// flight); each frame's sum runs in patch order.
 __global__ void k_zncc_reduce(const float* __restrict__ num, int nf, PatchGrid g,
                               const float* __restrict__ tn2, const float* __restrict__ isf,
                               int sh, int sw, unsigned long long* __restrict__ csum) {
-  const int f = blockIdx.y, np = g.ny * g.nx;
+  const int f0 = 2 * blockIdx.y, np = g.ny * g.nx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= kNWin || f >= nf) return;
+  if (t >= kNWin || f0 >= nf) return;
+  const bool two = f0 + 1 < nf;
+  const int f1 = two ? f0 + 1 : f0;  // a missing second frame repeats the first (not stored)
   int dy, dx;
   dperm_inv(t, dy, dx);
-  const float* nf_ = num + (size_t)f * np * kNWin + t;
-  const float* is = isf + (size_t)f * sh * sw + (size_t)dy * sw + dx;
-  float acc = 0.f;
+  const float* n0 = num + (size_t)f0 * np * kNWin + t;
+  const float* n1 = num + (size_t)f1 * np * kNWin + t;
+  const float* i0 = isf + (size_t)f0 * sh * sw + (size_t)dy * sw + dx;
+  const float* i1 = isf + (size_t)f1 * sh * sw + (size_t)dy * sw + dx;
+  float acc0 = 0.f, acc1 = 0.f;
   int p = 0;
   for (int py = 0; py < g.ny; ++py) {
-    const float* isr = is + (size_t)py * kPatch * sw;
+    const size_t ro = (size_t)py * kPatch * sw;
 #pragma unroll 4
     for (int px = 0; px < g.nx; ++px, ++p) {
       const float t2 = __ldg(tn2 + p);
       const float ps = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
-      acc = fmaf(__ldg(nf_ + (size_t)p * kNWin) * ps, __ldg(isr + px * kPatch), acc);
+      const size_t no = (size_t)p * kNWin, io = ro + px * kPatch;
+      acc0 = fmaf(__ldg(n0 + no) * ps, __ldg(i0 + io), acc0);
+      acc1 = fmaf(__ldg(n1 + no) * ps, __ldg(i1 + io), acc1);
     }
   }
-  csum[(size_t)f * kNWin + dy * kWin + dx] = (unsigned long long)__float2ll_rn(acc * (float)kFix);
+  const size_t o = (size_t)dy * kWin + dx;
+  csum[(size_t)f0 * kNWin + o] = (unsigned long long)__float2ll_rn(acc0 * (float)kFix);
+  if (two) csum[(size_t)f1 * kNWin + o] = (unsigned long long)__float2ll_rn(acc1 * (float)kFix);
 }
 
 // ---- per-template constants -----------------------------------------------------
@@ -580,8 +589,8 @@ cudaError_t launch_corr_bf16(const void* tmap, int nf, int R, PatchGrid g,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int sh = kPatch * (g.ny - 1) + 2 * R + 1, sw = kPatch * (g.nx - 1) + 2 * R + 1;
-  k_zncc_reduce<<<dim3((kNWin + 127) / 128, nf), 128, 0, st>>>(num, nf, g, td.tn2, isf, sh, sw,
-                                                               csum);
+  k_zncc_reduce<<<dim3((kNWin + 127) / 128, (nf + 1) / 2), 128, 0, st>>>(num, nf, g, td.tn2,
+                                                                         isf, sh, sw, csum);
   return cudaGetLastError();
 }
 
