@@ -20,21 +20,22 @@
 // The frames arrive by TMA from Fc images laid out [row][8-column block][frame]
 // [8], so each frame row of the region is one box of 6 column blocks x 128 frames.
 //
-// One tcgen05.mma of M = 128, K = 16 costs about the same for any N in 64..128,
-// and a tcgen05.commit stalls the issuing thread for a few hundred cycles, so
-// the kernel runs N = 128 and commits rarely.  TMEM (512 columns) holds 4
-// accumulators of 128 columns: dy block a of pass P (P counts passes over all
-// units) uses slot (a + P) mod 4.  Only 4 dy blocks are ever live at once
+// One tcgen05.mma of M = 128, K = 16 occupies the tensor pipe for N / 2 cycles
+// (64 at N = 128), so one warp must issue an MMA in less than that: the issue
+// loop is kept to straight-line, warp-uniform code, and commits are grouped.
+// The kernel runs N = 128 so that four accumulators fit in TMEM (512 columns):
+// dy block a of pass P (P counts passes over all units) uses slot (a + P) mod 4.  Only 4 dy blocks are ever live at once
 // (block 0 ends at row 27, block 4 starts at row 32), and the rotation gives
 // every other hand-off between passes many rows of slack.
 //
 // Warp roles (one persistent CTA per SM, 320 threads):
 //   warp 8  producer: per work unit the patch's A store (bulk copy, double
 //           buffered across units), then 3 passes x 53 frame rows of B through
-//           an 8-row ring released in groups of 4 rows;
-//   warp 9  MMA issuer: per row, 3 MMAs for each dy block the row feeds; one
-//           commit per 4 rows frees a ring group, one per finished dy block
-//           hands its accumulator to the epilogue;
+//           an 8-row ring whose rows land and are released in groups of 4;
+//   warp 9  MMA issuer (the whole warp in step, one elected lane issuing): per
+//           row, 3 MMAs for each dy block the row feeds; one commit per 4 rows
+//           frees a ring group, one per finished dy block hands its accumulator
+//           to the epilogue;
 //   warps 0-7 epilogue: TMEM -> registers (warp w: lanes 32 (w mod 4) .. + 31,
 //           columns 64 (w / 4) .. + 63), + B_p(d), stores of the per-patch
 //           numerators, then release of the accumulator slot.
