@@ -111,6 +111,30 @@ __device__ __forceinline__ void mma_bf16_x3(uint32_t d, uint64_t a0, uint64_t b0
 // Last frame row of dy block a (rows beyond 52 only feed displacements past 32).
 __host__ __device__ __forceinline__ int last_row(int a) { return min(8 * a + 27, kRows - 1); }
 
+// The row segments the issue loop walks: rows [y0, y1) feed exactly dy blocks
+// a0..a1.  Checked at compile time against the rule they encode (row y feeds
+// block a iff 8a <= y <= last_row(a)), so that every row of a pass is issued
+// once with its full block set.
+struct RowSegment {
+  int y0, y1, a0, a1;
+};
+constexpr RowSegment kRowSegments[] = {{0, 8, 0, 0},   {8, 16, 0, 1},  {16, 24, 0, 2},
+                                       {24, 28, 0, 3}, {28, 32, 1, 3}, {32, 36, 1, 4},
+                                       {36, 44, 2, 4}, {44, 52, 3, 4}, {52, 53, 4, 4}};
+constexpr bool row_segments_match() {
+  int y = 0;
+  for (const RowSegment& g : kRowSegments) {
+    if (g.y0 != y || g.y1 <= g.y0) return false;
+    for (; y < g.y1; ++y)
+      for (int a = 0; a < kDyBlk; ++a) {
+        const bool fed = 8 * a <= y && y <= (8 * a + 27 < kRows - 1 ? 8 * a + 27 : kRows - 1);
+        if (fed != (g.a0 <= a && a <= g.a1)) return false;
+      }
+  }
+  return y == kRows;
+}
+static_assert(row_segments_match(), "row segments and dy-block sets of the issue loop");
+
 // State of the MMA-issuing warp carried from row to row.
 struct IssueState {
   uint32_t it;    // frame rows consumed (position in the ring)
@@ -301,15 +325,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint64_t ad_row = a_desc0 + 27;
           const uint32_t pass = u * kPasses + b;
           // row segments with a fixed set of dy blocks (a with 8a <= y <= last_row(a))
-          fail = !(issue_rows<0, 0>(0, 8, pass, ad_row, st, c) &&
-                   issue_rows<0, 1>(8, 16, pass, ad_row, st, c) &&
-                   issue_rows<0, 2>(16, 24, pass, ad_row, st, c) &&
-                   issue_rows<0, 3>(24, 28, pass, ad_row, st, c) &&
-                   issue_rows<1, 3>(28, 32, pass, ad_row, st, c) &&
-                   issue_rows<1, 4>(32, 36, pass, ad_row, st, c) &&
-                   issue_rows<2, 4>(36, 44, pass, ad_row, st, c) &&
-                   issue_rows<3, 4>(44, 52, pass, ad_row, st, c) &&
-                   issue_rows<4, 4>(52, 53, pass, ad_row, st, c));
+          // (kRowSegments, spelled out so that each segment's block set is a
+          // template argument)
+#define VIMG_SEG(i)                                                                      \
+  issue_rows<kRowSegments[i].a0, kRowSegments[i].a1>(kRowSegments[i].y0, kRowSegments[i].y1, \
+                                                     pass, ad_row, st, c)
+          fail = !(VIMG_SEG(0) && VIMG_SEG(1) && VIMG_SEG(2) && VIMG_SEG(3) && VIMG_SEG(4) &&
+                   VIMG_SEG(5) && VIMG_SEG(6) && VIMG_SEG(7) && VIMG_SEG(8));
+#undef VIMG_SEG
+          static_assert(sizeof(kRowSegments) / sizeof(kRowSegments[0]) == 9, "nine segments");
         }
         if (fail) break;
         mma_commit_elect(&a_empty[buf]);
