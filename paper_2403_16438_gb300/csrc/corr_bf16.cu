@@ -71,7 +71,7 @@ constexpr uint32_t kAXl = kCb * kASlice;               // 3,360 B per xl
 constexpr uint32_t kABytes = kXl * kAXl;               // 53,760 B per patch
 constexpr uint32_t kBStage = kCb * kNF * 16;           // 12,288 B per frame row
 constexpr int kStages = 8;                             // ring of frame rows
-constexpr int kGroupRows = 4;                          // rows released by one commit
+constexpr int kGroupRows = 4;                          // rows landing on one barrier, released by one commit
 constexpr size_t kSmem = 2 * (size_t)kABytes + (size_t)kStages * kBStage;  // 205,824 B
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (kEpiWarps + 2) * 32;         // 320
