@@ -473,21 +473,34 @@ cudaError_t launch_stats(const uint16_t* frames, int nf, int H, int W, PatchGrid
 constexpr int kCsEntries = kMaxWin * kMaxWin + 1;  // keeps what follows 16-byte aligned
 constexpr int kRegionRows = kPatch + 2 * kMaxR;                     // 53
 constexpr int kHalfRow = 17;  // columns per lane in the 33rd-row pass (0..16 or 16..32)
+// Region row stride for a group of G patches: at least one column beyond the
+// G * 21 + 32 that the windows read (a lane's last 8-byte pair may reach one
+// column past its 53 values), and 2 mod 4, so that lanes on consecutive rows
+// reading 8-byte pairs fall in distinct banks (rs / 2 odd).
+__host__ __device__ constexpr int corr_region_stride(int G) {
+  return G * kPatch + 2 * kMaxR + 1 + ((2 - (G * kPatch + 2 * kMaxR + 1) % 4) + 4) % 4;
+}
+
+static_assert(corr_region_stride(11) == 266 && corr_region_stride(10) == 246 &&
+                  corr_region_stride(8) == 202 && corr_region_stride(7) == 182,
+              "region strides of the patch-group sizes");
+
 template <int GP>
 struct CorrGeom {
   static_assert(GP >= 2 && GP <= 16, "the 33rd-row pass maps 16 patches x 2 column halves");
   static constexpr int kWarps = GP + 1;                            // per group
   static constexpr int kThreads = 32 * kWarps;                     // per group
   static constexpr int kCta = 2 * kThreads;                        // two groups
-  static constexpr int kStride = (GP * kPatch + 2 * kMaxR) | 1;    // region row stride
+  static constexpr int kStride = corr_region_stride(GP);          // region row stride
   static constexpr int kIsf = (GP - 1) * kPatch + kMaxWin;         // isf columns
+  static constexpr int kIsfFloats = (kMaxWin * kIsf + 3) & ~3;     // keeps the region 16-B aligned
   static constexpr size_t kSmem =                                  // per group, 16-byte multiple
-      (sizeof(unsigned long long) * kCsEntries + sizeof(float) * kMaxWin * kIsf +
+      (sizeof(unsigned long long) * kCsEntries + sizeof(float) * kIsfFloats +
        sizeof(float) * kRegionRows * kStride + 15) & ~(size_t)15;
 };
 
 // floor(i / d) as a multiply-high by m = ceil(2^32 / d): exact for i < 2^32 / d,
-// far above any index here (d <= 263, i < 14,000).
+// far above any index here (d <= 266, i < 14,100).
 __device__ __forceinline__ unsigned fast_div(unsigned i, unsigned m) { return __umulhi(i, m); }
 
 template <int N>
@@ -520,6 +533,42 @@ __device__ __forceinline__ void corr_row(const float* __restrict__ rrow, int rs,
   }
 }
 
+// corr_row with the frame values read as 8-byte pairs: rrow - SH is 8-byte
+// aligned (SH = the parity of the row start), rs is even, and the window's
+// values are the pairs' elements SH .. SH + NX + 19; the FMAs and their order
+// are those of corr_row.
+template <int NX, int SH>
+__device__ __forceinline__ void corr_row_pairs(const float* __restrict__ rrow, int rs,
+                                               const float* __restrict__ trow,
+                                               float (&acc)[NX]) {
+  constexpr int kPairs = (NX + kPatch - 1 + SH + 1) / 2;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) acc[j] = 0.f;
+  const float2* rp = reinterpret_cast<const float2*>(rrow - SH);
+  const int rs2 = rs >> 1;
+#pragma unroll 1
+  for (int ky = 0; ky < kPatch; ++ky) {
+    float fr[2 * kPairs];
+#pragma unroll
+    for (int i = 0; i < kPairs; ++i) {
+      const float2 v = rp[i];
+      fr[2 * i] = v.x, fr[2 * i + 1] = v.y;
+    }
+    float t[kTplStride];
+#pragma unroll
+    for (int i = 0; i < kTplStride; i += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(trow + i));
+      t[i] = v.x, t[i + 1] = v.y, t[i + 2] = v.z, t[i + 3] = v.w;
+    }
+#pragma unroll
+    for (int kx = 0; kx < kPatch; ++kx)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) acc[j] = fmaf(t[kx], fr[SH + j + kx], acc[j]);
+    rp += rs2;
+    trow += kTplStride;
+  }
+}
+
 template <int NX, int GP>
 __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
     k_corr_f32(const __grid_constant__ MotionBatch b, const int* __restrict__ list,
@@ -530,7 +579,7 @@ __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
   const int lane = gtid & 31, gwarp = gtid >> 5;
   unsigned long long* cs = reinterpret_cast<unsigned long long*>(smem + grp * C::kSmem);
   float* ism = reinterpret_cast<float*>(cs + kCsEntries);  // [w][scols]
-  float* reg = ism + kMaxWin * C::kIsf;                   // [rows][rs]
+  float* reg = ism + C::kIsfFloats;                      // [rows][rs], 16-byte aligned
   // With a frame list (fallback frames of the learned proposal; one job) only the
   // listed frames are processed; their count is read from device memory.
   int n_items = b.corr_begin[b.n];
@@ -565,9 +614,9 @@ __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
     const int py = rem / groups_per_row, gx = rem - py * groups_per_row;
     const int px0 = gx * GP, G = min(GP, g.nx - px0);
     const int cols = G * kPatch + 2 * R;
-    // Rows are allocated for the widest window (a lane always reads 53 values) and
-    // given an odd stride so that lanes on different rows hit distinct banks.
-    const int rs = (G * kPatch + 2 * kMaxR) | 1;  // <= C::kStride
+    // Rows are allocated for the widest window (a lane always reads 53 values);
+    // the stride lets lanes on different rows read 8-byte pairs from distinct banks.
+    const int rs = corr_region_stride(G);  // <= C::kStride
     const int scols = (G - 1) * kPatch + w;       // isf columns this item uses
     const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
     const int p0 = py * g.nx + px0;
@@ -633,8 +682,13 @@ __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
         const bool active = dy < w;
         const int dd = active ? dy : 0;
         float acc[NX];
-        corr_row<NX>(reg + dd * rs + u * kPatch, rs, tc + (size_t)(p0 + u) * kPatch * kTplStride,
-                     acc);
+        // the row start's parity is u's (21 is odd, rs even): warp-uniform
+        const float* rstart = reg + dd * rs + u * kPatch;
+        const float* tp = tc + (size_t)(p0 + u) * kPatch * kTplStride;
+        if (u & 1)
+          corr_row_pairs<NX, 1>(rstart, rs, tp, acc);
+        else
+          corr_row_pairs<NX, 0>(rstart, rs, tp, acc);
         if (active) {
           const float t2 = __ldg(tn2 + p0 + u);
           const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
