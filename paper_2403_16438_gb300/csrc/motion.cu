@@ -569,7 +569,12 @@ __device__ __forceinline__ void corr_row_pairs(const float* __restrict__ rrow, i
   }
 }
 
-template <int NX, int GP>
+// kPairs: the frame values of a row are read as 8-byte pairs (rows of stride
+// corr_region_stride(G)); otherwise as single words from rows of odd stride.
+// Pairs save load instructions, which pays on wide frames whose groups of
+// many warps compete for issue; the single-word form, with one copy of the row
+// loop, is faster where the groups have few patches (latency-bound).
+template <int NX, int GP, bool kPairs>
 __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
     k_corr_f32(const __grid_constant__ MotionBatch b, const int* __restrict__ list,
                const int* __restrict__ list_n) {
@@ -616,7 +621,7 @@ __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
     const int cols = G * kPatch + 2 * R;
     // Rows are allocated for the widest window (a lane always reads 53 values);
     // the stride lets lanes on different rows read 8-byte pairs from distinct banks.
-    const int rs = corr_region_stride(G);  // <= C::kStride
+    const int rs = kPairs ? corr_region_stride(G) : ((G * kPatch + 2 * kMaxR) | 1);  // <= C::kStride
     const int scols = (G - 1) * kPatch + w;       // isf columns this item uses
     const int ry = g.y0 + py * kPatch - R, rx = g.x0 + px0 * kPatch - R;
     const int p0 = py * g.nx + px0;
@@ -685,10 +690,14 @@ __global__ void __launch_bounds__(CorrGeom<GP>::kCta, 1)
         // the row start's parity is u's (21 is odd, rs even): warp-uniform
         const float* rstart = reg + dd * rs + u * kPatch;
         const float* tp = tc + (size_t)(p0 + u) * kPatch * kTplStride;
-        if (u & 1)
-          corr_row_pairs<NX, 1>(rstart, rs, tp, acc);
-        else
-          corr_row_pairs<NX, 0>(rstart, rs, tp, acc);
+        if constexpr (kPairs) {
+          if (u & 1)
+            corr_row_pairs<NX, 1>(rstart, rs, tp, acc);
+          else
+            corr_row_pairs<NX, 0>(rstart, rs, tp, acc);
+        } else {
+          corr_row<NX>(rstart, rs, tp, acc);
+        }
         if (active) {
           const float t2 = __ldg(tn2 + p0 + u);
           const float pscale = t2 > 0.f ? (float)kPatch * rsqrtf(t2) : 0.f;
@@ -752,8 +761,14 @@ int sm_count() {
 
 template <int GP>
 static cudaError_t corr_attr() {
-  return cudaFuncSetAttribute(k_corr_f32<kMaxWin, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(2 * CorrGeom<GP>::kSmem));
+  cudaError_t e = cudaFuncSetAttribute(k_corr_f32<kMaxWin, GP, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(2 * CorrGeom<GP>::kSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_corr_f32<kMaxWin, GP, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * CorrGeom<GP>::kSmem));
+  return e;
 }
 
 cudaError_t kernels_init() {
@@ -770,16 +785,20 @@ cudaError_t kernels_init() {
 
 bool corr_group_valid(int cg) { return cg == 0 || cg == 7 || cg == 8 || cg == 10 || cg == 11; }
 
-// The jobs of b whose group size is GP, with their work items counted in
-// groups of GP patches, in one launch.
-template <int GP>
+// Pair loads for a job: at least two groups per patch row, so that the
+// groups are mostly full.
+static bool corr_pairs_for(const MotionJob& J, int GP) { return J.g.nx >= 2 * GP; }
+
+// The jobs of b whose group size is GP (and whose load form is kPairs), with
+// their work items counted in groups of GP patches, in one launch.
+template <int GP, bool kPairs>
 static cudaError_t launch_corr_group(const MotionBatch& b, cudaStream_t st, const int* list,
                                      const int* list_n) {
   MotionBatch s{};
   long long c = 0;
   for (int i = 0; i < b.n; ++i) {
     const MotionJob& J = b.j[i];
-    if ((J.cg ? J.cg : kGroup) != GP) continue;
+    if ((J.cg ? J.cg : kGroup) != GP || corr_pairs_for(J, GP) != kPairs) continue;
     s.j[s.n] = J;
     c += (long long)J.nf * J.g.ny * ((J.g.nx + GP - 1) / GP);
     if (c > INT_MAX) return cudaErrorInvalidValue;
@@ -787,8 +806,8 @@ static cudaError_t launch_corr_group(const MotionBatch& b, cudaStream_t st, cons
   }
   if (s.n == 0 || c == 0) return cudaSuccess;
   const int grid = std::min(sm_count(), (int)((c + 1) / 2));
-  k_corr_f32<kMaxWin, GP><<<grid, CorrGeom<GP>::kCta, 2 * CorrGeom<GP>::kSmem, st>>>(s, list,
-                                                                                      list_n);
+  k_corr_f32<kMaxWin, GP, kPairs><<<grid, CorrGeom<GP>::kCta, 2 * CorrGeom<GP>::kSmem, st>>>(
+      s, list, list_n);
   return cudaGetLastError();
 }
 
@@ -799,10 +818,14 @@ cudaError_t launch_corr_f32_multi(const MotionBatch& b, cudaStream_t st, const i
   for (int i = 0; i < b.n; ++i)
     if (!corr_group_valid(b.j[i].cg)) return cudaErrorInvalidValue;
   cudaError_t e = kernels_init();
-  if (e == cudaSuccess) e = launch_corr_group<11>(b, st, list, list_n);
-  if (e == cudaSuccess) e = launch_corr_group<10>(b, st, list, list_n);
-  if (e == cudaSuccess) e = launch_corr_group<8>(b, st, list, list_n);
-  if (e == cudaSuccess) e = launch_corr_group<7>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<11, true>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<11, false>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<10, true>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<10, false>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<8, true>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<8, false>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<7, true>(b, st, list, list_n);
+  if (e == cudaSuccess) e = launch_corr_group<7, false>(b, st, list, list_n);
   return e;
 }
 
